@@ -1,0 +1,320 @@
+"""Benchmark of the fused LB reaction-diffusion step on GB300.
+
+Workload (default): gs_8192 -- Gray-Scott, two species, D2Q9, 8192 x 8192
+periodic, FP32, D_u = 0.1, D_v = 0.05, F = 0.037, k = 0.06, 256 random
+16 x 16 spots (u = 0.5, v = 0.25) plus 1 % noise.  One benchmark step is one
+LB time step over the whole grid: one launch of the fused kernel (pull-stream,
+rho_s = sum_i f_i,s, Gray-Scott source, BGK relaxation, store) with the FP64
+mass reduction of rho_s fused in.  The state (9.66 GB in two copies) is far
+larger than L2, so no L2 flush is needed between steps.
+
+Metric: MLUPS = species x sites x steps / s / 1e6 (species-site updates).
+
+Printed: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle (the reference for this method) on a bounded window of the same
+workload on the host cores instead.
+
+Multi-GPU: the method has no exchange step here; N ranks run N independent
+replicas (weak scaling) and the value is the sum over ranks of the work
+divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1007_3109_gb300 import inputs  # noqa: E402
+
+# Algorithmic bytes per site per step (read + write every stored value once).
+BYTES_PER_SITE = {("D2Q9", "fp32", 2): 144, ("D2Q5", "fp32", 2): 80, ("D2Q9", "fp64", 2): 288,
+                  ("D2Q9", "fp32_bf16dev", 2): 80, ("D2Q9", "fp32_fp16dev", 2): 80,
+                  ("D2Q5", "fp32_bf16dev", 2): 48, ("D2Q5", "fp32_fp16dev", 2): 48}
+
+# DRAM traffic per launch of the step kernel from an ncu capture (see
+# profiles/), valid only for the kernel source it was taken on.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def _src_hash(path):
+    with open(path, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower() == "active"})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+def workload_params(name: str, lattice: str, tau_from_diffusion):
+    w = inputs.WORKLOADS[name]
+    return w, [float(tau_from_diffusion(D)) for D in w["D"]]
+
+
+def run_cpu_oracle_sample(name, lattice, window, steps):
+    """The FP64 oracle, as it stands, on a periodic window of the workload."""
+    import oracle as orc
+    w, taus = workload_params(name, lattice, orc.tau_from_diffusion)
+    n = w["nx"]
+    rho_full_rows = inputs.rho0_spots(n, n, w["seed"], rows=slice(0, window))
+    rho0 = np.ascontiguousarray(rho_full_rows[:, :window, :window])
+    reac = orc.Reaction("gray_scott", F=w["reaction"]["F"], k=w["reaction"]["k"])
+    f = orc.init(lattice, rho0)
+    f = orc.step(lattice, taus, reac, f)  # warm the library and the pages
+    t0 = time.perf_counter()
+    f = orc.run(lattice, taus, reac, f, steps)
+    dt = time.perf_counter() - t0
+    ssu = 2 * window * window * steps
+    return ssu, dt, orc.threads()
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle as orc
+    lattice = args.lattice
+    w, taus = workload_params(args.workload, lattice, orc.tau_from_diffusion)
+    window = args.ref_window
+    n = w["nx"]
+    rho0 = np.ascontiguousarray(inputs.rho0_spots(n, n, w["seed"], rows=slice(0, window))[:, :window, :window])
+    reac = orc.Reaction("gray_scott", F=w["reaction"]["F"], k=w["reaction"]["k"])
+    f = orc.init(lattice, rho0)
+    for _ in range(args.warmup):
+        f = orc.step(lattice, taus, reac, f)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = orc.step(lattice, taus, reac, f)
+    dt = time.perf_counter() - t0
+    mlups = 2 * window * window * args.steps / dt / 1e6
+    sample = f"{window}x{window} periodic window of {args.workload} ({lattice}, 2 species, FP64), one oracle step per bench step"
+    line = {"metric": "MLUPS", "value": mlups, "unit": "MLUPS (species-site updates/s / 1e6)", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": args.workload, "lattice": lattice, "nx": window, "ny": window, "species": 2,
+                       "precision": "fp64", "sample_of": f"{n}x{n}"},
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": orc.threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="gs_8192")
+    ap.add_argument("--lattice", default="D2Q9", choices=["D2Q9", "D2Q5"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32_bf16dev", "fp32_fp16dev"])
+    ap.add_argument("--ref-window", type=int, default=512)
+    ap.add_argument("--cpu-window", type=int, default=1024)
+    ap.add_argument("--cpu-steps", type=int, default=100)
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    from paper_1007_3109_gb300 import binding as B
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w, taus = workload_params(args.workload, args.lattice, B.lb_rd_tau_from_diffusion)
+    n = w["nx"]
+    F, k = w["reaction"]["F"], w["reaction"]["k"]
+    rho0 = inputs.initial_density(args.workload)
+    stream = torch.cuda.current_stream()
+    sim = B.Simulation(args.lattice, 2, n, n, taus, "gray_scott", F=F, k=k, precision=args.precision,
+                       track_mass=True, stream=stream.cuda_stream)
+    rho0_dev = torch.from_numpy(rho0).cuda()
+    sim.init(rho0_dev)
+    sim.step(args.warmup)
+    barrier()
+
+    # -- device-timed region --------------------------------------------------
+    B.lb_rd_set_timing(sim.h, True)
+    launches0 = B.lb_rd_launch_count(sim.h)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            sim.step(1)
+        ev1.record(stream)
+        barrier()
+    launches = B.lb_rd_launch_count(sim.h) - launches0
+    ms_total = ev0.elapsed_time(ev1)
+    kernel_ms, kernel_launches = B.lb_rd_kernel_time(sim.h)
+    B.lb_rd_set_timing(sim.h, False)
+    t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_total = float(t.item())
+    mass = sim.mass()
+    assert np.all(np.isfinite(mass)), "non-finite mass"
+
+    sites = n * n
+    ssu_per_step = 2 * sites
+    value = ssu_per_step * args.steps * world / (ms_total / 1e3) / 1e6
+
+    # -- roofline of the step kernel ---------------------------------------------
+    peak, peak_kind = measured_peaks()
+    bps = BYTES_PER_SITE[(args.lattice, args.precision, 2)]
+    avg_launch_s = kernel_ms / 1e3 / max(kernel_launches, 1)
+    achieved = bps * sites / avg_launch_s / 1e9
+    traffic = None
+    kernel_file = {"fp32": "step_f32.cu", "fp64": "step_f64.cu"}.get(args.precision, "step_half.cu")
+    if os.path.exists(TRAFFIC_FILE):
+        with open(TRAFFIC_FILE) as fh:
+            tr = json.load(fh)
+        key = f"{args.workload}/{args.lattice}/{args.precision}"
+        ent = tr.get(key)
+        src = os.path.join(ROOT, "paper_1007_3109_gb300", "csrc", kernel_file)
+        if ent and ent.get("src_sha") == _src_hash(src):
+            traffic = ent["bytes_per_launch"]
+
+    # -- end to end through the C ABI with host buffers --------------------------
+    del rho0_dev
+    pinned_in = torch.from_numpy(rho0).pin_memory()
+    pinned_out = torch.empty(rho0.shape, dtype=torch.float64).pin_memory()
+    mass_out = np.empty(2)
+    rho_in_np, rho_out_np = pinned_in.numpy(), pinned_out.numpy()
+    e2e_steps = args.e2e_steps
+    barrier()
+    t0 = time.perf_counter()
+    B.lb_rd_init(sim.h, rho_in_np)
+    B.lb_rd_step(sim.h, e2e_steps)
+    B.lb_rd_moments(sim.h, rho_out_np, mass_out)
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    e2e_mlups = ssu_per_step * e2e_steps * world / e2e_s / 1e6
+    h2d = rho0.nbytes / e2e_steps
+    d2h = (rho0.nbytes + mass_out.nbytes) / e2e_steps
+
+    line = {
+        "metric": "MLUPS", "value": value, "unit": "MLUPS (species-site updates/s / 1e6)", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp64": "f64"}.get(args.precision, "f32+" + args.precision.split("_")[1]),
+        "data": "synthetic",
+        "config": {"workload": args.workload, "lattice": args.lattice, "nx": n, "ny": n, "species": 2,
+                   "precision": args.precision, "lb_steps_per_step": 1, "mass_diagnostic": "fused, every step",
+                   "l2": f"no flush: state of {2 * sim_state_bytes(args.lattice, args.precision, n) / 1e9:.2f} GB >> 129 MB L2",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "kernel": f"step_{args.precision}", "bytes_per_site": bps,
+                     "peak_kind": peak_kind, "avg_launch_ms": avg_launch_s * 1e3},
+        "e2e": {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "lb_steps": e2e_steps, "path": "lb_rd_init(host) + lb_rd_step + lb_rd_moments(host)"},
+        "gpu_launches": int(launches),
+        "clocks": clocks.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        ssu, dt, cores = run_cpu_oracle_sample(args.workload, args.lattice, args.cpu_window, args.cpu_steps)
+        line["cpu_baseline"] = {"value": ssu / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                                "sample": f"{args.cpu_window}x{args.cpu_window} periodic window of {args.workload}, "
+                                          f"{args.cpu_steps} FP64 oracle steps ({dt:.1f} s)"}
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def sim_state_bytes(lattice, precision, n):
+    Q = 9 if lattice == "D2Q9" else 5
+    per = {"fp32": 4 * Q, "fp64": 8 * Q}.get(precision, 4 + 2 * (Q - 1))
+    return 2 * per * n * n
+
+
+if __name__ == "__main__":
+    sys.exit(main())

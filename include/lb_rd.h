@@ -1,0 +1,188 @@
+/*
+ * lb_rd.h -- C ABI of the GB300 (sm_103a) lattice-Boltzmann reaction-diffusion
+ * library.
+ *
+ * The method is the multi-species lattice BGK scheme of Ayodele, Varnik and
+ * Raabe, "Lattice Boltzmann study of pattern formation in reaction-diffusion
+ * systems" (arXiv 1007.3109), Sec. II.A:
+ *
+ *   f_i,s(x + e_i, t + 1) = f_i,s(x, t) + (w_i rho_s - f_i,s(x, t)) / tau_s
+ *                           + w_i R_s(rho_1, ..., rho_S)          (Eq. relax)
+ *   rho_s = sum_i f_i,s,   f_i,s^eq = w_i rho_s                  (Eq. equili)
+ *   D_s = c_s^2 (tau_s - 1/2),  c_s^2 = 1/3   (end of Sec. II.A, Eq. app22)
+ *
+ * on a periodic nx x ny lattice (Sec. II.B, Sec. IV) with the D2Q9 velocity
+ * set of Eq. Weights (or D2Q5), and the reactions of Sec. II.B (transformation
+ * A -> B, Eq. reac_diff3) and Sec. III (Gray-Scott, Eqs. reac_diff10/11 in
+ * Pearson's (F, k) form).
+ *
+ * Conventions for every entry point:
+ *  - Every function returns an lb_rd_status; LB_RD_OK is 0.  On failure the
+ *    message of the calling thread's last error is in lb_rd_last_error().
+ *  - Densities are FP64, row-major [s][y][x] (x fastest), S * ny * nx values.
+ *  - A host pointer is any pageable or pinned host address; a device pointer
+ *    is a CUDA device address on the current device (e.g. a torch tensor's
+ *    data_ptr()).  is_device selects which one a pointer argument is.
+ *  - Handles own all the device memory they allocate; callers own their
+ *    buffers.  A device buffer passed in must stay alive until the call that
+ *    reads or writes it has returned and, for asynchronous calls, until the
+ *    handle's stream has been synchronised.
+ *  - Work is enqueued on the handle's stream (lb_rd_config.stream).  Calls
+ *    that return data to the host synchronise that stream.
+ *  - A handle is not thread safe: one thread at a time may use it.  The
+ *    server (lb_rd_server_*) is thread safe for submit and poll.
+ *  - No entry point falls back to the CPU: without a usable CUDA device the
+ *    calls that need one return LB_RD_ECUDA.
+ */
+#ifndef LB_RD_H
+#define LB_RD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LB_RD_API __attribute__((visibility("default")))
+#else
+#define LB_RD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+typedef enum {
+    LB_RD_OK = 0,
+    LB_RD_EINVAL = 1,   /* bad argument: tau <= 1/2, unknown enum, size < 1, NULL pointer */
+    LB_RD_ENOMEM = 2,   /* a device allocation or the server's memory budget failed */
+    LB_RD_ECUDA = 3,    /* a CUDA call failed (no device, launch error, ...) */
+    LB_RD_EPENDING = 4, /* server request not finished yet */
+    LB_RD_ETIMEOUT = 5, /* a bounded device-side wait gave up */
+    LB_RD_EBUSY = 6,    /* server full: request not admitted yet */
+    LB_RD_ENOTFOUND = 7 /* unknown or already collected server ticket */
+} lb_rd_status;
+
+/* Velocity sets.  D2Q9: e = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),
+ * (-1,-1),(1,-1) with w = 4/9, 1/9 x4, 1/36 x4 (Eq. Weights).  D2Q5: the
+ * first five velocities with w = 1/3, 1/6 x4 (not in the paper; the same
+ * c_s^2 = 1/3, so the same tau <-> D map). */
+typedef enum { LB_RD_D2Q9 = 0, LB_RD_D2Q5 = 1 } lb_rd_lattice;
+
+/* Storage and arithmetic of the distributions.
+ *  FP64:        f in double, double arithmetic without FMA contraction, in
+ *               the operation order of Eq. relax (bit-reproducible).
+ *  FP32:        f in float, float arithmetic.
+ *  FP32_BF16DEV / FP32_FP16DEV: float arithmetic; per species and site the
+ *               post-collision mass rho* = rho + R in float and the Q - 1
+ *               deviations g_i = (1 - 1/tau)(f_i - w_i rho), i >= 1, in bf16
+ *               or fp16 (g_0 = -sum g_i is implied); f*_i = w_i rho* + g_i. */
+typedef enum {
+    LB_RD_FP64 = 0,
+    LB_RD_FP32 = 1,
+    LB_RD_FP32_BF16DEV = 2,
+    LB_RD_FP32_FP16DEV = 3
+} lb_rd_precision;
+
+/* Reactions R_s(rho).
+ *  NONE:        R = 0 (pure diffusion).
+ *  LINEAR:      transformation A -> B at rate kappa (Sec. II.B):
+ *               R_A = -kappa rho_A; with a second species R_B = +kappa rho_A.
+ *  GRAY_SCOTT:  2 species u = A, v = B, Eqs. reac_diff10/11 with
+ *               A0 = k1 = 1, k_f = k_0 = F, k_2 = k:
+ *               R_u = -u v^2 + F (1 - u),  R_v = u v^2 - (F + k) v. */
+typedef enum {
+    LB_RD_REACTION_NONE = 0,
+    LB_RD_REACTION_LINEAR = 1,
+    LB_RD_REACTION_GRAY_SCOTT = 2
+} lb_rd_reaction_kind;
+
+typedef struct {
+    int32_t kind; /* lb_rd_reaction_kind */
+    double kappa; /* LINEAR rate */
+    double F;     /* GRAY_SCOTT feed rate */
+    double k;     /* GRAY_SCOTT kill rate */
+} lb_rd_reaction;
+
+/* One simulation: the paper's statement of the problem. */
+typedef struct {
+    int32_t lattice;         /* lb_rd_lattice */
+    int32_t nspecies;        /* 1 or 2 (GRAY_SCOTT needs 2) */
+    int64_t nx, ny;          /* periodic grid, 1 .. 65535 each */
+    double tau[2];           /* relaxation time per species, > 1/2 (D = (tau - 1/2)/3) */
+    lb_rd_reaction reaction;
+    int32_t precision;       /* lb_rd_precision */
+    int32_t track_mass;      /* nonzero: every step also reduces sum_x rho_s in FP64 */
+    void *stream;            /* cudaStream_t for all work; NULL = legacy default stream */
+} lb_rd_config;
+
+typedef struct lb_rd_handle lb_rd_handle;
+
+/* Message of the calling thread's last failure ("" if none).  Valid until the
+ * thread's next lb_rd call. */
+LB_RD_API const char *lb_rd_last_error(void);
+
+/* Library version string, e.g. "lb_rd 1.0 sm_103a". */
+LB_RD_API const char *lb_rd_version(void);
+
+/* tau = D / c_s^2 + 1/2 = 3 D + 1/2 (end of Sec. II.A).  Pure arithmetic. */
+LB_RD_API double lb_rd_tau_from_diffusion(double D);
+
+/* Validate cfg without touching the GPU; *bytes (if not NULL) receives the
+ * device memory lb_rd_create will allocate.  EINVAL names the bad field. */
+LB_RD_API int lb_rd_check_config(const lb_rd_config *cfg, size_t *bytes);
+
+/* Allocate a simulation on the current device.  The state is undefined until
+ * lb_rd_init.  ENOMEM if the device allocation fails. */
+LB_RD_API int lb_rd_create(const lb_rd_config *cfg, lb_rd_handle **out);
+
+/* Synchronise the handle's stream and free everything the handle owns.
+ * NULL is accepted. */
+LB_RD_API int lb_rd_destroy(lb_rd_handle *h);
+
+/* Set time t = 0 with f_i,s = w_i rho0_s at every site (equilibrium; the
+ * paper does not state its initial distributions).  rho0: [S][ny][nx] FP64,
+ * host (copied before return) or device (read asynchronously). */
+LB_RD_API int lb_rd_init(lb_rd_handle *h, const double *rho0, int is_device);
+
+/* Advance nsteps >= 0 time steps of Eq. relax (collide, then stream with
+ * periodic wrap).  Asynchronous on the handle's stream.  Each step is one
+ * fused kernel: pull-stream, rho_s = sum_i f_i,s, R_s, BGK + source, store. */
+LB_RD_API int lb_rd_step(lb_rd_handle *h, int64_t nsteps);
+
+/* Current time step t of the handle. */
+LB_RD_API int lb_rd_get_time(const lb_rd_handle *h, int64_t *t);
+
+/* Densities rho_s(x, t) = sum_i f_i,s(x, t) at the current time (pre-collision,
+ * i.e. after t streams; t = 0 gives sum_i w_i rho0).  rho_out: [S][ny][nx]
+ * FP64 or NULL; mass_out: S doubles, sum over all sites of rho_s, reduced in
+ * FP64, or NULL.  Synchronises the handle's stream. */
+LB_RD_API int lb_rd_moments(lb_rd_handle *h, double *rho_out, double *mass_out, int is_device);
+
+/* Post-collision distributions f*_i,s(x, t) (the values about to be streamed
+ * from x in step t -> t + 1), FP64 [s][i][y][x], Q planes per species.
+ * Synchronises. */
+LB_RD_API int lb_rd_get_distributions(lb_rd_handle *h, double *f_out, int is_device);
+
+/* Checkpoint: raw device state (distributions, densities, time) to a host
+ * buffer of lb_rd_state_size() bytes, and back.  Restore needs a handle
+ * created with the same config; the resumed run is bitwise identical to an
+ * uninterrupted one.  Both synchronise. */
+LB_RD_API int lb_rd_state_size(const lb_rd_handle *h, size_t *bytes);
+LB_RD_API int lb_rd_save(lb_rd_handle *h, void *host_buf, size_t bytes);
+LB_RD_API int lb_rd_restore(lb_rd_handle *h, const void *host_buf, size_t bytes);
+
+/* Device time of the step kernels.  When enabled, lb_rd_step brackets every
+ * step kernel with CUDA events on the handle's stream; lb_rd_kernel_time
+ * synchronises and returns the summed duration and launch count since the
+ * last reset (enable = 1 also resets). */
+LB_RD_API int lb_rd_set_timing(lb_rd_handle *h, int enable);
+LB_RD_API int lb_rd_kernel_time(lb_rd_handle *h, double *total_ms, int64_t *launches);
+
+/* Number of kernels this handle has launched since creation. */
+LB_RD_API int lb_rd_launch_count(const lb_rd_handle *h, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LB_RD_H */

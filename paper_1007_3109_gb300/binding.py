@@ -1,0 +1,281 @@
+"""Thin ctypes binding of the C ABI in include/lb_rd.h.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``lib/liblbrd.so``.  There is no CPU path; if the library is missing
+the calls raise instead of computing anything here.
+
+The functions keep the C names (``lb_rd_create``, ``lb_rd_step``, ...) and
+take numpy arrays (host memory) or CUDA torch tensors (device memory) where
+the C functions take a pointer plus an ``is_device`` flag.  ``Simulation`` is
+a small owner of one handle built from those functions.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_int32, c_int64, c_size_t, c_void_p, c_char_p
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "liblbrd.so")
+
+LB_RD_OK, LB_RD_EINVAL, LB_RD_ENOMEM, LB_RD_ECUDA = 0, 1, 2, 3
+LB_RD_EPENDING, LB_RD_ETIMEOUT, LB_RD_EBUSY, LB_RD_ENOTFOUND = 4, 5, 6, 7
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EPENDING", 5: "ETIMEOUT",
+                6: "EBUSY", 7: "ENOTFOUND"}
+
+LATTICES = {"D2Q9": 0, "D2Q5": 1}
+Q_OF = {"D2Q9": 9, "D2Q5": 5}
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_bf16dev": 2, "fp32_fp16dev": 3}
+REACTIONS = {"none": 0, "linear": 1, "gray_scott": 2}
+
+
+class LbRdError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class lb_rd_reaction(ctypes.Structure):
+    _fields_ = [("kind", c_int32), ("kappa", c_double), ("F", c_double), ("k", c_double)]
+
+
+class lb_rd_config(ctypes.Structure):
+    _fields_ = [("lattice", c_int32), ("nspecies", c_int32), ("nx", c_int64), ("ny", c_int64),
+                ("tau", c_double * 2), ("reaction", lb_rd_reaction), ("precision", c_int32),
+                ("track_mass", c_int32), ("stream", c_void_p)]
+
+
+_LIB = None
+
+_SIGNATURES = {
+    "lb_rd_last_error": ([], c_char_p),
+    "lb_rd_version": ([], c_char_p),
+    "lb_rd_tau_from_diffusion": ([c_double], c_double),
+    "lb_rd_check_config": ([POINTER(lb_rd_config), POINTER(c_size_t)], c_int),
+    "lb_rd_create": ([POINTER(lb_rd_config), POINTER(c_void_p)], c_int),
+    "lb_rd_destroy": ([c_void_p], c_int),
+    "lb_rd_init": ([c_void_p, c_void_p, c_int], c_int),
+    "lb_rd_step": ([c_void_p, c_int64], c_int),
+    "lb_rd_get_time": ([c_void_p, POINTER(c_int64)], c_int),
+    "lb_rd_moments": ([c_void_p, c_void_p, c_void_p, c_int], c_int),
+    "lb_rd_get_distributions": ([c_void_p, c_void_p, c_int], c_int),
+    "lb_rd_state_size": ([c_void_p, POINTER(c_size_t)], c_int),
+    "lb_rd_save": ([c_void_p, c_void_p, c_size_t], c_int),
+    "lb_rd_restore": ([c_void_p, c_void_p, c_size_t], c_int),
+    "lb_rd_set_timing": ([c_void_p, c_int], c_int),
+    "lb_rd_kernel_time": ([c_void_p, POINTER(c_double), POINTER(c_int64)], c_int),
+    "lb_rd_launch_count": ([c_void_p, POINTER(c_int64)], c_int),
+}
+
+
+def lib():
+    """Load liblbrd.so (once).  Raises if it has not been built."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'` (no CPU fallback exists)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _LIB = L
+    return _LIB
+
+
+def _check(status: int):
+    if status != LB_RD_OK:
+        raise LbRdError(status, lib().lb_rd_last_error().decode())
+
+
+def _ptr(buf, writable: bool = False):
+    """(address, is_device) of a numpy array or a torch tensor (contiguous)."""
+    if buf is None:
+        return None, 0
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"] or buf.dtype != np.float64:
+            raise ValueError("host buffers must be C-contiguous float64 arrays")
+        if writable and not buf.flags["WRITEABLE"]:
+            raise ValueError("output buffer is read-only")
+        return buf.ctypes.data, 0
+    # torch tensor (imported lazily: torch is plumbing, not required here)
+    if not buf.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    if str(buf.dtype) != "torch.float64":
+        raise ValueError("tensors must be float64")
+    return buf.data_ptr(), 1 if buf.is_cuda else 0
+
+
+def make_config(lattice="D2Q9", nspecies=1, nx=64, ny=64, tau=(1.0, 1.0), reaction="none", kappa=0.0, F=0.0,
+                k=0.0, precision="fp32", track_mass=False, stream=None) -> lb_rd_config:
+    cfg = lb_rd_config()
+    cfg.lattice = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
+    cfg.nspecies = int(nspecies)
+    cfg.nx, cfg.ny = int(nx), int(ny)
+    taus = [float(t) for t in np.atleast_1d(tau)]
+    taus += [1.0] * (2 - len(taus))
+    cfg.tau[0], cfg.tau[1] = float(taus[0]), float(taus[1])
+    cfg.reaction.kind = REACTIONS[reaction] if isinstance(reaction, str) else int(reaction)
+    cfg.reaction.kappa, cfg.reaction.F, cfg.reaction.k = float(kappa), float(F), float(k)
+    cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    cfg.track_mass = 1 if track_mass else 0
+    cfg.stream = stream
+    return cfg
+
+
+# -- C entry points with the same names --------------------------------------
+
+def lb_rd_version() -> str:
+    return lib().lb_rd_version().decode()
+
+
+def lb_rd_tau_from_diffusion(D: float) -> float:
+    return lib().lb_rd_tau_from_diffusion(float(D))
+
+
+def lb_rd_check_config(cfg: lb_rd_config) -> int:
+    n = c_size_t(0)
+    _check(lib().lb_rd_check_config(ctypes.byref(cfg), ctypes.byref(n)))
+    return n.value
+
+
+def lb_rd_create(cfg: lb_rd_config) -> int:
+    h = c_void_p()
+    _check(lib().lb_rd_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h.value
+
+
+def lb_rd_destroy(h: int):
+    _check(lib().lb_rd_destroy(h))
+
+
+def lb_rd_init(h: int, rho0):
+    p, dev = _ptr(rho0)
+    _check(lib().lb_rd_init(h, p, dev))
+
+
+def lb_rd_step(h: int, nsteps: int):
+    _check(lib().lb_rd_step(h, int(nsteps)))
+
+
+def lb_rd_get_time(h: int) -> int:
+    t = c_int64(0)
+    _check(lib().lb_rd_get_time(h, ctypes.byref(t)))
+    return t.value
+
+
+def lb_rd_moments(h: int, rho_out=None, mass_out=None):
+    pr, dev_r = _ptr(rho_out, True)
+    pm, dev_m = _ptr(mass_out, True)
+    if rho_out is not None and mass_out is not None and dev_r != dev_m:
+        raise ValueError("rho_out and mass_out must both be host or both be device buffers")
+    _check(lib().lb_rd_moments(h, pr, pm, dev_r if rho_out is not None else dev_m))
+
+
+def lb_rd_get_distributions(h: int, f_out):
+    p, dev = _ptr(f_out, True)
+    _check(lib().lb_rd_get_distributions(h, p, dev))
+
+
+def lb_rd_state_size(h: int) -> int:
+    n = c_size_t(0)
+    _check(lib().lb_rd_state_size(h, ctypes.byref(n)))
+    return n.value
+
+
+def lb_rd_save(h: int) -> bytearray:
+    buf = bytearray(lb_rd_state_size(h))
+    cbuf = (ctypes.c_char * len(buf)).from_buffer(buf)
+    _check(lib().lb_rd_save(h, ctypes.addressof(cbuf), len(buf)))
+    return buf
+
+
+def lb_rd_restore(h: int, buf: bytes | bytearray):
+    data = bytearray(buf)
+    cbuf = (ctypes.c_char * len(data)).from_buffer(data)
+    _check(lib().lb_rd_restore(h, ctypes.addressof(cbuf), len(data)))
+
+
+def lb_rd_set_timing(h: int, enable: bool):
+    _check(lib().lb_rd_set_timing(h, 1 if enable else 0))
+
+
+def lb_rd_kernel_time(h: int):
+    ms, n = c_double(0), c_int64(0)
+    _check(lib().lb_rd_kernel_time(h, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def lb_rd_launch_count(h: int) -> int:
+    n = c_int64(0)
+    _check(lib().lb_rd_launch_count(h, ctypes.byref(n)))
+    return n.value
+
+
+class Simulation:
+    """Owner of one lb_rd handle (a convenience over the functions above)."""
+
+    def __init__(self, lattice="D2Q9", nspecies=1, nx=64, ny=64, tau=(1.0, 1.0), reaction="none", kappa=0.0,
+                 F=0.0, k=0.0, precision="fp32", track_mass=False, stream=None):
+        self.cfg = make_config(lattice, nspecies, nx, ny, tau, reaction, kappa, F, k, precision, track_mass, stream)
+        self.lattice = lattice
+        self.S, self.nx, self.ny = int(nspecies), int(nx), int(ny)
+        self.Q = Q_OF[lattice] if isinstance(lattice, str) else (9 if lattice == 0 else 5)
+        self.h = lb_rd_create(self.cfg)
+
+    def init(self, rho0):
+        if isinstance(rho0, np.ndarray):
+            rho0 = np.ascontiguousarray(rho0, dtype=np.float64)
+            if rho0.shape != (self.S, self.ny, self.nx):
+                raise ValueError(f"rho0 must have shape {(self.S, self.ny, self.nx)}, got {rho0.shape}")
+        lb_rd_init(self.h, rho0)
+        return self
+
+    def step(self, n: int = 1):
+        lb_rd_step(self.h, n)
+        return self
+
+    @property
+    def time(self) -> int:
+        return lb_rd_get_time(self.h)
+
+    def moments(self):
+        rho = np.empty((self.S, self.ny, self.nx))
+        mass = np.empty(self.S)
+        lb_rd_moments(self.h, rho, mass)
+        return rho, mass
+
+    def mass(self):
+        m = np.empty(self.S)
+        lb_rd_moments(self.h, None, m)
+        return m
+
+    def distributions(self):
+        f = np.empty((self.S, self.Q, self.ny, self.nx))
+        lb_rd_get_distributions(self.h, f)
+        return f
+
+    def save(self) -> bytearray:
+        return lb_rd_save(self.h)
+
+    def restore(self, buf):
+        lb_rd_restore(self.h, buf)
+
+    def close(self):
+        if self.h:
+            lb_rd_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

