@@ -179,6 +179,7 @@ def main():
     ap.add_argument("--workload", default="gs_8192")
     ap.add_argument("--lattice", default="D2Q9", choices=["D2Q9", "D2Q5"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32_bf16dev", "fp32_fp16dev"])
+    ap.add_argument("--n", type=int, default=0, help="grid side override (same recipe, smaller grid)")
     ap.add_argument("--ref-window", type=int, default=512)
     ap.add_argument("--cpu-window", type=int, default=1024)
     ap.add_argument("--cpu-steps", type=int, default=100)
@@ -208,9 +209,9 @@ def main():
         torch.cuda.synchronize()
 
     w, taus = workload_params(args.workload, args.lattice, B.lb_rd_tau_from_diffusion)
-    n = w["nx"]
+    n = args.n or w["nx"]
     F, k = w["reaction"]["F"], w["reaction"]["k"]
-    rho0 = inputs.initial_density(args.workload)
+    rho0 = inputs.initial_density(args.workload, nx=n, ny=n)
     stream = torch.cuda.current_stream()
     sim = B.Simulation(args.lattice, 2, n, n, taus, "gray_scott", F=F, k=k, precision=args.precision,
                        track_mass=True, stream=stream.cuda_stream)
@@ -283,7 +284,7 @@ def main():
         "metric": "MLUPS", "value": value, "unit": "MLUPS (species-site updates/s / 1e6)", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32", "fp64": "f64"}.get(args.precision, "f32+" + args.precision.split("_")[1]),
+        "dtype": {"fp32": "f32", "fp64": "f64", "fp32_bf16dev": "f32+bf16", "fp32_fp16dev": "f32+f16"}[args.precision],
         "data": "synthetic",
         "config": {"workload": args.workload, "lattice": args.lattice, "nx": n, "ny": n, "species": 2,
                    "precision": args.precision, "lb_steps_per_step": 1, "mass_diagnostic": "fused, every step",

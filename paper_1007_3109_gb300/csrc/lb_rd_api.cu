@@ -126,8 +126,8 @@ int lb_rd_create(const lb_rd_config *cfg, lb_rd_handle **out) {
     if (e != cudaSuccess || ndev == 0)
         return fail(LB_RD_ECUDA, std::string("no CUDA device: ") + (e ? cudaGetErrorString(e) : "count is 0"));
     if (cfg->precision == LB_RD_FP32_BF16DEV || cfg->precision == LB_RD_FP32_FP16DEV) {
-        if (cfg->nx % 8 != 0)
-            return fail(LB_RD_EINVAL, "16-bit deviation storage needs nx to be a multiple of 8");
+        if (cfg->nx % 4 != 0)
+            return fail(LB_RD_EINVAL, "16-bit deviation storage needs nx to be a multiple of 4");
     }
     lb_rd_handle *h = new lb_rd_handle();
     h->cfg = *cfg;

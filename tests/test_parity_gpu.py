@@ -125,7 +125,8 @@ def test_decay_128_full_run(lat):
         k = 2 * np.pi / 128
         G = (1 - 1e-3) * (2 / 3 + np.cos(k) / 3)
         amp = 2 * np.mean(rho[0] * np.cos(k * np.arange(128))[None, :])
-        assert amp == pytest.approx(0.1 * G ** t, rel=1e-3 if prec == "fp32" else 1e-8)
+        # the 1e-6 input noise projects onto the mode at the 1e-6 relative level
+        assert amp == pytest.approx(0.1 * G ** t, rel=1e-3 if prec == "fp32" else 1e-5)
         assert mass[0] / rho0.sum() == pytest.approx((1 - 1e-3) ** t, rel=1e-5 if prec == "fp32" else 1e-12)
 
 

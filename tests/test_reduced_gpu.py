@@ -1,0 +1,102 @@
+"""Reduced storage (FP32 rho* + bf16/fp16 deviations) against the FP64 oracle.
+
+Tolerances (rel = max |gpu - oracle| / max |oracle| per species) come from the
+arithmetic and were calibrated once against a CPU emulation of the same
+storage scheme (numpy, FP32 arithmetic, deviations rounded to bf16 / fp16):
+on the Gray-Scott noisy-square run the emulation gives 2.6e-4 (bf16) and
+3.6e-5 (fp16) after 150 steps and 2.3e-3 / 4.8e-4 after 1000 steps, where
+the instability amplifies every rounding (FP32 storage alone: 2e-4).  The
+bounds below are about twice those.  With tau = 1 the deviations vanish and
+the scheme is exact up to FP32 rounding; the mass is carried by rho* alone,
+so sum_x rho is conserved at FP32 accuracy whatever the deviation format.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from oracle import Reaction
+from paper_1007_3109_gb300 import binding as B
+from paper_1007_3109_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+BOUND_150 = {"fp32_bf16dev": 6e-4, "fp32_fp16dev": 1e-4}
+BOUND_1000 = {"fp32_bf16dev": 5e-3, "fp32_fp16dev": 1e-3}
+
+
+def rel_err(a, b):
+    return np.max(np.abs(a - b), axis=(1, 2)) / np.max(np.abs(b), axis=(1, 2))
+
+
+def run(lat, S, rho0, taus, reac, steps, precision, track_mass=False):
+    ny, nx = rho0.shape[1:]
+    with B.Simulation(lat, S, nx, ny, taus, reac.kind, kappa=reac.kappa, F=reac.F, k=reac.k, precision=precision,
+                      track_mass=track_mass) as sim:
+        sim.init(rho0).step(steps)
+        rho, mass = sim.moments()
+        f = sim.distributions()
+    return rho, mass, f
+
+
+@pytest.mark.parametrize("precision", ["fp32_bf16dev", "fp32_fp16dev"])
+@pytest.mark.parametrize("lat,ny,nx", [("D2Q9", 48, 64), ("D2Q5", 40, 36), ("D2Q9", 3, 12)])
+def test_gray_scott_150_steps(lat, ny, nx, precision):
+    rho0 = inputs.rho0_square(nx, ny, seed=21, side=max(2, min(nx, ny) // 3))
+    taus, reac = [0.8, 0.65], Reaction("gray_scott", F=0.04, k=0.06)
+    rho, mass, f = run(lat, 2, rho0, taus, reac, 150, precision)
+    ref = orc.density(lat, orc.run(lat, taus, reac, orc.init(lat, rho0), 150))
+    assert np.all(rel_err(rho, ref) <= BOUND_150[precision]), rel_err(rho, ref)
+    # exported distributions are consistent with the densities of the next pull
+    ex, ey, _ = orc.lattice(lat)
+    pulled = sum(np.roll(f[:, i], (ey[i], ex[i]), axis=(1, 2)) for i in range(len(ex)))
+    ref1 = orc.density(lat, orc.run(lat, taus, reac, orc.init(lat, rho0), 151))
+    assert np.all(rel_err(pulled, ref1) <= BOUND_150[precision] * 2)
+
+
+@pytest.mark.parametrize("precision", ["fp32_bf16dev", "fp32_fp16dev"])
+def test_tau1_is_exact_up_to_fp32(precision):
+    rho0 = inputs.rho0_cosine(64, 32, seed=5, noise=1e-3)
+    reac = Reaction("linear", kappa=1e-3)
+    rho, mass, _ = run("D2Q9", 1, rho0, [1.0], reac, 500, precision)
+    ref = orc.density("D2Q9", orc.run("D2Q9", [1.0], reac, orc.init("D2Q9", rho0), 500))
+    assert rel_err(rho, ref)[0] <= 1e-5
+
+
+@pytest.mark.parametrize("precision", ["fp32_bf16dev", "fp32_fp16dev"])
+def test_mass_conserved_without_reaction(precision):
+    rng = np.random.default_rng(2)
+    rho0 = 0.5 + rng.random((2, 40, 48))
+    rho, mass, _ = run("D2Q9", 2, rho0, [0.7, 1.4], Reaction("none"), 400, precision, track_mass=True)
+    np.testing.assert_allclose(mass, rho0.sum(axis=(1, 2)), rtol=2e-6)
+    ref = orc.density("D2Q9", orc.run("D2Q9", [0.7, 1.4], Reaction("none"), orc.init("D2Q9", rho0), 400))
+    assert np.all(rel_err(rho, ref) <= BOUND_150[precision])
+
+
+@pytest.mark.parametrize("precision", ["fp32_bf16dev", "fp32_fp16dev"])
+def test_gs_512_1000_steps(precision):
+    w = inputs.WORKLOADS["gs_512"]
+    rho0 = inputs.initial_density("gs_512")
+    taus = [float(t) for t in orc.tau_from_diffusion(np.array(w["D"]))]
+    reac = Reaction("gray_scott", F=0.04, k=0.06)
+    rho, mass, _ = run("D2Q9", 2, rho0, taus, reac, 1000, precision)
+    ref = orc.density("D2Q9", orc.run("D2Q9", taus, reac, orc.init("D2Q9", rho0), 1000))
+    assert np.all(rel_err(rho, ref) <= BOUND_1000[precision]), rel_err(rho, ref)
+
+
+def test_reduced_storage_rejects_unaligned_width():
+    with pytest.raises(B.LbRdError) as ei:
+        B.Simulation("D2Q9", 2, 70, 16, [0.8, 0.65], "gray_scott", F=0.04, k=0.06, precision="fp32_bf16dev")
+    assert ei.value.status == B.LB_RD_EINVAL
+
+
+def test_reduced_checkpoint_is_bitwise():
+    rho0 = inputs.rho0_square(64, 32, seed=6, side=12)
+    kw = dict(lattice="D2Q9", nspecies=2, nx=64, ny=32, tau=[0.8, 0.65], reaction="gray_scott", F=0.04, k=0.06,
+              precision="fp32_bf16dev")
+    with B.Simulation(**kw) as a, B.Simulation(**kw) as b:
+        a.init(rho0).step(20)
+        ck = a.save()
+        a.step(30)
+        b.restore(ck)
+        b.step(30)
+        np.testing.assert_array_equal(a.moments()[0], b.moments()[0])
