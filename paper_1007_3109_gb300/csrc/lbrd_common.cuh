@@ -32,9 +32,16 @@ struct Lattice<9> {
     // Weight class: 0 rest, 1 axis, 2 diagonal (Eq. Weights: 4/9, 1/9, 1/36).
     __host__ __device__ static constexpr int wclass(int i) { return i == 0 ? 0 : (i <= 4 ? 1 : 2); }
     static constexpr int kClasses = 3;
+    // Double: the correctly rounded 4/9, 1/9, 1/36.  Float: w1 one ulp below
+    // the rounded 1/9, w2 = w1 / 4 and w0 = 1 - 5 w1, all exact in float, so
+    // that the weights sum to exactly 1 (the correctly rounded floats sum to
+    // 1 + 2e-8, which would drift the mass by that much every step).
     template <typename T>
     __host__ __device__ static constexpr T wc(int c) {
-        return c == 0 ? T(4) / T(9) : (c == 1 ? T(1) / T(9) : T(1) / T(36));
+        if constexpr (sizeof(T) == 4)
+            return c == 0 ? T(0x1.c71c74p-2f) : (c == 1 ? T(0x1.c71c70p-4f) : T(0x1.c71c70p-6f));
+        else
+            return c == 0 ? T(4) / T(9) : (c == 1 ? T(1) / T(9) : T(1) / T(36));
     }
 };
 
@@ -44,10 +51,14 @@ struct Lattice<5> {
     __host__ __device__ static constexpr int ey(int i) { return i == 2 ? 1 : (i == 4 ? -1 : 0); }
     __host__ __device__ static constexpr int wclass(int i) { return i == 0 ? 0 : 1; }
     static constexpr int kClasses = 2;
-    // D2Q5 (not in the paper): w0 = 1/3, w1..4 = 1/6, c_s^2 = 1/3.
+    // D2Q5 (not in the paper): w0 = 1/3, w1..4 = 1/6, c_s^2 = 1/3.  Float:
+    // w1 = rounded 1/6 and w0 = 1 - 4 w1 (exact), an exact partition of unity.
     template <typename T>
     __host__ __device__ static constexpr T wc(int c) {
-        return c == 0 ? T(1) / T(3) : T(1) / T(6);
+        if constexpr (sizeof(T) == 4)
+            return c == 0 ? T(0x1.555554p-2f) : T(0x1.555556p-3f);
+        else
+            return c == 0 ? T(1) / T(3) : T(1) / T(6);
     }
 };
 

@@ -31,9 +31,11 @@ def tol(precision, reac, steps):
 
 
 def rel_err(a, b):
+    """max |a - b| / max |b| per species (denominator floored at 1e-4 so that
+    a field that has decayed to ~0 is judged on absolute error)."""
     a, b = np.asarray(a), np.asarray(b)
     ax = tuple(range(1, a.ndim))
-    return np.max(np.abs(a - b), axis=ax) / np.max(np.abs(b), axis=ax)
+    return np.max(np.abs(a - b), axis=ax) / np.maximum(np.max(np.abs(b), axis=ax), 1e-4)
 
 
 def oracle_density(lat, taus, reac, rho0, steps):
@@ -152,7 +154,7 @@ def test_fused_mass_diagnostic():
                           track_mass=True) as sim:
             sim.init(rho0).step(60)
             m = sim.mass()
-        np.testing.assert_allclose(m, ref.sum(axis=(1, 2)), rtol=1e-6 if prec == "fp32" else 1e-13)
+        np.testing.assert_allclose(m, ref.sum(axis=(1, 2)), rtol=1e-5 if prec == "fp32" else 1e-13)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
