@@ -181,6 +181,44 @@ LB_RD_API int lb_rd_kernel_time(lb_rd_handle *h, double *total_ms, int64_t *laun
 /* Number of kernels this handle has launched since creation. */
 LB_RD_API int lb_rd_launch_count(const lb_rd_handle *h, int64_t *launches);
 
+
+/* Allocation-free fused step.  The paper has no counterpart: this exists for
+ * callers that cannot allocate device memory, such as a real-time loop whose
+ * memory was all reserved at start-up or a plugin that may only use the
+ * buffers its host application hands it.  It never calls cudaMalloc,
+ * cudaFree or any allocating library routine.
+ *
+ * One time step t -> t + 1 of cfg (the same fused kernel as lb_rd_step) from
+ * state_in to state_out, and mass_out[s] = sum_x rho_s(t + 1), reduced in
+ * FP64.  All three pointers are device memory owned by the caller; state_in
+ * and state_out must not overlap.  Work goes on cfg->stream; the call returns
+ * without synchronising.
+ *
+ * State layout: the post-collision distributions f*(t) exactly as they follow
+ * the 56-byte header of an lb_rd_save buffer (lb_rd_save's payload up to the
+ * density cache).  Rows have a pitch of nx rounded up to a multiple of 32
+ * elements.  FP64 / FP32: S * Q planes [s][i][y][pitch] of double / float.
+ * 16-bit deviation storage: per species one float plane of rho* followed by
+ * Q - 1 planes of 16-bit deviations.
+ *
+ * Scratch: the reduction's per-block partial sums and its arrival counter
+ * live in a static device array of 65536 doubles plus 256 bytes (512 KiB),
+ * held by every GPU that loads the library until the process exits.  One
+ * block runs per tile (256 x 2 sites in FP32 and 16-bit storage, 32 x 4
+ * sites in FP64), and the grid's tiles times S may not exceed 65536: for two
+ * species that is up to 16.7 million FP32 sites (4096 x 4096) or 4.2 million
+ * FP64 sites (2048 x 2048).  Larger grids return LB_RD_EINVAL with the
+ * counts in the message.
+ *
+ * The first call on a device, with that device current, looks up the
+ * array's device address (cudaGetSymbolAddress) and caches it; make that
+ * first call before any stream capture.  Every call clears the counter on
+ * its stream before the kernel.  All calls share the one array, which keeps
+ * the last call's contents: calls whose work overlaps on the GPU (different
+ * streams, or several host threads) race on it and must be serialised by the
+ * caller. */
+LB_RD_API int lb_rd_step_noalloc(const lb_rd_config *cfg, const void *state_in, void *state_out, double *mass_out);
+
 #ifdef __cplusplus
 }
 #endif

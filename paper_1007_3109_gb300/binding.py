@@ -66,6 +66,7 @@ _SIGNATURES = {
     "lb_rd_set_timing": ([c_void_p, c_int], c_int),
     "lb_rd_kernel_time": ([c_void_p, POINTER(c_double), POINTER(c_int64)], c_int),
     "lb_rd_launch_count": ([c_void_p, POINTER(c_int64)], c_int),
+    "lb_rd_step_noalloc": ([POINTER(lb_rd_config), c_void_p, c_void_p, c_void_p], c_int),
 }
 
 
@@ -212,6 +213,11 @@ def lb_rd_launch_count(h: int) -> int:
     n = c_int64(0)
     _check(lib().lb_rd_launch_count(h, ctypes.byref(n)))
     return n.value
+
+
+def lb_rd_step_noalloc(cfg: lb_rd_config, state_in: int, state_out: int, mass_out: int):
+    """Allocation-free step between caller-owned device buffers (addresses)."""
+    _check(lib().lb_rd_step_noalloc(ctypes.byref(cfg), state_in, state_out, mass_out))
 
 
 class Simulation:

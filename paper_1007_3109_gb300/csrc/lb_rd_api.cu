@@ -44,6 +44,11 @@ size_t rho_elem(int prec) { return prec == LB_RD_FP64 ? 8 : 4; }
 
 }  // namespace
 
+namespace lbrd {
+// Error reporting for entry points defined in other translation units.
+int report_error(int code, const std::string &msg) { return fail(code, msg); }
+}  // namespace lbrd
+
 struct lb_rd_handle {
     lb_rd_config cfg{};
     int Q = 0, S = 0, prec = 0;

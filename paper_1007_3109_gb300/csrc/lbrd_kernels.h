@@ -43,6 +43,16 @@ StepShape step_shape_half(int64_t nx, int64_t ny);
 cudaError_t launch_step_half(int Q, int S, int half_kind, const StepArgs &a, cudaStream_t st);
 cudaError_t launch_init_half(int Q, int S, int half_kind, const InitArgs &a, cudaStream_t st);
 
+// One block per tile (no persistent grid) and the tile counts of those
+// launches: used by the allocation-free entry point, whose per-block scratch
+// is sized from the launch.
+int64_t step_tiles_f64(int64_t nx, int64_t ny);
+int64_t step_tiles_f32(int64_t nx, int64_t ny);
+int64_t step_tiles_half(int64_t nx, int64_t ny);
+cudaError_t launch_step_f64_per_tile(int Q, int S, const StepArgs &a, cudaStream_t st);
+cudaError_t launch_step_f32_per_tile(int Q, int S, const StepArgs &a, cudaStream_t st);
+cudaError_t launch_step_half_per_tile(int Q, int S, int half_kind, const StepArgs &a, cudaStream_t st);
+
 // Post-collision distributions of the stored state as packed FP64
 // [s][i][y][x].  prec: lb_rd_precision.
 cudaError_t launch_export(int prec, int Q, int S, const void *state, int64_t nx, int64_t ny, int64_t pitch,

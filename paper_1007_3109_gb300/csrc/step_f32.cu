@@ -217,4 +217,30 @@ cudaError_t launch_init_f32(int Q, int S, const InitArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// One block per tile instead of the persistent grid: the launch used by the
+// allocation-free entry point, whose per-block scratch is sized from the grid.
+int64_t step_tiles_f32(int64_t nx, int64_t ny) {
+    int64_t tiles_x, ntiles;
+    tiles_for(nx, ny, &tiles_x, &ntiles);
+    return ntiles;
+}
+
+namespace {
+template <int Q, int S>
+cudaError_t launch_per_tile(const StepArgs &a, cudaStream_t st) {
+    int64_t tiles_x, ntiles;
+    tiles_for(a.nx, a.ny, &tiles_x, &ntiles);
+    step_f32_kernel<Q, S><<<(unsigned)ntiles, dim3(kBX, kBY), 0, st>>>(a, tiles_x, ntiles);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_step_f32_per_tile(int Q, int S, const StepArgs &a, cudaStream_t st) {
+    if (Q == 9 && S == 1) return launch_per_tile<9, 1>(a, st);
+    if (Q == 9 && S == 2) return launch_per_tile<9, 2>(a, st);
+    if (Q == 5 && S == 1) return launch_per_tile<5, 1>(a, st);
+    if (Q == 5 && S == 2) return launch_per_tile<5, 2>(a, st);
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace lbrd

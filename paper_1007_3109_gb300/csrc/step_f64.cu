@@ -130,4 +130,25 @@ cudaError_t launch_init_f64(int Q, int S, const InitArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// One block per tile instead of the persistent grid (allocation-free entry).
+int64_t step_tiles_f64(int64_t nx, int64_t ny) { return ((nx + kBX - 1) / kBX) * ((ny + kBY - 1) / kBY); }
+
+namespace {
+template <int Q, int S>
+cudaError_t launch_per_tile(const StepArgs &a, cudaStream_t st) {
+    const int64_t tiles_x = (a.nx + kBX - 1) / kBX;
+    const int64_t ntiles = tiles_x * ((a.ny + kBY - 1) / kBY);
+    step_f64_kernel<Q, S><<<(unsigned)ntiles, dim3(kBX, kBY), 0, st>>>(a, tiles_x, ntiles);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_step_f64_per_tile(int Q, int S, const StepArgs &a, cudaStream_t st) {
+    if (Q == 9 && S == 1) return launch_per_tile<9, 1>(a, st);
+    if (Q == 9 && S == 2) return launch_per_tile<9, 2>(a, st);
+    if (Q == 5 && S == 1) return launch_per_tile<5, 1>(a, st);
+    if (Q == 5 && S == 2) return launch_per_tile<5, 2>(a, st);
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace lbrd

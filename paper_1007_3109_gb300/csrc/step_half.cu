@@ -262,4 +262,34 @@ cudaError_t launch_init_half(int Q, int S, int half_kind, const InitArgs &a, cud
     return half_kind ? dispatch_init<1>(Q, S, a, st) : dispatch_init<0>(Q, S, a, st);
 }
 
+// One block per tile instead of the persistent grid (allocation-free entry).
+int64_t step_tiles_half(int64_t nx, int64_t ny) {
+    int64_t tiles_x, ntiles;
+    tiles_for(nx, ny, &tiles_x, &ntiles);
+    return ntiles;
+}
+
+namespace {
+template <int Q, int S, int H>
+cudaError_t launch_per_tile(const StepArgs &a, cudaStream_t st) {
+    int64_t tiles_x, ntiles;
+    tiles_for(a.nx, a.ny, &tiles_x, &ntiles);
+    step_half_kernel<Q, S, H><<<(unsigned)ntiles, dim3(kBX, kBY), 0, st>>>(a, tiles_x, ntiles);
+    return cudaGetLastError();
+}
+template <int H>
+cudaError_t dispatch_per_tile(int Q, int S, const StepArgs &a, cudaStream_t st) {
+    if (Q == 9 && S == 1) return launch_per_tile<9, 1, H>(a, st);
+    if (Q == 9 && S == 2) return launch_per_tile<9, 2, H>(a, st);
+    if (Q == 5 && S == 1) return launch_per_tile<5, 1, H>(a, st);
+    if (Q == 5 && S == 2) return launch_per_tile<5, 2, H>(a, st);
+    return cudaErrorInvalidValue;
+}
+}  // namespace
+
+cudaError_t launch_step_half_per_tile(int Q, int S, int half_kind, const StepArgs &a, cudaStream_t st) {
+    if (a.nx % kVec) return cudaErrorInvalidValue;
+    return half_kind ? dispatch_per_tile<1>(Q, S, a, st) : dispatch_per_tile<0>(Q, S, a, st);
+}
+
 }  // namespace lbrd
