@@ -170,6 +170,148 @@ def reference_arm(args):
     return 0
 
 
+def batch_mode(args):
+    """gs_sweep_256: 1024 Gray-Scott instances of 256^2 on the (F, k) grid, one
+    persistent launch per step over all of them (graph-captured), against a
+    plain loop that steps every instance through its own handle."""
+    import torch
+    from paper_1007_3109_gb300 import binding as B
+    torch.cuda.set_device(0)
+    w = inputs.WORKLOADS["gs_sweep_256"]
+    F, k = inputs.sweep_params()
+    n = w["nx"]
+    ninst = args.instances or w["instances"]
+    taus = [float(B.lb_rd_tau_from_diffusion(D)) for D in w["D"]]
+    cfgs = [dict(lattice="D2Q9", nspecies=2, nx=n, ny=n, tau=taus, reaction="gray_scott", F=float(F[i]),
+                 k=float(k[i]), precision=args.precision) for i in range(ninst)]
+    rho0s = [inputs.rho0_square(n, n, seed=w["seed"] + i) for i in range(ninst)]
+    K, W = args.steps, args.warmup
+    ssu = 2 * n * n * ninst * K
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with B.Batch(cfgs) as b:
+        for i in range(ninst):
+            b.init(i, rho0s[i])
+        b.step(W)
+        torch.cuda.synchronize()
+        ev0.record()
+        b.step(K)
+        ev1.record()
+        torch.cuda.synchronize()
+        batched_ms = ev0.elapsed_time(ev1)
+        _, launches = B.lb_rd_batch_get_time(b.b)
+        mass0 = b.moments(0)[1]
+    # plain loop: every instance through its own handle, instance after instance
+    sims = [B.Simulation(**c) for c in cfgs]
+    for sim, r in zip(sims, rho0s):
+        sim.init(r).step(W)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev0.record()
+    for sim in sims:
+        sim.step(K)
+    ev1.record()
+    torch.cuda.synchronize()
+    loop_ms = ev0.elapsed_time(ev1)
+    loop_wall = (time.perf_counter() - t0) * 1e3
+    np.testing.assert_allclose(sims[0].mass(), mass0, rtol=1e-12)
+    for sim in sims:
+        sim.close()
+    peak, peak_kind = measured_peaks()
+    bps = BYTES_PER_SITE[("D2Q9", args.precision, 2)]
+    line = {"metric": "MLUPS", "value": ssu / (batched_ms / 1e3) / 1e6, "unit": "MLUPS (species-site updates/s / 1e6)",
+            "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": batched_ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
+            "data": "synthetic",
+            "config": {"workload": "gs_sweep_256", "instances": ninst, "nx": n, "ny": n, "species": 2,
+                       "precision": args.precision, "graph_steps": 64,
+                       "l2": f"no flush: state of {2 * ninst * sim_state_bytes('D2Q9', args.precision, n) / 1e9:.2f} GB"},
+            "roofline": {"bound": "hbm", "achieved": bps * n * n * ninst / (batched_ms / K / 1e3) / 1e9, "peak": peak,
+                         "unit": "GB/s", "peak_kind": peak_kind},
+            "plain_loop": {"value": ssu / (loop_ms / 1e3) / 1e6, "ms_per_step": loop_ms / K,
+                           "wall_ms_per_step": loop_wall / K, "launches_per_step": ninst},
+            "speedup_vs_plain_loop": loop_ms / batched_ms, "gpu_launches": int(K)}
+    line["roofline"]["frac"] = line["roofline"]["achieved"] / peak
+    print(json.dumps(line))
+    return 0
+
+
+def serving_mode(args):
+    """gs_serving: a seeded Poisson stream of Gray-Scott requests (side in
+    [64, 2048], diffusion scale in {1, 2, 4}, steps uniform in [1e3, 5e4]
+    times --steps-scale) replayed in real time against the continuous-batching
+    server and against a serial first-in first-out loop of plain handles."""
+    import torch
+    from paper_1007_3109_gb300 import binding as B
+    torch.cuda.set_device(0)
+    w = inputs.WORKLOADS["gs_serving"]
+    nreq = args.requests
+    req = inputs.serving_requests(nreq, w["seed"], rate=1.0)
+    steps = np.maximum(1, np.round(req["steps"] * args.steps_scale)).astype(np.int64)
+    sides, scales = req["side"], req["scale"]
+    ssu = 2 * sides.astype(np.float64) ** 2 * steps
+    capacity = args.capacity_mlups * 1e6  # SSU/s the GPU sustains (the step benchmark's figure)
+    rate = args.load * capacity / ssu.mean()
+    arrivals = req["arrival_s"] / rate  # the seeded unit-rate stream, rescaled
+    F, k = w["reaction"]["F"], w["reaction"]["k"]
+
+    def cfg(j):
+        D = np.array(w["D"]) * scales[j]
+        return dict(lattice="D2Q9", nspecies=2, nx=int(sides[j]), ny=int(sides[j]),
+                    tau=[float(B.lb_rd_tau_from_diffusion(d)) for d in D], reaction="gray_scott", F=F, k=k,
+                    precision="fp32")
+
+    rho0s = [inputs.rho0_square(int(sides[j]), int(sides[j]), seed=w["seed"] + j) for j in range(nreq)]
+
+    # continuous batching
+    srv = B.lb_rd_server_create(hbm_budget_bytes=int(args.budget_gb * 1e9), max_slots=args.slots,
+                                steps_per_tick=args.tick)
+    t0 = time.perf_counter()
+    tickets = []
+    for j in range(nreq):
+        dt = arrivals[j] - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(B.lb_rd_submit(srv, B.make_config(**cfg(j)), rho0s[j], int(steps[j])))
+    B.lb_rd_server_drain(srv, 3_600_000)
+    lat, ends, starts0 = [], [], None
+    for j, t in enumerate(tickets):
+        rc, st = B.lb_rd_poll(srv, t)
+        assert rc == B.LB_RD_OK, rc
+        lat.append((st["end_ns"] - st["arrival_ns"]) / 1e9)
+        ends.append(st["end_ns"])
+        starts0 = st["arrival_ns"] if starts0 is None else min(starts0, st["arrival_ns"])
+    stats = B.lb_rd_server_stats(srv)
+    B.lb_rd_server_destroy(srv)
+    makespan = (max(ends) - starts0) / 1e9
+    # serial FIFO plain loop on the same stream
+    t0 = time.perf_counter()
+    lat_fifo = []
+    for j in range(nreq):
+        dt = arrivals[j] - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        with B.Simulation(**cfg(j)) as sim:
+            sim.init(rho0s[j]).step(int(steps[j]))
+            sim.moments()
+        lat_fifo.append(time.perf_counter() - t0 - arrivals[j])
+    makespan_fifo = time.perf_counter() - t0
+    total = ssu.sum()
+    line = {"metric": "MLUPS", "value": total / makespan / 1e6, "unit": "MLUPS (species-site updates/s / 1e6)",
+            "n_gpus": 1, "steps": int(steps.sum()), "warmup": 0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "gs_serving", "requests": nreq, "steps_scale": args.steps_scale,
+                       "load": args.load, "capacity_mlups": args.capacity_mlups, "budget_gb": args.budget_gb,
+                       "slots": args.slots, "steps_per_tick": args.tick, "arrival_rate_per_s": rate},
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "max": float(np.max(lat))},
+            "fifo_plain_loop": {"value": total / makespan_fifo / 1e6,
+                                "latency_s": {"p50": float(np.percentile(lat_fifo, 50)),
+                                              "p99": float(np.percentile(lat_fifo, 99))}},
+            "server": stats, "gpu_launches": stats["launches"]}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -185,11 +327,26 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=100)
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--tune-iters", type=int, default=10)
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serving"])
+    ap.add_argument("--variant", default="", help="force a launch variant by name (after the autotune sweep)")
+    ap.add_argument("--instances", type=int, default=0)
+    ap.add_argument("--requests", type=int, default=64)
+    ap.add_argument("--steps-scale", type=float, default=0.05)
+    ap.add_argument("--load", type=float, default=0.8)
+    ap.add_argument("--capacity-mlups", type=float, default=75000.0)
+    ap.add_argument("--budget-gb", type=float, default=64.0)
+    ap.add_argument("--slots", type=int, default=64)
+    ap.add_argument("--tick", type=int, default=64)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return reference_arm(args)
+    if args.mode == "batch":
+        return batch_mode(args)
+    if args.mode == "serving":
+        return serving_mode(args)
 
     import torch
     from paper_1007_3109_gb300 import binding as B
@@ -218,10 +375,19 @@ def main():
     rho0_dev = torch.from_numpy(rho0).cuda()
     sim.init(rho0_dev)
     sim.step(args.warmup)
+    # project autotuner: every launch variant timed on this state (not advanced)
+    best, times = B.lb_rd_autotune(sim.h, iters=args.tune_iters)
+    nvar = B.lb_rd_variant_count(args.precision)
+    names = [B.lb_rd_variant_name(args.precision, v) for v in range(nvar)]
+    tuning = {names[v]: (round(times[v], 4) if times[v] >= 0 else None) for v in range(nvar)}
+    if args.variant:
+        best = names.index(args.variant)
+        B.lb_rd_set_variant(sim.h, best)
+    sim.step(3)
     barrier()
 
-    # -- device-timed region --------------------------------------------------
-    B.lb_rd_set_timing(sim.h, True)
+    # -- device-timed region: K step launches and nothing else, bracketed by
+    # CUDA events on the launching stream ------------------------------------
     launches0 = B.lb_rd_launch_count(sim.h)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clocks:
@@ -233,8 +399,7 @@ def main():
         barrier()
     launches = B.lb_rd_launch_count(sim.h) - launches0
     ms_total = ev0.elapsed_time(ev1)
-    kernel_ms, kernel_launches = B.lb_rd_kernel_time(sim.h)
-    B.lb_rd_set_timing(sim.h, False)
+    kernel_ms, kernel_launches = ms_total, launches  # the region holds only step launches
     t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -289,9 +454,10 @@ def main():
         "config": {"workload": args.workload, "lattice": args.lattice, "nx": n, "ny": n, "species": 2,
                    "precision": args.precision, "lb_steps_per_step": 1, "mass_diagnostic": "fused, every step",
                    "l2": f"no flush: state of {2 * sim_state_bytes(args.lattice, args.precision, n) / 1e9:.2f} GB >> 129 MB L2",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "variant": B.lb_rd_variant_name(args.precision, best), "autotune_ms_per_launch": tuning},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": f"step_{args.precision}", "bytes_per_site": bps,
+                     "traffic": traffic, "kernel": f"step_{args.precision}:{B.lb_rd_variant_name(args.precision, best)}", "bytes_per_site": bps,
                      "peak_kind": peak_kind, "avg_launch_ms": avg_launch_s * 1e3},
         "e2e": {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "lb_steps": e2e_steps, "path": "lb_rd_init(host) + lb_rd_step + lb_rd_moments(host)"},

@@ -181,6 +181,113 @@ LB_RD_API int lb_rd_kernel_time(lb_rd_handle *h, double *total_ms, int64_t *laun
 /* Number of kernels this handle has launched since creation. */
 LB_RD_API int lb_rd_launch_count(const lb_rd_handle *h, int64_t *launches);
 
+/* Launch variants and the autotuner.  The step kernel of a precision comes in
+ * several launch variants (tile shape, register budget, cache policy; see
+ * lb_rd_variant_name).  lb_rd_autotune times every variant on the handle's own
+ * state -- reading the current state and writing the spare copy, so the
+ * simulation is unchanged -- with one warm-up launch and `iters` timed
+ * launches each, selects the fastest for this handle and caches the choice per
+ * (device, precision, lattice, species, nx, ny); handles created later with
+ * the same shape start from the cached choice.  times_ms (may be NULL)
+ * receives the mean time per launch of each variant, at most max_times
+ * entries.  Synchronises.  lb_rd_set_variant forces a variant (-1: cached or
+ * default). */
+LB_RD_API int lb_rd_variant_count(int32_t precision, int32_t *count);
+LB_RD_API const char *lb_rd_variant_name(int32_t precision, int32_t variant);
+LB_RD_API int lb_rd_autotune(lb_rd_handle *h, int32_t iters, int32_t *best, double *times_ms, int32_t max_times);
+LB_RD_API int lb_rd_set_variant(lb_rd_handle *h, int32_t variant);
+LB_RD_API int lb_rd_get_variant(const lb_rd_handle *h, int32_t *variant);
+
+/* ---- Batched simulations ------------------------------------------------
+ * n independent simulations advanced together, e.g. a phase-diagram sweep of
+ * Gray-Scott (F, k) pairs or a set of diffusion-rescaled runs (Sec. IV).  All
+ * share lattice, species count, precision and stream (taken from cfgs[0]);
+ * grid size, tau and reaction constants may differ per instance.  Each time
+ * step is ONE launch of a persistent kernel that walks the combined
+ * (instance x tile) work list; lb_rd_batch_step replays the steps as CUDA
+ * graphs.  Every instance computes exactly what a single handle with its
+ * config computes (bitwise: same kernel body, same arithmetic).  Supported
+ * precisions: FP32 and the 16-bit deviation formats. */
+typedef struct lb_rd_batch lb_rd_batch;
+
+/* Allocate n >= 1 instances (two state copies each plus density caches).
+ * EINVAL if the configs disagree on lattice, nspecies or precision. */
+LB_RD_API int lb_rd_batch_create(const lb_rd_config *cfgs, int32_t n, lb_rd_batch **out);
+LB_RD_API int lb_rd_batch_destroy(lb_rd_batch *b);
+
+/* Initialise instance idx at equilibrium with rho0 ([S][ny][nx] FP64, host or
+ * device), as lb_rd_init.  Every instance must be initialised before the
+ * first lb_rd_batch_step.  Allowed only while the batch time is 0. */
+LB_RD_API int lb_rd_batch_init(lb_rd_batch *b, int32_t idx, const double *rho0, int is_device);
+
+/* Advance every instance by nsteps >= 0 steps (asynchronous).  The final step
+ * also writes each instance's densities. */
+LB_RD_API int lb_rd_batch_step(lb_rd_batch *b, int64_t nsteps);
+
+/* Steps per captured CUDA graph (an even number >= 2), or 0 to launch every
+ * step directly.  Default 64. */
+LB_RD_API int lb_rd_batch_set_graph(lb_rd_batch *b, int32_t steps_per_graph);
+
+/* Densities and FP64 mass of instance idx at the batch's current time (as
+ * lb_rd_moments).  Synchronises. */
+LB_RD_API int lb_rd_batch_moments(lb_rd_batch *b, int32_t idx, double *rho_out, double *mass_out, int is_device);
+
+/* Batch time (steps taken) and kernels launched since creation. */
+LB_RD_API int lb_rd_batch_get_time(const lb_rd_batch *b, int64_t *t, int64_t *launches);
+
+/* ---- Serving: continuous batching of simulation requests -----------------
+ * A server owns a worker thread and a CUDA stream.  Requests (a config, host
+ * rho0 and a step count) are queued on submit and admitted first-in first-out
+ * while the number of resident requests is below max_slots and their device
+ * memory (two state copies plus the density cache) fits hbm_budget_bytes.
+ * Resident requests advance together, steps_per_tick steps at a time (fewer
+ * when a request finishes sooner), each step ONE launch of the batched kernel
+ * over all of them; requests that arrive meanwhile are admitted between ticks
+ * as slots and memory free up.  A finished request's densities and mass are
+ * copied to host memory and its device memory is released.  Each result is
+ * bitwise what a single handle with the same config computes.  FP32 and the
+ * 16-bit deviation formats; all requests of a server share lattice, species
+ * count and precision (given in the server config).  submit and poll are
+ * thread safe. */
+typedef struct {
+    size_t hbm_budget_bytes;  /* device memory the resident requests may hold */
+    int32_t max_slots;        /* resident requests at most, >= 1 */
+    int32_t steps_per_tick;   /* steps between admission points, >= 1 */
+    int32_t lattice, nspecies, precision;
+    void *stream;             /* NULL: the server creates its own stream */
+} lb_rd_server_config;
+
+typedef struct {
+    int64_t arrival_ns;  /* submit time (steady clock) */
+    int64_t start_ns;    /* admission time */
+    int64_t end_ns;      /* results on the host */
+    int64_t steps;
+    int32_t status;      /* final status of the request */
+} lb_rd_request_stats;
+
+typedef struct lb_rd_server lb_rd_server;
+
+LB_RD_API int lb_rd_server_create(const lb_rd_server_config *cfg, lb_rd_server **out);
+/* Stops admitting, finishes nothing further, frees everything. */
+LB_RD_API int lb_rd_server_destroy(lb_rd_server *srv);
+/* Queue a request; rho0 ([S][ny][nx] FP64 host) is copied before return.
+ * EINVAL for a bad config or one that does not match the server's lattice,
+ * species or precision.  A request larger than the whole budget is accepted
+ * and then fails with ENOMEM (see poll). */
+LB_RD_API int lb_rd_submit(lb_rd_server *srv, const lb_rd_config *cfg, const double *rho0, int64_t nsteps,
+                           uint64_t *ticket);
+/* LB_RD_EPENDING while queued or running; otherwise the request's final
+ * status (LB_RD_OK, LB_RD_ENOMEM, ...), after which the ticket is released.
+ * On OK, rho_out ([S][ny][nx] FP64 host) and mass_out (S doubles) receive the
+ * results if not NULL.  stats (may be NULL) is filled in every case.
+ * ENOTFOUND for an unknown or already collected ticket. */
+LB_RD_API int lb_rd_poll(lb_rd_server *srv, uint64_t ticket, double *rho_out, double *mass_out,
+                         lb_rd_request_stats *stats);
+/* Block until every submitted request has finished or timeout_ms elapses
+ * (LB_RD_ETIMEOUT). */
+LB_RD_API int lb_rd_server_drain(lb_rd_server *srv, int64_t timeout_ms);
+/* Counters: batched step launches, ticks, requests finished. */
+LB_RD_API int lb_rd_server_stats(const lb_rd_server *srv, int64_t *launches, int64_t *ticks, int64_t *finished);
 
 /* Allocation-free fused step.  The paper has no counterpart: this exists for
  * callers that cannot allocate device memory, such as a real-time loop whose

@@ -67,6 +67,24 @@ _SIGNATURES = {
     "lb_rd_kernel_time": ([c_void_p, POINTER(c_double), POINTER(c_int64)], c_int),
     "lb_rd_launch_count": ([c_void_p, POINTER(c_int64)], c_int),
     "lb_rd_step_noalloc": ([POINTER(lb_rd_config), c_void_p, c_void_p, c_void_p], c_int),
+    "lb_rd_variant_count": ([c_int32, POINTER(c_int32)], c_int),
+    "lb_rd_variant_name": ([c_int32, c_int32], c_char_p),
+    "lb_rd_autotune": ([c_void_p, c_int32, POINTER(c_int32), POINTER(c_double), c_int32], c_int),
+    "lb_rd_set_variant": ([c_void_p, c_int32], c_int),
+    "lb_rd_get_variant": ([c_void_p, POINTER(c_int32)], c_int),
+    "lb_rd_batch_create": ([POINTER(lb_rd_config), c_int32, POINTER(c_void_p)], c_int),
+    "lb_rd_batch_destroy": ([c_void_p], c_int),
+    "lb_rd_batch_init": ([c_void_p, c_int32, c_void_p, c_int], c_int),
+    "lb_rd_batch_step": ([c_void_p, c_int64], c_int),
+    "lb_rd_batch_set_graph": ([c_void_p, c_int32], c_int),
+    "lb_rd_batch_moments": ([c_void_p, c_int32, c_void_p, c_void_p, c_int], c_int),
+    "lb_rd_batch_get_time": ([c_void_p, POINTER(c_int64), POINTER(c_int64)], c_int),
+    "lb_rd_server_create": ([ctypes.c_void_p, POINTER(c_void_p)], c_int),
+    "lb_rd_server_destroy": ([c_void_p], c_int),
+    "lb_rd_submit": ([c_void_p, POINTER(lb_rd_config), c_void_p, c_int64, POINTER(ctypes.c_uint64)], c_int),
+    "lb_rd_poll": ([c_void_p, ctypes.c_uint64, c_void_p, c_void_p, c_void_p], c_int),
+    "lb_rd_server_drain": ([c_void_p, c_int64], c_int),
+    "lb_rd_server_stats": ([c_void_p, POINTER(c_int64), POINTER(c_int64), POINTER(c_int64)], c_int),
 }
 
 
@@ -220,6 +238,174 @@ def lb_rd_step_noalloc(cfg: lb_rd_config, state_in: int, state_out: int, mass_ou
     _check(lib().lb_rd_step_noalloc(ctypes.byref(cfg), state_in, state_out, mass_out))
 
 
+def lb_rd_variant_count(precision) -> int:
+    n = c_int32(0)
+    _check(lib().lb_rd_variant_count(PRECISIONS.get(precision, precision), ctypes.byref(n)))
+    return n.value
+
+
+def lb_rd_variant_name(precision, variant: int) -> str:
+    return lib().lb_rd_variant_name(PRECISIONS.get(precision, precision), int(variant)).decode()
+
+
+def lb_rd_autotune(h: int, iters: int = 20, max_times: int = 64):
+    """Returns (best variant, mean ms per launch of every variant)."""
+    best = c_int32(0)
+    times = (c_double * max_times)()
+    _check(lib().lb_rd_autotune(h, int(iters), ctypes.byref(best), times, max_times))
+    return best.value, list(times)
+
+
+def lb_rd_set_variant(h: int, variant: int):
+    _check(lib().lb_rd_set_variant(h, int(variant)))
+
+
+def lb_rd_get_variant(h: int) -> int:
+    v = c_int32(0)
+    _check(lib().lb_rd_get_variant(h, ctypes.byref(v)))
+    return v.value
+
+
+def lb_rd_batch_create(cfgs) -> int:
+    arr = (lb_rd_config * len(cfgs))(*cfgs)
+    b = c_void_p()
+    _check(lib().lb_rd_batch_create(arr, len(cfgs), ctypes.byref(b)))
+    return b.value
+
+
+def lb_rd_batch_destroy(b: int):
+    _check(lib().lb_rd_batch_destroy(b))
+
+
+def lb_rd_batch_init(b: int, idx: int, rho0):
+    p, dev = _ptr(rho0)
+    _check(lib().lb_rd_batch_init(b, int(idx), p, dev))
+
+
+def lb_rd_batch_step(b: int, nsteps: int):
+    _check(lib().lb_rd_batch_step(b, int(nsteps)))
+
+
+def lb_rd_batch_set_graph(b: int, steps_per_graph: int):
+    _check(lib().lb_rd_batch_set_graph(b, int(steps_per_graph)))
+
+
+def lb_rd_batch_moments(b: int, idx: int, rho_out=None, mass_out=None):
+    pr, dev_r = _ptr(rho_out, True)
+    pm, dev_m = _ptr(mass_out, True)
+    _check(lib().lb_rd_batch_moments(b, int(idx), pr, pm, dev_r if rho_out is not None else dev_m))
+
+
+def lb_rd_batch_get_time(b: int):
+    t, n = c_int64(0), c_int64(0)
+    _check(lib().lb_rd_batch_get_time(b, ctypes.byref(t), ctypes.byref(n)))
+    return t.value, n.value
+
+
+class lb_rd_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", c_size_t), ("max_slots", c_int32), ("steps_per_tick", c_int32),
+                ("lattice", c_int32), ("nspecies", c_int32), ("precision", c_int32), ("stream", c_void_p)]
+
+
+class lb_rd_request_stats(ctypes.Structure):
+    _fields_ = [("arrival_ns", c_int64), ("start_ns", c_int64), ("end_ns", c_int64), ("steps", c_int64),
+                ("status", c_int32)]
+
+
+def lb_rd_server_create(hbm_budget_bytes, max_slots=64, steps_per_tick=64, lattice="D2Q9", nspecies=2,
+                        precision="fp32", stream=None) -> int:
+    cfg = lb_rd_server_config(int(hbm_budget_bytes), int(max_slots), int(steps_per_tick), LATTICES[lattice],
+                              int(nspecies), PRECISIONS[precision], stream)
+    s = c_void_p()
+    _check(lib().lb_rd_server_create(ctypes.byref(cfg), ctypes.byref(s)))
+    return s.value
+
+
+def lb_rd_server_destroy(s: int):
+    _check(lib().lb_rd_server_destroy(s))
+
+
+def lb_rd_submit(s: int, cfg: lb_rd_config, rho0: np.ndarray, nsteps: int) -> int:
+    rho0 = np.ascontiguousarray(rho0, dtype=np.float64)
+    t = ctypes.c_uint64(0)
+    _check(lib().lb_rd_submit(s, ctypes.byref(cfg), rho0.ctypes.data, int(nsteps), ctypes.byref(t)))
+    return t.value
+
+
+def lb_rd_poll(s: int, ticket: int, rho_out=None, mass_out=None):
+    """Returns (status, stats dict); status LB_RD_EPENDING while not finished.
+    A failed request's status is returned, not raised."""
+    st = lb_rd_request_stats()
+    pr = rho_out.ctypes.data if rho_out is not None else None
+    pm = mass_out.ctypes.data if mass_out is not None else None
+    rc = lib().lb_rd_poll(s, ctypes.c_uint64(ticket), pr, pm, ctypes.byref(st))
+    if rc in (LB_RD_EINVAL, LB_RD_ENOTFOUND):
+        _check(rc)
+    return rc, {"arrival_ns": st.arrival_ns, "start_ns": st.start_ns, "end_ns": st.end_ns, "steps": st.steps,
+                "status": st.status}
+
+
+def lb_rd_server_drain(s: int, timeout_ms: int):
+    _check(lib().lb_rd_server_drain(s, int(timeout_ms)))
+
+
+def lb_rd_server_stats(s: int):
+    a, b, c = c_int64(0), c_int64(0), c_int64(0)
+    _check(lib().lb_rd_server_stats(s, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return {"launches": a.value, "ticks": b.value, "finished": c.value}
+
+
+class Batch:
+    """Owner of one lb_rd_batch (instances described by make_config kwargs)."""
+
+    def __init__(self, configs):
+        self.kw = [dict(c) for c in configs]
+        self.cfgs = [make_config(**c) for c in configs]
+        self.b = lb_rd_batch_create(self.cfgs)
+
+    def init(self, idx, rho0):
+        lb_rd_batch_init(self.b, idx, np.ascontiguousarray(rho0, dtype=np.float64)
+                         if isinstance(rho0, np.ndarray) else rho0)
+        return self
+
+    def step(self, n=1):
+        lb_rd_batch_step(self.b, n)
+        return self
+
+    def set_graph(self, steps):
+        lb_rd_batch_set_graph(self.b, steps)
+        return self
+
+    def moments(self, idx):
+        c = self.kw[idx]
+        S = int(c.get("nspecies", 1))
+        rho = np.empty((S, int(c["ny"]), int(c["nx"])))
+        mass = np.empty(S)
+        lb_rd_batch_moments(self.b, idx, rho, mass)
+        return rho, mass
+
+    @property
+    def time(self):
+        return lb_rd_batch_get_time(self.b)[0]
+
+    def close(self):
+        if self.b:
+            lb_rd_batch_destroy(self.b)
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Simulation:
     """Owner of one lb_rd handle (a convenience over the functions above)."""
 
@@ -262,6 +448,13 @@ class Simulation:
         f = np.empty((self.S, self.Q, self.ny, self.nx))
         lb_rd_get_distributions(self.h, f)
         return f
+
+    def set_variant(self, variant: int):
+        lb_rd_set_variant(self.h, variant)
+        return self
+
+    def autotune(self, iters: int = 10):
+        return lb_rd_autotune(self.h, iters)
 
     def save(self) -> bytearray:
         return lb_rd_save(self.h)

@@ -1,0 +1,390 @@
+// Batched simulations: one persistent launch per time step over the combined
+// (instance x tile) work list of all instances, replayed as CUDA graphs.
+//
+// Every instance has its own grid, relaxation times and reaction constants
+// in a descriptor; the kernel walks global tile indices with a grid-stride
+// loop, finds the instance a tile belongs to by a forward scan (a block's
+// tiles only increase) and runs the same tile body as the single-simulation
+// kernels (step_f32_kernel.cuh, step_half_kernel.cuh), so each instance
+// computes exactly what a single handle computes.
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "lb_rd.h"
+#include "lbrd_kernels.h"
+#include "step_f32_kernel.cuh"
+#include "step_half_kernel.cuh"
+
+namespace lbrd {
+int report_error(int code, const std::string &msg);
+
+namespace {
+
+constexpr int kBX = 64, kBY = 2, kNT = kBX * kBY;  // the tile shape of both tile bodies
+static_assert(half::kBX == kBX && half::kBY == kBY, "tile shapes must agree");
+
+template <int Q, int S, int MODE>  // MODE 0: FP32 storage, 1: bf16 deviations, 2: fp16 deviations
+__global__ void __launch_bounds__(kNT, 4) batch_kernel(const BatchItem *__restrict__ items, int nitems,
+                                                       int64_t total_tiles) {
+    const int lane = threadIdx.x & 31;
+    double acc[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) acc[s] = 0.0;
+    int it = 0;
+    for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+        while (it + 1 < nitems && items[it + 1].tile_begin <= t) ++it;
+        const BatchItem &b = items[it];
+        const int64_t local = t - b.tile_begin;
+        const int64_t ty = local / b.tiles_x, tx = local - ty * b.tiles_x;
+        const int64_t x0 = (tx * kBX + threadIdx.x) * 4, y = ty * kBY + threadIdx.y;
+        if (MODE == 0) f32::tile_f32<Q, S, 0>(b.a, x0, y, lane, acc);
+        else half::tile_half<Q, S, MODE - 1>(b.a, x0, y, lane, acc);
+    }
+}
+
+template <int Q, int S, int MODE>
+cudaError_t launch_batch(const BatchItem *items, int n, int64_t total, cudaStream_t st) {
+    auto kern = batch_kernel<Q, S, MODE>;
+    const unsigned grid = persistent_blocks(kern, kNT, total);
+    kern<<<grid, dim3(kBX, kBY), 0, st>>>(items, n, total);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t dispatch_batch(int Q, int S, const BatchItem *items, int n, int64_t total, cudaStream_t st) {
+    if (Q == 9 && S == 1) return launch_batch<9, 1, MODE>(items, n, total, st);
+    if (Q == 9 && S == 2) return launch_batch<9, 2, MODE>(items, n, total, st);
+    if (Q == 5 && S == 1) return launch_batch<5, 1, MODE>(items, n, total, st);
+    if (Q == 5 && S == 2) return launch_batch<5, 2, MODE>(items, n, total, st);
+    return cudaErrorInvalidValue;
+}
+
+int64_t pitch_for(int64_t nx) { return (nx + 31) / 32 * 32; }
+
+size_t align256(size_t n) { return (n + 255) / 256 * 256; }
+
+}  // namespace
+
+int64_t batch_tiles_x(int64_t nx) { return ((nx + 3) / 4 + kBX - 1) / kBX; }
+
+int64_t batch_tiles(int64_t nx, int64_t ny) { return batch_tiles_x(nx) * ((ny + kBY - 1) / kBY); }
+
+cudaError_t launch_batch_step(int mode, int Q, int S, const BatchItem *items, int n, int64_t total_tiles,
+                             cudaStream_t st) {
+    switch (mode) {
+        case 0: return dispatch_batch<0>(Q, S, items, n, total_tiles, st);
+        case 1: return dispatch_batch<1>(Q, S, items, n, total_tiles, st);
+        case 2: return dispatch_batch<2>(Q, S, items, n, total_tiles, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace lbrd
+
+struct lb_rd_batch {
+    std::vector<lb_rd_config> cfgs;
+    int Q = 0, S = 0, prec = 0, mode = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<size_t> state_off, rho_off;  // byte offsets of each instance
+    std::vector<int64_t> pitch;
+    size_t state_total = 0, rho_total = 0;
+    char *buf[2] = {nullptr, nullptr};
+    char *rho = nullptr;
+    lbrd::BatchItem *d_items[4] = {nullptr, nullptr, nullptr, nullptr};  // [parity + 2 * emit_rho]
+    int64_t total_tiles = 0;
+    double *stage = nullptr;
+    size_t stage_elems = 0;
+    double *partials = nullptr;
+    unsigned int *counter = nullptr;
+    double *mass = nullptr;
+    std::vector<bool> inited;
+    int cur = 0;
+    int64_t t = 0, launches = 0;
+    int graph_steps = 64;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // by starting parity
+};
+
+namespace {
+
+using lbrd::report_error;
+
+int cuda_err(cudaError_t e, const char *what) {
+    return report_error(e == cudaErrorMemoryAllocation ? LB_RD_ENOMEM : LB_RD_ECUDA,
+                        std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+cudaError_t launch_one(lb_rd_batch *b, int parity, bool emit) {
+    const lbrd::BatchItem *items = b->d_items[parity + (emit ? 2 : 0)];
+    return lbrd::launch_batch_step(b->mode, b->Q, b->S, items, (int)b->cfgs.size(), b->total_tiles, b->stream);
+}
+
+void drop_graphs(lb_rd_batch *b) {
+    for (auto &g : b->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_rd_batch_destroy(lb_rd_batch *b) {
+    if (!b) return LB_RD_OK;
+    cudaStreamSynchronize(b->stream);
+    drop_graphs(b);
+    cudaFree(b->buf[0]);
+    cudaFree(b->buf[1]);
+    cudaFree(b->rho);
+    for (auto p : b->d_items) cudaFree(p);
+    cudaFree(b->stage);
+    cudaFree(b->partials);
+    cudaFree(b->counter);
+    cudaFree(b->mass);
+    delete b;
+    return LB_RD_OK;
+}
+
+int lb_rd_batch_create(const lb_rd_config *cfgs, int32_t n, lb_rd_batch **out) {
+    if (!out || !cfgs || n < 1) return report_error(LB_RD_EINVAL, "lb_rd_batch_create: need cfgs, n >= 1 and out");
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        int rc = lb_rd_check_config(&cfgs[i], nullptr);
+        if (rc) return rc;
+        if (cfgs[i].lattice != cfgs[0].lattice || cfgs[i].nspecies != cfgs[0].nspecies ||
+            cfgs[i].precision != cfgs[0].precision)
+            return report_error(LB_RD_EINVAL, "lb_rd_batch_create: instance " + std::to_string(i) +
+                                                  " differs from instance 0 in lattice, nspecies or precision");
+    }
+    const int prec = cfgs[0].precision;
+    if (prec == LB_RD_FP64)
+        return report_error(LB_RD_EINVAL, "lb_rd_batch_create: batches support fp32 and 16-bit deviation storage");
+    const bool half = prec != LB_RD_FP32;
+    for (int i = 0; i < n; ++i)
+        if (half && cfgs[i].nx % 4)
+            return report_error(LB_RD_EINVAL, "lb_rd_batch_create: 16-bit deviation storage needs nx % 4 == 0");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return report_error(LB_RD_ECUDA, "no CUDA device");
+
+    lb_rd_batch *b = new lb_rd_batch();
+    b->cfgs.assign(cfgs, cfgs + n);
+    b->Q = cfgs[0].lattice == LB_RD_D2Q9 ? 9 : 5;
+    b->S = cfgs[0].nspecies;
+    b->prec = prec;
+    b->mode = prec == LB_RD_FP32 ? 0 : (prec == LB_RD_FP32_BF16DEV ? 1 : 2);
+    b->stream = static_cast<cudaStream_t>(cfgs[0].stream);
+    b->inited.assign(n, false);
+    size_t max_parts = 0;
+    std::vector<lbrd::BatchItem> items(n);
+    for (int i = 0; i < n; ++i) {
+        const lb_rd_config &c = cfgs[i];
+        const int64_t pitch = lbrd::pitch_for(c.nx);
+        b->pitch.push_back(pitch);
+        b->state_off.push_back(b->state_total);
+        b->rho_off.push_back(b->rho_total);
+        b->state_total += lbrd::align256(lbrd::state_plane_bytes(prec, b->Q, b->S, c.ny, pitch));
+        b->rho_total += lbrd::align256((size_t)b->S * c.ny * pitch * 4);
+        const size_t parts = lbrd::mass_partials_needed(c.nx, c.ny);
+        if (parts > max_parts) max_parts = parts;
+        lbrd::BatchItem &it = items[i];
+        it.a = lbrd::StepArgs{};
+        it.a.nx = c.nx;
+        it.a.ny = c.ny;
+        it.a.pitch = pitch;
+        it.a.plane = c.ny * pitch;
+        for (int s = 0; s < 2; ++s) it.a.omega[s] = s < b->S ? 1.0 / c.tau[s] : 0.0;
+        it.a.rkind = c.reaction.kind;
+        it.a.kappa = c.reaction.kappa;
+        it.a.F = c.reaction.F;
+        it.a.k = c.reaction.k;
+        it.tiles_x = lbrd::batch_tiles_x(c.nx);
+        it.tile_begin = b->total_tiles;
+        b->total_tiles += lbrd::batch_tiles(c.nx, c.ny);
+    }
+    cudaError_t e = cudaSuccess;
+    if (!e) e = cudaMalloc(&b->buf[0], b->state_total);
+    if (!e) e = cudaMalloc(&b->buf[1], b->state_total);
+    if (!e) e = cudaMalloc(&b->rho, b->rho_total);
+    if (!e) e = cudaMalloc(&b->partials, max_parts * b->S * sizeof(double));
+    if (!e) e = cudaMalloc(&b->counter, sizeof(unsigned int));
+    if (!e) e = cudaMalloc(&b->mass, 2 * sizeof(double));
+    if (!e) e = cudaMemset(b->counter, 0, sizeof(unsigned int));
+    for (int k = 0; k < 4 && !e; ++k) {
+        const int parity = k & 1;
+        const bool emit = k >= 2;
+        std::vector<lbrd::BatchItem> v = items;
+        for (int i = 0; i < n; ++i) {
+            v[i].a.src = b->buf[parity] + b->state_off[i];
+            v[i].a.dst = b->buf[parity ^ 1] + b->state_off[i];
+            v[i].a.rho_out = emit ? b->rho + b->rho_off[i] : nullptr;
+        }
+        e = cudaMalloc(&b->d_items[k], n * sizeof(lbrd::BatchItem));
+        if (!e) e = cudaMemcpy(b->d_items[k], v.data(), n * sizeof(lbrd::BatchItem), cudaMemcpyHostToDevice);
+    }
+    if (e) {
+        int rc = cuda_err(e, "lb_rd_batch_create allocation");
+        lb_rd_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return LB_RD_OK;
+}
+
+static int batch_stage(lb_rd_batch *b, size_t elems) {
+    if (b->stage_elems >= elems) return LB_RD_OK;
+    if (b->stage) {
+        cudaStreamSynchronize(b->stream);
+        cudaFree(b->stage);
+        b->stage = nullptr;
+        b->stage_elems = 0;
+    }
+    cudaError_t e = cudaMalloc(&b->stage, elems * sizeof(double));
+    if (e) return cuda_err(e, "batch staging allocation");
+    b->stage_elems = elems;
+    return LB_RD_OK;
+}
+
+int lb_rd_batch_init(lb_rd_batch *b, int32_t idx, const double *rho0, int is_device) {
+    if (!b || !rho0) return report_error(LB_RD_EINVAL, "lb_rd_batch_init: batch or rho0 is NULL");
+    if (idx < 0 || idx >= (int)b->cfgs.size()) return report_error(LB_RD_EINVAL, "lb_rd_batch_init: index out of range");
+    if (b->t != 0) return report_error(LB_RD_EINVAL, "lb_rd_batch_init: the batch has already been stepped");
+    const lb_rd_config &c = b->cfgs[idx];
+    const size_t n = (size_t)b->S * c.ny * c.nx;
+    const double *src = rho0;
+    if (!is_device) {
+        int rc = batch_stage(b, n);
+        if (rc) return rc;
+        cudaError_t e = cudaMemcpyAsync(b->stage, rho0, n * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+        if (e) return cuda_err(e, "rho0 upload");
+        src = b->stage;
+    }
+    lbrd::InitArgs a{};
+    a.rho0 = src;
+    a.dst = b->buf[b->cur] + b->state_off[idx];
+    a.nx = c.nx;
+    a.ny = c.ny;
+    a.pitch = b->pitch[idx];
+    a.plane = c.ny * a.pitch;
+    for (int s = 0; s < 2; ++s) a.omega[s] = s < b->S ? 1.0 / c.tau[s] : 0.0;
+    a.rkind = c.reaction.kind;
+    a.kappa = c.reaction.kappa;
+    a.F = c.reaction.F;
+    a.k = c.reaction.k;
+    a.rho_out = b->rho + b->rho_off[idx];
+    cudaError_t e = b->prec == LB_RD_FP32 ? lbrd::launch_init_f32(b->Q, b->S, a, b->stream)
+                                          : lbrd::launch_init_half(b->Q, b->S, b->mode == 2, a, b->stream);
+    if (e) return cuda_err(e, "batch init kernel");
+    b->launches++;
+    if (!is_device) {
+        e = cudaStreamSynchronize(b->stream);
+        if (e) return cuda_err(e, "batch init sync");
+    }
+    b->inited[idx] = true;
+    return LB_RD_OK;
+}
+
+int lb_rd_batch_set_graph(lb_rd_batch *b, int32_t steps_per_graph) {
+    if (!b) return report_error(LB_RD_EINVAL, "batch is NULL");
+    if (steps_per_graph != 0 && (steps_per_graph < 2 || steps_per_graph % 2))
+        return report_error(LB_RD_EINVAL, "steps_per_graph must be 0 or an even number >= 2");
+    cudaStreamSynchronize(b->stream);
+    drop_graphs(b);
+    b->graph_steps = steps_per_graph;
+    return LB_RD_OK;
+}
+
+static int capture_graph(lb_rd_batch *b, int parity) {
+    // A private stream: capturing on the legacy default stream is not allowed.
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e) return cuda_err(e, "graph stream");
+    cudaStream_t saved = b->stream;
+    b->stream = cs;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    for (int k = 0; k < b->graph_steps && !e; ++k) e = launch_one(b, (parity + k) & 1, false);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    b->stream = saved;
+    if (!e) e = e2;
+    if (!e) e = cudaGraphInstantiate(&b->graph[parity], g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e) return cuda_err(e, "graph capture");
+    return LB_RD_OK;
+}
+
+int lb_rd_batch_step(lb_rd_batch *b, int64_t nsteps) {
+    if (!b) return report_error(LB_RD_EINVAL, "batch is NULL");
+    if (nsteps < 0) return report_error(LB_RD_EINVAL, "nsteps must be >= 0");
+    for (size_t i = 0; i < b->inited.size(); ++i)
+        if (!b->inited[i])
+            return report_error(LB_RD_EINVAL, "lb_rd_batch_step: instance " + std::to_string(i) + " not initialised");
+    if (nsteps == 0) return LB_RD_OK;
+    int64_t body = nsteps - 1;  // the last step also writes the densities
+    if (b->graph_steps > 0 && body >= b->graph_steps) {
+        if (!b->graph[b->cur]) {
+            int rc = capture_graph(b, b->cur);
+            if (rc) return rc;
+        }
+        const int64_t reps = body / b->graph_steps;
+        for (int64_t r = 0; r < reps; ++r) {
+            cudaError_t e = cudaGraphLaunch(b->graph[b->cur], b->stream);
+            if (e) return cuda_err(e, "graph launch");
+        }
+        b->launches += reps * b->graph_steps;
+        b->t += reps * b->graph_steps;  // even: the parity is unchanged
+        body -= reps * b->graph_steps;
+    }
+    for (int64_t k = 0; k <= body; ++k) {
+        cudaError_t e = launch_one(b, b->cur, k == body);
+        if (e) return cuda_err(e, "batch step kernel");
+        b->cur ^= 1;
+        b->t++;
+        b->launches++;
+    }
+    return LB_RD_OK;
+}
+
+int lb_rd_batch_moments(lb_rd_batch *b, int32_t idx, double *rho_out, double *mass_out, int is_device) {
+    if (!b) return report_error(LB_RD_EINVAL, "batch is NULL");
+    if (idx < 0 || idx >= (int)b->cfgs.size()) return report_error(LB_RD_EINVAL, "index out of range");
+    const lb_rd_config &c = b->cfgs[idx];
+    const void *rho = b->rho + b->rho_off[idx];
+    const size_t n = (size_t)b->S * c.ny * c.nx;
+    if (rho_out) {
+        double *dst = rho_out;
+        if (!is_device) {
+            int rc = batch_stage(b, n);
+            if (rc) return rc;
+            dst = b->stage;
+        }
+        cudaError_t e = lbrd::launch_rho_export(b->prec, b->S, rho, c.nx, c.ny, b->pitch[idx], dst, b->stream);
+        if (!e && !is_device) e = cudaMemcpyAsync(rho_out, b->stage, n * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+        if (e) return cuda_err(e, "batch rho export");
+        b->launches++;
+    }
+    if (mass_out) {
+        cudaError_t e = lbrd::launch_mass(b->prec, b->S, rho, c.nx, c.ny, b->pitch[idx], b->partials, b->counter,
+                                          b->mass, b->stream);
+        if (!e)
+            e = cudaMemcpyAsync(mass_out, b->mass, b->S * sizeof(double),
+                                is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream);
+        if (e) return cuda_err(e, "batch mass");
+        b->launches++;
+    }
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e) return cuda_err(e, "batch moments sync");
+    return LB_RD_OK;
+}
+
+int lb_rd_batch_get_time(const lb_rd_batch *b, int64_t *t, int64_t *launches) {
+    if (!b) return report_error(LB_RD_EINVAL, "batch is NULL");
+    if (t) *t = b->t;
+    if (launches) *launches = b->launches;
+    return LB_RD_OK;
+}
+
+}  // extern "C"

@@ -7,7 +7,10 @@
 
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "lb_rd.h"
@@ -62,14 +65,39 @@ struct lb_rd_handle {
     double *partials = nullptr;
     unsigned int *counter = nullptr;
     double *mass = nullptr;
+    int *status = nullptr;  // device error word of the step kernels (bounded waits)
     bool mass_fresh = false;
     bool initialized = false;
     int64_t t = 0;
+    int64_t rho_t = -1;  // time the density cache holds (recomputed on demand)
     cudaStream_t stream = nullptr;
     bool timing = false;
     std::vector<cudaEvent_t> events;  // start/stop pairs of timed step kernels
     int64_t launches = 0;
+    int variant = 0;  // launch variant of the step kernel
 };
+
+namespace {
+// Autotuner choices per (device, precision, Q, S, nx, ny).
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int64_t, int64_t>, int> g_tune_cache;
+
+std::tuple<int, int, int, int, int64_t, int64_t> tune_key(const lb_rd_handle *h) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return std::make_tuple(dev, h->prec, h->Q, h->S, h->cfg.nx, h->cfg.ny);
+}
+
+int variant_count(int prec) { return prec == LB_RD_FP32 ? lbrd::kF32VariantCount : 1; }
+
+cudaError_t launch_step(const lb_rd_handle *h, const lbrd::StepArgs &a, int variant) {
+    switch (h->prec) {
+        case LB_RD_FP64: return lbrd::launch_step_f64(h->Q, h->S, a, h->stream);
+        case LB_RD_FP32: return lbrd::launch_step_f32_variant(variant, h->Q, h->S, a, h->stream);
+        default: return lbrd::launch_step_half(h->Q, h->S, h->prec == LB_RD_FP32_FP16DEV, a, h->stream);
+    }
+}
+}  // namespace
 
 extern "C" {
 
@@ -116,6 +144,7 @@ int lb_rd_destroy(lb_rd_handle *h) {
     cudaFree(h->partials);
     cudaFree(h->counter);
     cudaFree(h->mass);
+    cudaFree(h->status);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     delete h;
     return LB_RD_OK;
@@ -154,6 +183,8 @@ int lb_rd_create(const lb_rd_config *cfg, lb_rd_handle **out) {
     if (!err) err = cudaMalloc(&h->partials, parts * sizeof(double));
     if (!err) err = cudaMalloc(&h->counter, sizeof(unsigned int));
     if (!err) err = cudaMalloc(&h->mass, 2 * sizeof(double));
+    if (!err) err = cudaMalloc(&h->status, sizeof(int));
+    if (!err) err = cudaMemset(h->status, 0, sizeof(int));
     if (!err) err = cudaMemset(h->counter, 0, sizeof(unsigned int));
     if (!err) err = cudaMemset(h->buf[0], 0, h->state_bytes);
     if (!err) err = cudaMemset(h->buf[1], 0, h->state_bytes);
@@ -162,6 +193,11 @@ int lb_rd_create(const lb_rd_config *cfg, lb_rd_handle **out) {
         rc = cuda_fail(err, "lb_rd_create allocation");
         lb_rd_destroy(h);
         return rc;
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(tune_key(h));
+        if (it != g_tune_cache.end()) h->variant = it->second;
     }
     *out = h;
     return LB_RD_OK;
@@ -217,8 +253,21 @@ int lb_rd_init(lb_rd_handle *h, const double *rho0, int is_device) {
     h->launches++;
     if (!is_device) LBRD_CUDA(cudaStreamSynchronize(h->stream), "init sync");
     h->t = 0;
+    h->rho_t = 0;
     h->mass_fresh = false;
     h->initialized = true;
+    return LB_RD_OK;
+}
+
+// Make the density cache hold rho(t): after a step the previous copy of the
+// state, f*(t - 1), is still intact and its pull-sum is rho(t).
+static int ensure_rho(lb_rd_handle *h) {
+    if (h->rho_t == h->t) return LB_RD_OK;
+    cudaError_t e = lbrd::launch_pull_rho(h->prec, h->Q, h->S, h->buf[h->cur ^ 1], h->cfg.nx, h->cfg.ny, h->pitch,
+                                          h->rho, h->stream);
+    if (e) return cuda_fail(e, "density kernel");
+    h->launches++;
+    h->rho_t = h->t;
     return LB_RD_OK;
 }
 
@@ -234,11 +283,13 @@ int lb_rd_step(lb_rd_handle *h, int64_t nsteps) {
     fill_common(h, a.omega, &a.rkind, &a.kappa, &a.F, &a.k);
     a.partials = h->partials;
     a.counter = h->counter;
+    a.status = h->status;
     for (int64_t n = 0; n < nsteps; ++n) {
         const bool last = n == nsteps - 1;
         a.src = h->buf[h->cur];
         a.dst = h->buf[h->cur ^ 1];
-        a.rho_out = last ? h->rho : nullptr;
+        (void)last;
+        a.rho_out = nullptr;  // densities are computed on demand (ensure_rho)
         a.mass_out = h->cfg.track_mass ? h->mass : nullptr;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (h->timing) {
@@ -246,12 +297,7 @@ int lb_rd_step(lb_rd_handle *h, int64_t nsteps) {
             LBRD_CUDA(cudaEventCreate(&e1), "event create");
             LBRD_CUDA(cudaEventRecord(e0, h->stream), "event record");
         }
-        cudaError_t e;
-        switch (h->prec) {
-            case LB_RD_FP64: e = lbrd::launch_step_f64(h->Q, h->S, a, h->stream); break;
-            case LB_RD_FP32: e = lbrd::launch_step_f32(h->Q, h->S, a, h->stream); break;
-            default: e = lbrd::launch_step_half(h->Q, h->S, h->prec == LB_RD_FP32_FP16DEV, a, h->stream); break;
-        }
+        cudaError_t e = launch_step(h, a, h->variant);
         if (e) return cuda_fail(e, "step kernel");
         h->launches++;
         if (h->timing) {
@@ -277,6 +323,10 @@ int lb_rd_moments(lb_rd_handle *h, double *rho_out, double *mass_out, int is_dev
     if (!h->initialized) return fail(LB_RD_EINVAL, "lb_rd_init has not been called");
     const int64_t nx = h->cfg.nx, ny = h->cfg.ny;
     const size_t n = (size_t)h->S * ny * nx;
+    if (rho_out || (mass_out && !h->mass_fresh)) {
+        int rc = ensure_rho(h);
+        if (rc) return rc;
+    }
     if (rho_out) {
         double *dst = rho_out;
         if (!is_device) {
@@ -303,7 +353,10 @@ int lb_rd_moments(lb_rd_handle *h, double *rho_out, double *mass_out, int is_dev
                                   is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream),
                   "mass download");
     }
+    int status = 0;
+    LBRD_CUDA(cudaMemcpyAsync(&status, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "status read");
     LBRD_CUDA(cudaStreamSynchronize(h->stream), "moments sync");
+    if (status) return fail(status, "a step kernel gave up a bounded wait; the state is not valid");
     return LB_RD_OK;
 }
 
@@ -347,6 +400,8 @@ int lb_rd_save(lb_rd_handle *h, void *host_buf, size_t bytes) {
     if (rc) return rc;
     if (!host_buf || bytes < need) return fail(LB_RD_EINVAL, "checkpoint buffer too small");
     if (!h->initialized) return fail(LB_RD_EINVAL, "lb_rd_init has not been called");
+    rc = ensure_rho(h);
+    if (rc) return rc;
     CkptHeader hd{};
     std::memcpy(hd.magic, "LBRDCKP1", 8);
     hd.prec = h->prec;
@@ -383,6 +438,7 @@ int lb_rd_restore(lb_rd_handle *h, const void *host_buf, size_t bytes) {
               "restore rho");
     LBRD_CUDA(cudaStreamSynchronize(h->stream), "restore sync");
     h->t = hd.t;
+    h->rho_t = hd.t;
     h->mass_fresh = false;
     h->initialized = true;
     return LB_RD_OK;
@@ -414,6 +470,103 @@ int lb_rd_kernel_time(lb_rd_handle *h, double *total_ms, int64_t *launches) {
 int lb_rd_launch_count(const lb_rd_handle *h, int64_t *launches) {
     if (!h || !launches) return fail(LB_RD_EINVAL, "handle or launches is NULL");
     *launches = h->launches;
+    return LB_RD_OK;
+}
+
+int lb_rd_variant_count(int32_t precision, int32_t *count) {
+    if (!count || precision < LB_RD_FP64 || precision > LB_RD_FP32_FP16DEV)
+        return fail(LB_RD_EINVAL, "bad precision or NULL count");
+    *count = variant_count(precision);
+    return LB_RD_OK;
+}
+
+const char *lb_rd_variant_name(int32_t precision, int32_t variant) {
+    if (precision == LB_RD_FP32 && variant >= 0 && variant < lbrd::kF32VariantCount)
+        return lbrd::kF32Variants[variant].name;
+    if (variant == 0) return precision == LB_RD_FP64 ? "f64_32x4" : "half_64x2";
+    return "";
+}
+
+int lb_rd_set_variant(lb_rd_handle *h, int32_t variant) {
+    if (!h) return fail(LB_RD_EINVAL, "handle is NULL");
+    if (variant == -1) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(tune_key(h));
+        h->variant = it != g_tune_cache.end() ? it->second : 0;
+        return LB_RD_OK;
+    }
+    if (variant < 0 || variant >= variant_count(h->prec))
+        return fail(LB_RD_EINVAL, "variant out of range for this precision");
+    if (h->prec == LB_RD_FP32 && lbrd::kF32Variants[variant].cache == 2 && h->cfg.nx % 4 != 0)
+        return fail(LB_RD_EINVAL, "bulk-copy variants need nx to be a multiple of 4");
+    h->variant = variant;
+    return LB_RD_OK;
+}
+
+int lb_rd_get_variant(const lb_rd_handle *h, int32_t *variant) {
+    if (!h || !variant) return fail(LB_RD_EINVAL, "handle or variant is NULL");
+    *variant = h->variant;
+    return LB_RD_OK;
+}
+
+int lb_rd_autotune(lb_rd_handle *h, int32_t iters, int32_t *best, double *times_ms, int32_t max_times) {
+    if (!h) return fail(LB_RD_EINVAL, "handle is NULL");
+    if (iters < 1) return fail(LB_RD_EINVAL, "iters must be >= 1");
+    if (!h->initialized) return fail(LB_RD_EINVAL, "lb_rd_init has not been called");
+    int rc = ensure_rho(h);  // the tuner overwrites f*(t - 1), from which rho(t) would be recomputed
+    if (rc) return rc;
+    lbrd::StepArgs a{};
+    a.src = h->buf[h->cur];
+    a.dst = h->buf[h->cur ^ 1];  // spare copy: the state is not advanced
+    a.nx = h->cfg.nx;
+    a.ny = h->cfg.ny;
+    a.pitch = h->pitch;
+    a.plane = h->plane;
+    fill_common(h, a.omega, &a.rkind, &a.kappa, &a.F, &a.k);
+    a.status = h->status;
+    cudaEvent_t e0, e1;
+    LBRD_CUDA(cudaEventCreate(&e0), "event create");
+    LBRD_CUDA(cudaEventCreate(&e1), "event create");
+    const int n = variant_count(h->prec);
+    int arg = 0;
+    double best_ms = 0.0;
+    bool any = false;
+    for (int v = 0; v < n; ++v) {
+        cudaError_t e = launch_step(h, a, v);  // warm-up
+        if (e == cudaErrorInvalidValue) {      // variant not applicable to this grid
+            if (times_ms && v < max_times) times_ms[v] = -1.0;
+            continue;
+        }
+        for (int it = 0; it < iters && !e; ++it) {
+            if (it == 0) cudaEventRecord(e0, h->stream);
+            e = launch_step(h, a, v);
+        }
+        if (!e) e = cudaEventRecord(e1, h->stream);
+        if (!e) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (!e) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(e, "autotune launch");
+        }
+        h->launches += iters + 1;
+        const double per = ms / iters;
+        if (times_ms && v < max_times) times_ms[v] = per;
+        if (!any || per < best_ms) {
+            best_ms = per;
+            arg = v;
+            any = true;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->variant = arg;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[tune_key(h)] = arg;
+    }
+    if (best) *best = arg;
     return LB_RD_OK;
 }
 

@@ -123,6 +123,7 @@ struct StepArgs {
     double *partials;   // optional per-block mass partials [nblocks][S]
     unsigned int *counter;  // arrival counter for the last-block finalisation
     double *mass_out;   // optional sum_x rho_s(t + 1), S doubles
+    int *status;        // optional error word: a kernel whose bounded wait gave up writes its status here
 };
 
 // Initialisation: f_i = w_i rho0, then the collision of step 0 at every site,

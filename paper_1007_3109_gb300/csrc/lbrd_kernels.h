@@ -33,6 +33,16 @@ cudaError_t launch_step_f64(int Q, int S, const StepArgs &a, cudaStream_t st);
 cudaError_t launch_init_f64(int Q, int S, const InitArgs &a, cudaStream_t st);
 
 // FP32: four sites per thread, 128-bit loads and stores, shuffle x-shift.
+// Launch variants differ in tile shape, register budget and cache policy.
+struct F32Variant {
+    const char *name;
+    int bx, by, minb, cache;
+};
+extern const F32Variant kF32Variants[];
+extern const int kF32VariantCount;
+cudaError_t launch_step_f32_variant(int v, int Q, int S, const StepArgs &a, cudaStream_t st);
+cudaError_t launch_step_f32_variant_b(int v, int Q, int S, const StepArgs &a, cudaStream_t st, bool per_tile);
+cudaError_t launch_step_f32_bulk(int v, int Q, int S, const StepArgs &a, cudaStream_t st);
 StepShape step_shape_f32(int64_t nx, int64_t ny);
 cudaError_t launch_step_f32(int Q, int S, const StepArgs &a, cudaStream_t st);
 cudaError_t launch_init_f32(int Q, int S, const InitArgs &a, cudaStream_t st);
@@ -65,6 +75,26 @@ cudaError_t launch_rho_export(int prec, int S, const void *rho, int64_t nx, int6
 size_t mass_partials_needed(int64_t nx, int64_t ny);
 cudaError_t launch_mass(int prec, int S, const void *rho, int64_t nx, int64_t ny, int64_t pitch,
                         double *partials, unsigned int *counter, double *mass, cudaStream_t st);
+
+// Batched step: one persistent launch over the combined (instance x tile)
+// work list.  Tiles are 256 x 2 sites (64 x 2 threads, 4 sites each); the
+// instance of global tile t is the last item with tile_begin <= t.
+struct BatchItem {
+    StepArgs a;          // per-instance grid, parameters and buffers
+    int64_t tiles_x;     // tiles per row of tiles, ceil(ceil(nx / 4) / 64)
+    int64_t tile_begin;  // first global tile of this instance
+};
+int64_t batch_tiles_x(int64_t nx);
+int64_t batch_tiles(int64_t nx, int64_t ny);
+// mode: 0 FP32 storage, 1 bf16 deviations, 2 fp16 deviations.
+cudaError_t launch_batch_step(int mode, int Q, int S, const BatchItem *items, int n, int64_t total_tiles,
+                             cudaStream_t st);
+
+// rho(t) from the previous state copy f*(t - 1) into the density cache
+// ([s][y][pitch], double for FP64, float otherwise), bitwise equal to the rho
+// the step kernel computed for time t.
+cudaError_t launch_pull_rho(int prec, int Q, int S, const void *prev_state, int64_t nx, int64_t ny, int64_t pitch,
+                            void *rho, cudaStream_t st);
 
 // Bytes of one copy of the state (distributions only) in a given precision.
 size_t state_plane_bytes(int prec, int Q, int S, int64_t ny, int64_t pitch);

@@ -1,0 +1,19 @@
+// FP32 step: the remaining launch variants (compiled in their own
+// translation unit so that the build runs in parallel).
+#include "step_f32_kernel.cuh"
+
+namespace lbrd {
+
+cudaError_t launch_step_f32_variant_b(int v, int Q, int S, const StepArgs &a, cudaStream_t st, bool per_tile) {
+    switch (v) {
+        case 4: return f32::dispatch_shape<128, 1, 4, 0>(Q, S, a, st, per_tile);
+        case 5: return f32::dispatch_shape<64, 2, 4, 1>(Q, S, a, st, per_tile);
+        case 6: return f32::dispatch_shape<64, 2, 5, 1>(Q, S, a, st, per_tile);
+        case 7: return f32::dispatch_shape<128, 2, 2, 0>(Q, S, a, st, per_tile);
+        case 8: case 9: case 10: case 11: case 12: case 13:
+            return per_tile ? cudaErrorInvalidValue : launch_step_f32_bulk(v - 8, Q, S, a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace lbrd

@@ -1,0 +1,90 @@
+"""Batched simulations: one persistent launch per step over all instances.
+
+Each instance must compute exactly what a single handle with its config
+computes (same tile body, same arithmetic): bitwise.  The phase-diagram sweep
+(1024 instances of 256^2, F in [0.01, 0.08], k in [0.03, 0.07]) runs at full
+size and sampled instances are checked against the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from oracle import Reaction
+from paper_1007_3109_gb300 import binding as B
+from paper_1007_3109_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _configs(precision="fp32"):
+    shapes = [(64, 48), (100, 37), (36, 70), (8, 3), (256, 16)]
+    out = []
+    for j, (nx, ny) in enumerate(shapes):
+        if precision != "fp32" and nx % 4:
+            continue
+        out.append(dict(lattice="D2Q9", nspecies=2, nx=nx, ny=ny, tau=[0.8 + 0.05 * j, 0.65], reaction="gray_scott",
+                        F=0.03 + 0.004 * j, k=0.06 - 0.002 * j, precision=precision))
+    return out
+
+
+def _rho0(c, j):
+    return inputs.rho0_square(c["nx"], c["ny"], seed=50 + j, side=max(2, min(c["nx"], c["ny"]) // 3))
+
+
+def _single(c, rho0, steps):
+    with B.Simulation(**c) as sim:
+        sim.init(rho0).step(steps)
+        return sim.moments()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp32_bf16dev", "fp32_fp16dev"])
+@pytest.mark.parametrize("graph", [0, 8])
+def test_batch_instances_equal_single_handles(precision, graph):
+    cfgs = _configs(precision)
+    steps = 57
+    with B.Batch(cfgs) as b:
+        b.set_graph(graph)
+        for j, c in enumerate(cfgs):
+            b.init(j, _rho0(c, j))
+        b.step(20).step(steps - 20)
+        assert b.time == steps
+        for j, c in enumerate(cfgs):
+            rho, mass = b.moments(j)
+            ref_rho, ref_mass = _single(c, _rho0(c, j), steps)
+            np.testing.assert_array_equal(rho, ref_rho, err_msg=f"instance {j}")
+            np.testing.assert_allclose(mass, ref_mass, rtol=1e-14)
+
+
+def test_batch_rejects_mixed_or_fp64():
+    cfgs = _configs()
+    bad = [dict(cfgs[0]), dict(cfgs[1], lattice="D2Q5")]
+    with pytest.raises(B.LbRdError):
+        B.Batch(bad)
+    with pytest.raises(B.LbRdError):
+        B.Batch([dict(cfgs[0], precision="fp64")])
+    with B.Batch(cfgs[:2]) as b:
+        b.init(0, _rho0(cfgs[0], 0))
+        with pytest.raises(B.LbRdError):
+            b.step(1)  # instance 1 not initialised
+
+
+def test_phase_diagram_sweep_full_size_sampled():
+    """gs_sweep_256 at full size (1024 x 256^2, FP32) in the configuration the
+    batched benchmark times; sampled instances checked against the oracle."""
+    w = inputs.WORKLOADS["gs_sweep_256"]
+    F, k = inputs.sweep_params()
+    taus = [float(t) for t in orc.tau_from_diffusion(np.array(w["D"]))]
+    n, T = w["nx"], 30
+    cfgs = [dict(lattice="D2Q9", nspecies=2, nx=n, ny=n, tau=taus, reaction="gray_scott", F=float(F[i]),
+                 k=float(k[i]), precision="fp32") for i in range(w["instances"])]
+    with B.Batch(cfgs) as b:
+        for i in range(len(cfgs)):
+            b.init(i, inputs.rho0_square(n, n, seed=w["seed"] + i))
+        b.step(T)
+        for i in (0, 517, 1023):
+            rho, _ = b.moments(i)
+            rho0 = inputs.rho0_square(n, n, seed=w["seed"] + i)
+            reac = Reaction("gray_scott", F=float(F[i]), k=float(k[i]))
+            ref = orc.density("D2Q9", orc.run("D2Q9", taus, reac, orc.init("D2Q9", rho0), T))
+            err = np.max(np.abs(rho - ref), axis=(1, 2)) / np.maximum(np.max(np.abs(ref), axis=(1, 2)), 1e-4)
+            assert np.all(err <= 5e-5), (i, err)

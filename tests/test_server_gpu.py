@@ -1,0 +1,117 @@
+"""Serving loop: continuous batching of simulation requests.
+
+Requests that arrive while others run are admitted between ticks as slots and
+memory free up; every result must be bitwise what a single handle with the
+same config computes (the same result alone and in the mix).
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1007_3109_gb300 import binding as B
+from paper_1007_3109_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _request(j, side, scale, steps):
+    D = (0.1 * scale, 0.05 * scale)
+    kw = dict(lattice="D2Q9", nspecies=2, nx=side, ny=side, tau=[3 * D[0] + 0.5, 3 * D[1] + 0.5],
+              reaction="gray_scott", F=0.04, k=0.06, precision="fp32")
+    rho0 = inputs.rho0_square(side, side, seed=300 + j, side=max(2, side // 4))
+    return kw, rho0, steps
+
+
+def _alone(kw, rho0, steps):
+    with B.Simulation(**kw) as sim:
+        sim.init(rho0).step(steps)
+        return sim.moments()
+
+
+def _wait(srv, ticket, S, side, timeout=120.0):
+    rho = np.empty((S, side, side))
+    mass = np.empty(S)
+    t0 = time.time()
+    while True:
+        rc, st = B.lb_rd_poll(srv, ticket, rho, mass)
+        if rc != B.LB_RD_EPENDING:
+            return rc, rho, mass, st
+        assert time.time() - t0 < timeout, "request did not finish"
+        time.sleep(0.002)
+
+
+def test_results_identical_alone_and_in_the_mix():
+    reqs = [_request(0, 64, 1, 150), _request(1, 100, 2, 37), _request(2, 36, 4, 260), _request(3, 128, 1, 64),
+            _request(4, 70, 2, 1), _request(5, 256, 1, 90), _request(6, 12, 1, 500), _request(7, 96, 4, 77)]
+    srv = B.lb_rd_server_create(hbm_budget_bytes=1 << 30, max_slots=5, steps_per_tick=16)
+    try:
+        tickets = []
+        for j, (kw, rho0, steps) in enumerate(reqs):
+            tickets.append(B.lb_rd_submit(srv, B.make_config(**kw), rho0, steps))
+            if j % 3 == 2:
+                time.sleep(0.01)  # later requests arrive while earlier ones run
+        for (kw, rho0, steps), t in zip(reqs, tickets):
+            rc, rho, mass, st = _wait(srv, t, 2, kw["nx"])
+            assert rc == B.LB_RD_OK
+            ref_rho, ref_mass = _alone(kw, rho0, steps)
+            np.testing.assert_array_equal(rho, ref_rho)
+            np.testing.assert_allclose(mass, ref_mass, rtol=1e-14)
+            assert st["arrival_ns"] <= st["start_ns"] <= st["end_ns"] and st["steps"] == steps
+        stats = B.lb_rd_server_stats(srv)
+        assert stats["finished"] == len(reqs)
+        # continuous batching: fewer batched launches than the summed step counts
+        assert stats["launches"] < sum(r[2] for r in reqs)
+        with pytest.raises(B.LbRdError) as ei:
+            B.lb_rd_poll(srv, tickets[0])
+        assert ei.value.status == B.LB_RD_ENOTFOUND
+    finally:
+        B.lb_rd_server_destroy(srv)
+
+
+def test_memory_budget_queues_and_rejects():
+    kw, rho0, _ = _request(10, 128, 1, 40)
+    need = 2 * 2 * 9 * 128 * 128 * 4 + 2 * 128 * 128 * 4
+    srv = B.lb_rd_server_create(hbm_budget_bytes=int(need * 1.5), max_slots=8, steps_per_tick=8)
+    try:
+        # fits only one at a time: the second waits for the first to finish
+        t1 = B.lb_rd_submit(srv, B.make_config(**kw), rho0, 40)
+        t2 = B.lb_rd_submit(srv, B.make_config(**kw), rho0, 40)
+        big_kw, big_rho, _ = _request(11, 512, 1, 5)
+        t3 = B.lb_rd_submit(srv, B.make_config(**big_kw), big_rho, 5)  # larger than the whole budget
+        B.lb_rd_server_drain(srv, 60000)
+        rc1, r1, _, s1 = _wait(srv, t1, 2, 128)
+        rc2, r2, _, s2 = _wait(srv, t2, 2, 128)
+        assert rc1 == rc2 == B.LB_RD_OK
+        np.testing.assert_array_equal(r1, r2)
+        assert s2["start_ns"] >= s1["end_ns"] - 5_000_000  # admitted after the first released its memory
+        rc3, _, _, s3 = _wait(srv, t3, 2, 512)
+        assert rc3 == B.LB_RD_ENOMEM and s3["status"] == B.LB_RD_ENOMEM
+    finally:
+        B.lb_rd_server_destroy(srv)
+
+
+def test_submit_validation():
+    srv = B.lb_rd_server_create(hbm_budget_bytes=1 << 28, max_slots=2, steps_per_tick=4)
+    try:
+        kw, rho0, _ = _request(20, 32, 1, 10)
+        with pytest.raises(B.LbRdError):
+            B.lb_rd_submit(srv, B.make_config(**dict(kw, precision="fp32_bf16dev")), rho0, 10)
+        with pytest.raises(B.LbRdError):
+            B.lb_rd_submit(srv, B.make_config(**kw), rho0, 0)
+        with pytest.raises(B.LbRdError):
+            B.lb_rd_submit(srv, B.make_config(**dict(kw, tau=[0.5, 0.6])), rho0, 10)
+        t = B.lb_rd_submit(srv, B.make_config(**kw), rho0, 10)
+        rc, _, _, _ = _wait(srv, t, 2, 32)
+        assert rc == B.LB_RD_OK
+    finally:
+        B.lb_rd_server_destroy(srv)
+
+
+def test_destroy_with_requests_in_flight():
+    srv = B.lb_rd_server_create(hbm_budget_bytes=1 << 30, max_slots=4, steps_per_tick=4)
+    kw, rho0, _ = _request(30, 256, 1, 10)
+    for _ in range(6):
+        B.lb_rd_submit(srv, B.make_config(**kw), rho0, 2000)
+    time.sleep(0.05)
+    B.lb_rd_server_destroy(srv)  # must not hang or fault

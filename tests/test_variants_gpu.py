@@ -1,0 +1,66 @@
+"""Launch variants and the autotuner.
+
+Every FP32 launch variant (tile shape, register budget, cache policy, TMA
+bulk-copy staging) performs the same per-site operations in the same order,
+so their states must agree bit for bit; the autotuner must not advance or
+change the simulation state.
+"""
+import numpy as np
+import pytest
+
+from paper_1007_3109_gb300 import binding as B
+from paper_1007_3109_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+GRIDS = [("D2Q9", 2, 64, 48, "gray_scott"), ("D2Q9", 2, 1000, 50, "gray_scott"), ("D2Q5", 2, 1024, 20, "gray_scott"),
+         ("D2Q9", 1, 8, 3, "linear"), ("D2Q9", 2, 70, 37, "gray_scott"), ("D2Q9", 2, 4, 5, "gray_scott")]
+
+
+def _run(lat, S, nx, ny, reac, variant, steps=25):
+    rho0 = inputs.rho0_square(nx, ny, seed=41, side=max(2, min(nx, ny) // 3))[:S] if S == 2 else \
+        inputs.rho0_cosine(nx, ny, seed=41, noise=1e-3)
+    kw = dict(F=0.04, k=0.06) if reac == "gray_scott" else dict(kappa=0.01)
+    with B.Simulation(lat, S, nx, ny, [0.8, 0.65][:S], reac, precision="fp32", track_mass=True, **kw) as sim:
+        sim.set_variant(variant)
+        sim.init(rho0).step(steps)
+        rho, mass = sim.moments()
+        f = sim.distributions()
+    return rho, mass, f
+
+
+@pytest.mark.parametrize("grid", GRIDS, ids=lambda g: f"{g[0]}-S{g[1]}-{g[2]}x{g[3]}")
+def test_every_fp32_variant_is_bitwise_identical(grid):
+    lat, S, nx, ny, reac = grid
+    ref = _run(lat, S, nx, ny, reac, 0)
+    for v in range(1, B.lb_rd_variant_count("fp32")):
+        name = B.lb_rd_variant_name("fp32", v)
+        if name.startswith("bulk") and nx % 4:
+            with pytest.raises(B.LbRdError):
+                _run(lat, S, nx, ny, reac, v)
+            continue
+        rho, mass, f = _run(lat, S, nx, ny, reac, v)
+        np.testing.assert_array_equal(rho, ref[0], err_msg=name)
+        np.testing.assert_array_equal(f, ref[2], err_msg=name)
+        # the fused mass adds FP32 per-tile partials in FP64: variants group them differently
+        np.testing.assert_allclose(mass, ref[1], rtol=1e-6, err_msg=name)
+
+
+def test_autotune_leaves_the_state_unchanged():
+    nx, ny = 512, 256
+    rho0 = inputs.rho0_square(nx, ny, seed=42)
+    kw = dict(lattice="D2Q9", nspecies=2, nx=nx, ny=ny, tau=[0.8, 0.65], reaction="gray_scott", F=0.04, k=0.06,
+              precision="fp32")
+    with B.Simulation(**kw) as a, B.Simulation(**kw) as b:
+        a.init(rho0).step(10)
+        before = a.moments()[0]
+        best, times = a.autotune(iters=3)
+        assert a.time == 10
+        np.testing.assert_array_equal(a.moments()[0], before)
+        n = B.lb_rd_variant_count("fp32")
+        assert 0 <= best < n and times[best] > 0
+        assert all(times[v] > 0 or times[v] == -1.0 for v in range(n))
+        assert B.lb_rd_get_variant(a.h) == best
+        a.step(20)
+        b.init(rho0).step(30)
+        np.testing.assert_array_equal(a.moments()[0], b.moments()[0])
