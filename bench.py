@@ -115,6 +115,19 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
 
 
+def reduce_over_ranks(ms: float, work: float, dist=None, device="cpu"):
+    """Replicas: the job's time is the slowest rank's, its work the sum over
+    ranks.  Returns (max ms, total work); without a process group, the inputs."""
+    if dist is None or not dist.is_initialized():
+        return ms, work
+    import torch
+    t_ms = torch.tensor([ms], dtype=torch.float64, device=device)
+    t_w = torch.tensor([work], dtype=torch.float64, device=device)
+    dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t_w, op=dist.ReduceOp.SUM)
+    return float(t_ms.item()), float(t_w.item())
+
+
 def workload_params(name: str, lattice: str, tau_from_diffusion):
     w = inputs.WORKLOADS[name]
     return w, [float(tau_from_diffusion(D)) for D in w["D"]]
@@ -374,15 +387,19 @@ def main():
                        track_mass=True, stream=stream.cuda_stream)
     rho0_dev = torch.from_numpy(rho0).cuda()
     sim.init(rho0_dev)
-    sim.step(args.warmup)
-    # project autotuner: every launch variant timed on this state (not advanced)
-    best, times = B.lb_rd_autotune(sim.h, iters=args.tune_iters)
     nvar = B.lb_rd_variant_count(args.precision)
     names = [B.lb_rd_variant_name(args.precision, v) for v in range(nvar)]
-    tuning = {names[v]: (round(times[v], 4) if times[v] >= 0 else None) for v in range(nvar)}
     if args.variant:
-        best = names.index(args.variant)
-        B.lb_rd_set_variant(sim.h, best)
+        B.lb_rd_set_variant(sim.h, names.index(args.variant))
+    sim.step(args.warmup)
+    tuning = {}
+    if args.tune_iters > 0:
+        # project autotuner: every launch variant timed on this state (not advanced)
+        best, times = B.lb_rd_autotune(sim.h, iters=args.tune_iters)
+        tuning = {names[v]: (round(times[v], 4) if times[v] >= 0 else None) for v in range(nvar)}
+    if args.variant:
+        B.lb_rd_set_variant(sim.h, names.index(args.variant))
+    best = B.lb_rd_get_variant(sim.h)
     sim.step(3)
     barrier()
 
@@ -393,39 +410,46 @@ def main():
     with ClockSampler(local) as clocks:
         barrier()
         ev0.record(stream)
-        for _ in range(args.steps):
-            sim.step(1)
+        B.lb_rd_step(sim.h, args.steps)
         ev1.record(stream)
         barrier()
     launches = B.lb_rd_launch_count(sim.h) - launches0
     ms_total = ev0.elapsed_time(ev1)
     kernel_ms, kernel_launches = ms_total, launches  # the region holds only step launches
-    t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_total = float(t.item())
-    mass = sim.mass()
-    assert np.all(np.isfinite(mass)), "non-finite mass"
-
+    steps_per_launch = args.steps / max(launches, 1)
     sites = n * n
     ssu_per_step = 2 * sites
-    value = ssu_per_step * args.steps * world / (ms_total / 1e3) / 1e6
+    ms_total, work = reduce_over_ranks(ms_total, float(ssu_per_step * args.steps), dist, "cuda")
+    mass = sim.mass()
+    assert np.all(np.isfinite(mass)), "non-finite mass"
+    value = work / (ms_total / 1e3) / 1e6
 
     # -- roofline of the step kernel ---------------------------------------------
     peak, peak_kind = measured_peaks()
     bps = BYTES_PER_SITE[(args.lattice, args.precision, 2)]
     avg_launch_s = kernel_ms / 1e3 / max(kernel_launches, 1)
+    # Algorithmic bytes of one launch: one read and one write of the state.  A
+    # two-step (temporal blocking) launch moves the state once for two steps,
+    # so its per-launch figure is HBM use and the per-step figure exceeds it.
     achieved = bps * sites / avg_launch_s / 1e9
+    effective = bps * sites * args.steps / (ms_total / 1e3) / 1e9
+    variant_name = B.lb_rd_variant_name(args.precision, best)
     traffic = None
-    kernel_file = {"fp32": "step_f32.cu", "fp64": "step_f64.cu"}.get(args.precision, "step_half.cu")
     if os.path.exists(TRAFFIC_FILE):
         with open(TRAFFIC_FILE) as fh:
             tr = json.load(fh)
-        key = f"{args.workload}/{args.lattice}/{args.precision}"
-        ent = tr.get(key)
-        src = os.path.join(ROOT, "paper_1007_3109_gb300", "csrc", kernel_file)
-        if ent and ent.get("src_sha") == _src_hash(src):
+        ent = tr.get(f"{args.workload}/{args.lattice}/{args.precision}/{variant_name}")
+        if ent and ent.get("n") == n and ent.get("src_sha") == _src_hash(
+                os.path.join(ROOT, "paper_1007_3109_gb300", "csrc", ent["src"])):
             traffic = ent["bytes_per_launch"]
+    single = None
+    if tuning:
+        ones = {k: v for k, v in tuning.items() if v and not k.startswith("tb2")}
+        if ones:
+            k1 = min(ones, key=ones.get)
+            gbs = bps * sites / (ones[k1] / 1e3) / 1e9
+            single = {"variant": k1, "ms_per_step": ones[k1], "GBs": gbs, "frac": gbs / peak,
+                      "source": "autotuner, CUDA events"}
 
     # -- end to end through the C ABI with host buffers --------------------------
     del rho0_dev
@@ -452,13 +476,16 @@ def main():
         "dtype": {"fp32": "f32", "fp64": "f64", "fp32_bf16dev": "f32+bf16", "fp32_fp16dev": "f32+f16"}[args.precision],
         "data": "synthetic",
         "config": {"workload": args.workload, "lattice": args.lattice, "nx": n, "ny": n, "species": 2,
-                   "precision": args.precision, "lb_steps_per_step": 1, "mass_diagnostic": "fused, every step",
+                   "precision": args.precision, "lb_steps_per_step": 1,
+                   "mass_diagnostic": "fused into every launch (every step, or every second step with temporal blocking)",
                    "l2": f"no flush: state of {2 * sim_state_bytes(args.lattice, args.precision, n) / 1e9:.2f} GB >> 129 MB L2",
                    "parallelism": f"replicas x{world}",
                    "variant": B.lb_rd_variant_name(args.precision, best), "autotune_ms_per_launch": tuning},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": f"step_{args.precision}:{B.lb_rd_variant_name(args.precision, best)}", "bytes_per_site": bps,
-                     "peak_kind": peak_kind, "avg_launch_ms": avg_launch_s * 1e3},
+                     "traffic": traffic, "kernel": f"step_{args.precision}:{variant_name}",
+                     "steps_per_launch": steps_per_launch, "bytes_per_site_per_launch": bps,
+                     "effective_per_step_GBs": effective, "effective_frac": effective / peak,
+                     "peak_kind": peak_kind, "avg_launch_ms": avg_launch_s * 1e3, "single_step": single},
         "e2e": {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "lb_steps": e2e_steps, "path": "lb_rd_init(host) + lb_rd_step + lb_rd_moments(host)"},
         "gpu_launches": int(launches),

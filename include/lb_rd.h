@@ -182,21 +182,37 @@ LB_RD_API int lb_rd_kernel_time(lb_rd_handle *h, double *total_ms, int64_t *laun
 LB_RD_API int lb_rd_launch_count(const lb_rd_handle *h, int64_t *launches);
 
 /* Launch variants and the autotuner.  The step kernel of a precision comes in
- * several launch variants (tile shape, register budget, cache policy; see
- * lb_rd_variant_name).  lb_rd_autotune times every variant on the handle's own
- * state -- reading the current state and writing the spare copy, so the
- * simulation is unchanged -- with one warm-up launch and `iters` timed
- * launches each, selects the fastest for this handle and caches the choice per
- * (device, precision, lattice, species, nx, ny); handles created later with
- * the same shape start from the cached choice.  times_ms (may be NULL)
- * receives the mean time per launch of each variant, at most max_times
- * entries.  Synchronises.  lb_rd_set_variant forces a variant (-1: cached or
- * default). */
+ * several launch variants (tile shape, register budget, cache policy, TMA
+ * bulk-copy staging, temporal blocking of two steps per launch; see
+ * lb_rd_variant_name).  lb_rd_autotune times every variant that fits the grid
+ * on the handle's own state -- reading the current state and writing the
+ * spare copy, so the simulation is unchanged -- with one warm-up launch and
+ * `iters` timed launches each, and selects the fastest single-step variant
+ * and, if faster per step, a two-step variant; the choice is cached per
+ * (device, precision, lattice, species, nx, ny) and handles created later with
+ * the same shape start from it.  With a two-step variant lb_rd_step advances
+ * two steps per launch except for the last one or two steps.  times_ms (may
+ * be NULL) receives the mean time per time step of each variant (-1 for a
+ * variant that does not fit), at most max_times entries; *best the variant
+ * used for the bulk of the steps.  Synchronises.  lb_rd_set_variant forces a
+ * variant (a two-step one is used together with the current single-step
+ * variant; -1 restores the cached or default choice); lb_rd_get_variant
+ * returns the variant used for the bulk of the steps. */
 LB_RD_API int lb_rd_variant_count(int32_t precision, int32_t *count);
 LB_RD_API const char *lb_rd_variant_name(int32_t precision, int32_t variant);
 LB_RD_API int lb_rd_autotune(lb_rd_handle *h, int32_t iters, int32_t *best, double *times_ms, int32_t max_times);
 LB_RD_API int lb_rd_set_variant(lb_rd_handle *h, int32_t variant);
 LB_RD_API int lb_rd_get_variant(const lb_rd_handle *h, int32_t *variant);
+
+/* Test switch for the error path of the bounded device-side waits (not part
+ * of the method).  When enabled, the next step launch of a TMA-staged variant
+ * (bulk-copy or two-step) makes block 0 wait for 16 bytes that are never
+ * copied; the wait gives up after about one second, the kernel records
+ * LB_RD_ETIMEOUT in the handle's status word, waits (bounded) for its copies
+ * in flight and returns.  The next lb_rd_moments returns LB_RD_ETIMEOUT; the
+ * state is then invalid until lb_rd_init, which clears the status.  Nothing
+ * faults, traps or hangs: the CUDA context stays usable.  One-shot. */
+LB_RD_API int lb_rd_debug_inject_wait_timeout(lb_rd_handle *h, int32_t enable);
 
 /* ---- Batched simulations ------------------------------------------------
  * n independent simulations advanced together, e.g. a phase-diagram sweep of

@@ -72,6 +72,7 @@ _SIGNATURES = {
     "lb_rd_autotune": ([c_void_p, c_int32, POINTER(c_int32), POINTER(c_double), c_int32], c_int),
     "lb_rd_set_variant": ([c_void_p, c_int32], c_int),
     "lb_rd_get_variant": ([c_void_p, POINTER(c_int32)], c_int),
+    "lb_rd_debug_inject_wait_timeout": ([c_void_p, c_int32], c_int),
     "lb_rd_batch_create": ([POINTER(lb_rd_config), c_int32, POINTER(c_void_p)], c_int),
     "lb_rd_batch_destroy": ([c_void_p], c_int),
     "lb_rd_batch_init": ([c_void_p, c_int32, c_void_p, c_int], c_int),
@@ -258,6 +259,10 @@ def lb_rd_autotune(h: int, iters: int = 20, max_times: int = 64):
 
 def lb_rd_set_variant(h: int, variant: int):
     _check(lib().lb_rd_set_variant(h, int(variant)))
+
+
+def lb_rd_debug_inject_wait_timeout(h: int, enable: bool = True):
+    _check(lib().lb_rd_debug_inject_wait_timeout(h, 1 if enable else 0))
 
 
 def lb_rd_get_variant(h: int) -> int:

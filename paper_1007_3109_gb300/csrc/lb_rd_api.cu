@@ -74,13 +74,16 @@ struct lb_rd_handle {
     bool timing = false;
     std::vector<cudaEvent_t> events;  // start/stop pairs of timed step kernels
     int64_t launches = 0;
-    int variant = 0;  // launch variant of the step kernel
+    int inject_timeout = 0;  // one-shot test switch for the bounded-wait error path
+    int variant = 0;      // single-step launch variant of the step kernel
+    int tb_variant = -1;  // two-step (temporal blocking) variant, or -1
 };
 
 namespace {
-// Autotuner choices per (device, precision, Q, S, nx, ny).
+// Autotuner choices per (device, precision, Q, S, nx, ny): single-step
+// variant and two-step variant (-1 if none is faster).
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int64_t, int64_t>, int> g_tune_cache;
+std::map<std::tuple<int, int, int, int, int64_t, int64_t>, std::pair<int, int>> g_tune_cache;
 
 std::tuple<int, int, int, int, int64_t, int64_t> tune_key(const lb_rd_handle *h) {
     int dev = 0;
@@ -89,6 +92,12 @@ std::tuple<int, int, int, int, int64_t, int64_t> tune_key(const lb_rd_handle *h)
 }
 
 int variant_count(int prec) { return prec == LB_RD_FP32 ? lbrd::kF32VariantCount : 1; }
+
+int variant_steps(int prec, int v) { return prec == LB_RD_FP32 ? lbrd::kF32Variants[v].steps : 1; }
+
+bool variant_fits(const lb_rd_handle *h, int v) {
+    return h->prec != LB_RD_FP32 || h->cfg.nx % lbrd::kF32Variants[v].nx_multiple == 0;
+}
 
 cudaError_t launch_step(const lb_rd_handle *h, const lbrd::StepArgs &a, int variant) {
     switch (h->prec) {
@@ -197,7 +206,10 @@ int lb_rd_create(const lb_rd_config *cfg, lb_rd_handle **out) {
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(tune_key(h));
-        if (it != g_tune_cache.end()) h->variant = it->second;
+        if (it != g_tune_cache.end()) {
+            h->variant = it->second.first;
+            h->tb_variant = it->second.second;
+        }
     }
     *out = h;
     return LB_RD_OK;
@@ -234,6 +246,7 @@ int lb_rd_init(lb_rd_handle *h, const double *rho0, int is_device) {
         LBRD_CUDA(cudaMemcpyAsync(h->stage, rho0, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "rho0 upload");
         src = h->stage;
     }
+    LBRD_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream), "status reset");
     lbrd::InitArgs a{};
     a.rho0 = src;
     a.dst = h->buf[h->cur];
@@ -284,11 +297,14 @@ int lb_rd_step(lb_rd_handle *h, int64_t nsteps) {
     a.partials = h->partials;
     a.counter = h->counter;
     a.status = h->status;
-    for (int64_t n = 0; n < nsteps; ++n) {
-        const bool last = n == nsteps - 1;
+    // With a two-step variant, all but the last one or two steps go two at a
+    // time; the last launch is always a single step, so that the other state
+    // copy holds f*(t - 1) and rho(t) can be recomputed from it on demand.
+    const int64_t n_two = h->tb_variant >= 0 ? (nsteps - 1) / 2 : 0;
+    for (int64_t n = 0; n < n_two + (nsteps - 2 * n_two); ++n) {
+        const bool two = n < n_two;
         a.src = h->buf[h->cur];
         a.dst = h->buf[h->cur ^ 1];
-        (void)last;
         a.rho_out = nullptr;  // densities are computed on demand (ensure_rho)
         a.mass_out = h->cfg.track_mass ? h->mass : nullptr;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -297,7 +313,9 @@ int lb_rd_step(lb_rd_handle *h, int64_t nsteps) {
             LBRD_CUDA(cudaEventCreate(&e1), "event create");
             LBRD_CUDA(cudaEventRecord(e0, h->stream), "event record");
         }
-        cudaError_t e = launch_step(h, a, h->variant);
+        a.inject_timeout = h->inject_timeout;
+        h->inject_timeout = 0;
+        cudaError_t e = launch_step(h, a, two ? h->tb_variant : h->variant);
         if (e) return cuda_fail(e, "step kernel");
         h->launches++;
         if (h->timing) {
@@ -306,7 +324,7 @@ int lb_rd_step(lb_rd_handle *h, int64_t nsteps) {
             h->events.push_back(e1);
         }
         h->cur ^= 1;
-        h->t++;
+        h->t += two ? 2 : 1;
     }
     if (nsteps > 0) h->mass_fresh = h->cfg.track_mass != 0;
     return LB_RD_OK;
@@ -473,6 +491,12 @@ int lb_rd_launch_count(const lb_rd_handle *h, int64_t *launches) {
     return LB_RD_OK;
 }
 
+int lb_rd_debug_inject_wait_timeout(lb_rd_handle *h, int32_t enable) {
+    if (!h) return fail(LB_RD_EINVAL, "handle is NULL");
+    h->inject_timeout = enable ? 1 : 0;
+    return LB_RD_OK;
+}
+
 int lb_rd_variant_count(int32_t precision, int32_t *count) {
     if (!count || precision < LB_RD_FP64 || precision > LB_RD_FP32_FP16DEV)
         return fail(LB_RD_EINVAL, "bad precision or NULL count");
@@ -492,20 +516,27 @@ int lb_rd_set_variant(lb_rd_handle *h, int32_t variant) {
     if (variant == -1) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(tune_key(h));
-        h->variant = it != g_tune_cache.end() ? it->second : 0;
+        h->variant = it != g_tune_cache.end() ? it->second.first : 0;
+        h->tb_variant = it != g_tune_cache.end() ? it->second.second : -1;
         return LB_RD_OK;
     }
     if (variant < 0 || variant >= variant_count(h->prec))
         return fail(LB_RD_EINVAL, "variant out of range for this precision");
-    if (h->prec == LB_RD_FP32 && lbrd::kF32Variants[variant].cache == 2 && h->cfg.nx % 4 != 0)
-        return fail(LB_RD_EINVAL, "bulk-copy variants need nx to be a multiple of 4");
-    h->variant = variant;
+    if (!variant_fits(h, variant))
+        return fail(LB_RD_EINVAL, std::string("variant ") + lb_rd_variant_name(h->prec, variant) + " needs nx to be a multiple of " +
+                                      std::to_string(lbrd::kF32Variants[variant].nx_multiple));
+    if (variant_steps(h->prec, variant) == 2) {
+        h->tb_variant = variant;
+    } else {
+        h->variant = variant;
+        h->tb_variant = -1;
+    }
     return LB_RD_OK;
 }
 
 int lb_rd_get_variant(const lb_rd_handle *h, int32_t *variant) {
     if (!h || !variant) return fail(LB_RD_EINVAL, "handle or variant is NULL");
-    *variant = h->variant;
+    *variant = h->tb_variant >= 0 ? h->tb_variant : h->variant;
     return LB_RD_OK;
 }
 
@@ -528,15 +559,14 @@ int lb_rd_autotune(lb_rd_handle *h, int32_t iters, int32_t *best, double *times_
     LBRD_CUDA(cudaEventCreate(&e0), "event create");
     LBRD_CUDA(cudaEventCreate(&e1), "event create");
     const int n = variant_count(h->prec);
-    int arg = 0;
-    double best_ms = 0.0;
-    bool any = false;
+    int best1 = -1, best2 = -1;
+    double ms1 = 0.0, ms2 = 0.0;
     for (int v = 0; v < n; ++v) {
-        cudaError_t e = launch_step(h, a, v);  // warm-up
-        if (e == cudaErrorInvalidValue) {      // variant not applicable to this grid
+        if (!variant_fits(h, v)) {  // variant not applicable to this grid
             if (times_ms && v < max_times) times_ms[v] = -1.0;
             continue;
         }
+        cudaError_t e = launch_step(h, a, v);  // warm-up
         for (int it = 0; it < iters && !e; ++it) {
             if (it == 0) cudaEventRecord(e0, h->stream);
             e = launch_step(h, a, v);
@@ -551,20 +581,26 @@ int lb_rd_autotune(lb_rd_handle *h, int32_t iters, int32_t *best, double *times_
             return cuda_fail(e, "autotune launch");
         }
         h->launches += iters + 1;
-        const double per = ms / iters;
+        const int steps = variant_steps(h->prec, v);
+        const double per = ms / iters / steps;  // per time step
         if (times_ms && v < max_times) times_ms[v] = per;
-        if (!any || per < best_ms) {
-            best_ms = per;
-            arg = v;
-            any = true;
+        if (steps == 1 && (best1 < 0 || per < ms1)) {
+            best1 = v;
+            ms1 = per;
+        }
+        if (steps == 2 && (best2 < 0 || per < ms2)) {
+            best2 = v;
+            ms2 = per;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    h->variant = arg;
+    h->variant = best1 >= 0 ? best1 : 0;
+    h->tb_variant = (best2 >= 0 && ms2 < ms1) ? best2 : -1;
+    const int arg = h->tb_variant >= 0 ? h->tb_variant : h->variant;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tune_cache[tune_key(h)] = arg;
+        g_tune_cache[tune_key(h)] = std::make_pair(h->variant, h->tb_variant);
     }
     if (best) *best = arg;
     return LB_RD_OK;

@@ -124,6 +124,7 @@ struct StepArgs {
     unsigned int *counter;  // arrival counter for the last-block finalisation
     double *mass_out;   // optional sum_x rho_s(t + 1), S doubles
     int *status;        // optional error word: a kernel whose bounded wait gave up writes its status here
+    int inject_timeout; // test switch: block 0's first stage waits for 16 bytes that never come
 };
 
 // Initialisation: f_i = w_i rho0, then the collision of step 0 at every site,

@@ -40,12 +40,28 @@ __global__ void __launch_bounds__(256) init_f32_kernel(InitArgs a) {
 
 // Variant table: {threads along x, rows per tile, min blocks per SM, cache policy}.
 const F32Variant kF32Variants[] = {
-    {"64x2_minb4", 64, 2, 4, 0},         {"64x2_minb5", 64, 2, 5, 0}, {"64x2_minb2", 64, 2, 2, 0},
-    {"32x4_minb4", 32, 4, 4, 0},         {"128x1_minb4", 128, 1, 4, 0}, {"64x2_minb4_stream", 64, 2, 4, 1},
-    {"64x2_minb5_stream", 64, 2, 5, 1}, {"128x2_minb2", 128, 2, 2, 0},
+    {"64x2_minb4", 64, 2, 4, 0, 1, 1},
+    {"64x2_minb5", 64, 2, 5, 0, 1, 1},
+    {"64x2_minb2", 64, 2, 2, 0, 1, 1},
+    {"32x4_minb4", 32, 4, 4, 0, 1, 1},
+    {"128x1_minb4", 128, 1, 4, 0, 1, 1},
+    {"64x2_minb4_stream", 64, 2, 4, 1, 1, 1},
+    {"64x2_minb5_stream", 64, 2, 5, 1, 1, 1},
+    {"128x2_minb2", 128, 2, 2, 0, 1, 1},
     // TMA bulk copies into a shared-memory ring (step_f32_bulk.cu): threads, stages
-    {"bulk128_s4", 128, 1, 4, 2},        {"bulk64_s4", 64, 1, 4, 2},   {"bulk128_s3", 128, 1, 3, 2},
-    {"bulk256_s2", 256, 1, 2, 2},        {"bulk256_s3", 256, 1, 3, 2}, {"bulk128_s2", 128, 1, 2, 2},
+    {"bulk128_s4", 128, 1, 4, 2, 1, 4},
+    {"bulk64_s4", 64, 1, 4, 2, 1, 4},
+    {"bulk128_s3", 128, 1, 3, 2, 1, 4},
+    {"bulk256_s2", 256, 1, 2, 2, 1, 4},
+    {"bulk256_s3", 256, 1, 3, 2, 1, 4},
+    {"bulk128_s2", 128, 1, 2, 2, 1, 4},
+    // temporal blocking, two steps per launch (step_f32_tb.cu): threads, strip width, stages
+    {"tb2_288x128_s8", 288, 128, 8, 3, 2, 128},
+    {"tb2_288x128_s4x2", 288, 128, 4, 3, 2, 128},
+    {"tb2_288x256_s6", 288, 256, 6, 3, 2, 256},
+    {"tb2_352x512_s2", 352, 512, 2, 3, 2, 512},
+    {"tb2_288x256_s2x2", 288, 256, 2, 3, 2, 256},
+    {"tb2_544x512_s2", 544, 512, 2, 3, 2, 512},
 };
 const int kF32VariantCount = sizeof(kF32Variants) / sizeof(kF32Variants[0]);
 

@@ -73,49 +73,53 @@ struct BulkGeom {
     static constexpr int kStageFloats = S * Q * kSlot;  // floats per stage
 };
 
-// Issue the copies of unit u into stage buffer `st` (called by one thread).
+// Issue the copies of unit u into stage buffer `st`.  Called by all 32 lanes
+// of one warp: lane 0 posts the expected bytes, lane p < S * Q issues plane
+// p's copies (a negative transaction count before the arrival is allowed).
 template <int Q, int S, int NT>
-__device__ __forceinline__ void issue_unit(const StepArgs &a, int64_t u, int64_t nstrips, float *st, unsigned bar) {
+__device__ __forceinline__ void issue_unit(const StepArgs &a, int64_t u, int64_t nstrips, float *st, unsigned bar,
+                                           unsigned extra_tx = 0) {
     using L = Lattice<Q>;
     using G = BulkGeom<Q, S, NT>;
+    const int lane = threadIdx.x & 31;
     const int64_t y = u / nstrips;
     const int64_t x0 = (u - y * nstrips) * G::TX;
     const int64_t xe = x0 + G::TX < a.nx ? x0 + G::TX : a.nx;
     const float *src = static_cast<const float *>(a.src);
-    // total bytes first (expect_tx must precede or match the copies)
-    unsigned total = 0;
+    if (lane == 0) {
+        unsigned total = 0;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int ex = L::ex(i);
-        total += (unsigned)((xe - x0) + (ex != 0 ? 4 : 0)) * 4u;
+        for (int i = 0; i < Q; ++i) total += (unsigned)((xe - x0) + (L::ex(i) != 0 ? 4 : 0)) * 4u;
+        mbar_expect_tx(bar, total * S + extra_tx);
     }
-    total *= S;
-    mbar_expect_tx(bar, total);
+    __syncwarp();
+    if (lane >= S * Q) return;
+    const int s = lane / Q, i = lane - s * Q;
+    int ex = 0, ey = 0;
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int ex = L::ex(i), ey = L::ey(i);
-            const int64_t yr = wrap(y - ey, a.ny);
-            const float *row = src + (int64_t)(s * Q + i) * a.plane + yr * a.pitch;
-            float *slot = st + (s * Q + i) * G::kSlot;
-            if (ex == 0) {
-                bulk_copy(smem_u32(slot + 4), row + x0, (unsigned)(xe - x0) * 4u, bar);
-            } else if (ex == 1) {
-                if (x0 == 0) {
-                    bulk_copy(smem_u32(slot), row + a.nx - 4, 16u, bar);
-                    bulk_copy(smem_u32(slot + 4), row, (unsigned)xe * 4u, bar);
-                } else {
-                    bulk_copy(smem_u32(slot), row + x0 - 4, (unsigned)(xe - x0 + 4) * 4u, bar);
-                }
-            } else {
-                if (xe == a.nx) {
-                    bulk_copy(smem_u32(slot + 4), row + x0, (unsigned)(xe - x0) * 4u, bar);
-                    bulk_copy(smem_u32(slot + 4 + (xe - x0)), row, 16u, bar);
-                } else {
-                    bulk_copy(smem_u32(slot + 4), row + x0, (unsigned)(xe - x0 + 4) * 4u, bar);
-                }
-            }
+    for (int q = 0; q < Q; ++q)
+        if (q == i) {
+            ex = L::ex(q);
+            ey = L::ey(q);
+        }
+    const int64_t yr = wrap(y - ey, a.ny);
+    const float *row = src + (int64_t)(s * Q + i) * a.plane + yr * a.pitch;
+    float *slot = st + (s * Q + i) * G::kSlot;
+    if (ex == 0) {
+        bulk_copy(smem_u32(slot + 4), row + x0, (unsigned)(xe - x0) * 4u, bar);
+    } else if (ex == 1) {
+        if (x0 == 0) {
+            bulk_copy(smem_u32(slot), row + a.nx - 4, 16u, bar);
+            bulk_copy(smem_u32(slot + 4), row, (unsigned)xe * 4u, bar);
+        } else {
+            bulk_copy(smem_u32(slot), row + x0 - 4, (unsigned)(xe - x0 + 4) * 4u, bar);
+        }
+    } else {
+        if (xe == a.nx) {
+            bulk_copy(smem_u32(slot + 4), row + x0, (unsigned)(xe - x0) * 4u, bar);
+            bulk_copy(smem_u32(slot + 4 + (xe - x0)), row, 16u, bar);
+        } else {
+            bulk_copy(smem_u32(slot + 4), row + x0, (unsigned)(xe - x0 + 4) * 4u, bar);
         }
     }
 }
@@ -139,10 +143,10 @@ __global__ void __launch_bounds__(NT, 1) step_bulk_kernel(StepArgs a, int64_t ns
 
     // units of this block: u_j = blockIdx.x + j * gridDim.x
     const int64_t nmine = blockIdx.x < nunits ? (nunits - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    if (tid == 0) {
+    if (tid < 32) {
         for (int k = 0; k < STAGES && k < nmine; ++k)
             issue_unit<Q, S, NT>(a, blockIdx.x + (int64_t)k * gridDim.x, nstrips, smem + k * G::kStageFloats,
-                                 smem_u32(&bars[k]));
+                                 smem_u32(&bars[k]), (a.inject_timeout && blockIdx.x == 0 && k == 0) ? 16u : 0u);
     }
     double acc[S];
 #pragma unroll
@@ -186,7 +190,7 @@ __global__ void __launch_bounds__(NT, 1) step_bulk_kernel(StepArgs a, int64_t ns
         }
         // all reads of this stage are done: refill it with unit j + STAGES
         __syncthreads();
-        if (tid == 0 && j + STAGES < nmine) {
+        if (tid < 32 && j + STAGES < nmine) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             issue_unit<Q, S, NT>(a, blockIdx.x + (j + STAGES) * gridDim.x, nstrips, smem + stage * G::kStageFloats,
                                  smem_u32(&bars[stage]));

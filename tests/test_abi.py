@@ -29,7 +29,8 @@ def lib():
 
 def test_header_declares_the_paper_entry_points():
     names = declared_symbols()
-    for required in ("lb_rd_create", "lb_rd_init", "lb_rd_step", "lb_rd_moments"):
+    for required in ("lb_rd_create", "lb_rd_init", "lb_rd_step", "lb_rd_moments", "lb_rd_submit", "lb_rd_poll",
+                     "lb_rd_batch_create", "lb_rd_batch_step", "lb_rd_autotune", "lb_rd_step_noalloc"):
         assert required in names, required
 
 
@@ -80,6 +81,25 @@ def test_config_validation_accepts_and_sizes(lib):
     assert n64 > n
     nh = B.lb_rd_check_config(_cfg(precision="fp32_bf16dev"))
     assert nh < n
+
+
+def test_server_and_batch_reject_bad_configs_on_the_host(lib):
+    # validation happens before any device call
+    cfg = B.lb_rd_server_config(0, 4, 8, 0, 2, 1, None)
+    out = B.c_void_p()
+    assert lib.lb_rd_server_create(B.ctypes.byref(cfg), B.ctypes.byref(out)) == B.LB_RD_EINVAL
+    cfg = B.lb_rd_server_config(1 << 30, 4, 8, 0, 2, 0, None)  # fp64 serving is not offered
+    assert lib.lb_rd_server_create(B.ctypes.byref(cfg), B.ctypes.byref(out)) == B.LB_RD_EINVAL
+    assert lib.lb_rd_batch_create(None, 0, B.ctypes.byref(out)) == B.LB_RD_EINVAL
+    assert lib.lb_rd_poll(None, 1, None, None, None) == B.LB_RD_EINVAL
+
+
+def test_variant_table_on_the_host(lib):
+    n = B.lb_rd_variant_count("fp32")
+    names = [B.lb_rd_variant_name("fp32", v) for v in range(n)]
+    assert len(set(names)) == n and names[0] == "64x2_minb4"
+    assert any(x.startswith("bulk") for x in names) and any(x.startswith("tb2") for x in names)
+    assert B.lb_rd_variant_count("fp64") == 1
 
 
 def test_null_arguments_are_errors_not_crashes(lib):
