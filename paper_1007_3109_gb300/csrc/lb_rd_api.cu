@@ -91,7 +91,9 @@ std::tuple<int, int, int, int, int64_t, int64_t> tune_key(const lb_rd_handle *h)
     return std::make_tuple(dev, h->prec, h->Q, h->S, h->cfg.nx, h->cfg.ny);
 }
 
-int variant_count(int prec) { return prec == LB_RD_FP32 ? lbrd::kF32VariantCount : 1; }
+int variant_count(int prec) {
+    return prec == LB_RD_FP32 ? lbrd::kF32VariantCount : (prec == LB_RD_FP64 ? 1 : lbrd::kHalfVariantCount);
+}
 
 int variant_steps(int prec, int v) { return prec == LB_RD_FP32 ? lbrd::kF32Variants[v].steps : 1; }
 
@@ -103,7 +105,8 @@ cudaError_t launch_step(const lb_rd_handle *h, const lbrd::StepArgs &a, int vari
     switch (h->prec) {
         case LB_RD_FP64: return lbrd::launch_step_f64(h->Q, h->S, a, h->stream);
         case LB_RD_FP32: return lbrd::launch_step_f32_variant(variant, h->Q, h->S, a, h->stream);
-        default: return lbrd::launch_step_half(h->Q, h->S, h->prec == LB_RD_FP32_FP16DEV, a, h->stream);
+        default:
+            return lbrd::launch_step_half_variant(variant, h->Q, h->S, h->prec == LB_RD_FP32_FP16DEV, a, h->stream);
     }
 }
 }  // namespace
@@ -507,7 +510,10 @@ int lb_rd_variant_count(int32_t precision, int32_t *count) {
 const char *lb_rd_variant_name(int32_t precision, int32_t variant) {
     if (precision == LB_RD_FP32 && variant >= 0 && variant < lbrd::kF32VariantCount)
         return lbrd::kF32Variants[variant].name;
-    if (variant == 0) return precision == LB_RD_FP64 ? "f64_32x4" : "half_64x2";
+    if (precision == LB_RD_FP64) return variant == 0 ? "f64_32x4" : "";
+    if ((precision == LB_RD_FP32_BF16DEV || precision == LB_RD_FP32_FP16DEV) && variant >= 0 &&
+        variant < lbrd::kHalfVariantCount)
+        return lbrd::kHalfVariantNames[variant];
     return "";
 }
 

@@ -54,6 +54,9 @@ cudaError_t launch_init_f32(int Q, int S, const InitArgs &a, cudaStream_t st);
 // half_kind: 0 = bf16, 1 = fp16.
 StepShape step_shape_half(int64_t nx, int64_t ny);
 cudaError_t launch_step_half(int Q, int S, int half_kind, const StepArgs &a, cudaStream_t st);
+extern const char *const kHalfVariantNames[];
+extern const int kHalfVariantCount;
+cudaError_t launch_step_half_variant(int v, int Q, int S, int half_kind, const StepArgs &a, cudaStream_t st);
 cudaError_t launch_init_half(int Q, int S, int half_kind, const InitArgs &a, cudaStream_t st);
 
 // One block per tile (no persistent grid) and the tile counts of those

@@ -85,6 +85,46 @@ cudaError_t dispatch_init(int Q, int S, const InitArgs &a, cudaStream_t st) {
 
 StepShape step_shape_half(int64_t, int64_t) { return {dim3(max_persistent_blocks()), dim3(kBX, kBY)}; }
 
+namespace {
+template <int Q, int S, int H, int BX, int BY, int MINB>
+cudaError_t launch_shape(const StepArgs &a, cudaStream_t st) {
+    const int64_t nvec = (a.nx + kVec - 1) / kVec;
+    const int64_t tiles_x = (nvec + BX - 1) / BX;
+    const int64_t ntiles = tiles_x * ((a.ny + BY - 1) / BY);
+    auto kern = half::step_half_shape<Q, S, H, BX, BY, MINB>;
+    kern<<<persistent_blocks(kern, BX * BY, ntiles), dim3(BX, BY), 0, st>>>(a, tiles_x, ntiles);
+    return cudaGetLastError();
+}
+template <int H, int BX, int BY, int MINB>
+cudaError_t dispatch_shape(int Q, int S, const StepArgs &a, cudaStream_t st) {
+    if (Q == 9 && S == 1) return launch_shape<9, 1, H, BX, BY, MINB>(a, st);
+    if (Q == 9 && S == 2) return launch_shape<9, 2, H, BX, BY, MINB>(a, st);
+    if (Q == 5 && S == 1) return launch_shape<5, 1, H, BX, BY, MINB>(a, st);
+    if (Q == 5 && S == 2) return launch_shape<5, 2, H, BX, BY, MINB>(a, st);
+    return cudaErrorInvalidValue;
+}
+template <int H>
+cudaError_t dispatch_variant(int v, int Q, int S, const StepArgs &a, cudaStream_t st) {
+    switch (v) {
+        case 0: return dispatch_step<H>(Q, S, a, st);
+        case 1: return dispatch_shape<H, 64, 2, 5>(Q, S, a, st);
+        case 2: return dispatch_shape<H, 32, 4, 4>(Q, S, a, st);
+        case 3: return dispatch_shape<H, 128, 2, 2>(Q, S, a, st);
+        case 4: return dispatch_shape<H, 64, 2, 6>(Q, S, a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+}  // namespace
+
+const char *const kHalfVariantNames[] = {"half_64x2", "half_64x2_minb5", "half_32x4_minb4", "half_128x2_minb2",
+                                         "half_64x2_minb6"};
+const int kHalfVariantCount = 5;
+
+cudaError_t launch_step_half_variant(int v, int Q, int S, int half_kind, const StepArgs &a, cudaStream_t st) {
+    if (a.nx % kVec) return cudaErrorInvalidValue;
+    return half_kind ? dispatch_variant<1>(v, Q, S, a, st) : dispatch_variant<0>(v, Q, S, a, st);
+}
+
 cudaError_t launch_step_half(int Q, int S, int half_kind, const StepArgs &a, cudaStream_t st) {
     if (a.nx % kVec) return cudaErrorInvalidValue;
     return half_kind ? dispatch_step<1>(Q, S, a, st) : dispatch_step<0>(Q, S, a, st);

@@ -184,5 +184,20 @@ __global__ void __launch_bounds__(kNT) step_half_kernel(StepArgs a, int64_t tile
     if (a.mass_out) block_mass_reduce<S, kNT>(acc, a.partials, a.counter, a.mass_out);
 }
 
+// Launch variants: tile of BX x BY threads (4 sites each), register budget
+// from MINB resident blocks per SM.
+template <int Q, int S, int H, int BX, int BY, int MINB>
+__global__ void __launch_bounds__(BX *BY, MINB) step_half_shape(StepArgs a, int64_t tiles_x, int64_t ntiles) {
+    const int lane = threadIdx.x & 31;
+    double acc[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) acc[s] = 0.0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t ty = tile / tiles_x, tx = tile - ty * tiles_x;
+        tile_half<Q, S, H>(a, (tx * BX + threadIdx.x) * kVec, ty * BY + threadIdx.y, lane, acc);
+    }
+    if (a.mass_out) block_mass_reduce<S, BX * BY>(acc, a.partials, a.counter, a.mass_out);
+}
+
 }  // namespace half
 }  // namespace lbrd

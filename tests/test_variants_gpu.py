@@ -76,3 +76,20 @@ def test_autotune_leaves_the_state_unchanged():
         a.step(20)
         b.init(rho0).step(30)
         np.testing.assert_array_equal(a.moments()[0], b.moments()[0])
+
+
+@pytest.mark.parametrize("precision", ["fp32_bf16dev", "fp32_fp16dev"])
+@pytest.mark.parametrize("nx,ny", [(64, 48), (512, 20), (12, 3)])
+def test_every_half_variant_is_bitwise_identical(precision, nx, ny):
+    rho0 = inputs.rho0_square(nx, ny, seed=43, side=max(2, min(nx, ny) // 3))
+    kw = dict(lattice="D2Q9", nspecies=2, nx=nx, ny=ny, tau=[0.8, 0.65], reaction="gray_scott", F=0.04, k=0.06,
+              precision=precision)
+    outs = []
+    for v in range(B.lb_rd_variant_count(precision)):
+        with B.Simulation(**kw) as sim:
+            sim.set_variant(v)
+            sim.init(rho0).step(21)
+            outs.append((B.lb_rd_variant_name(precision, v), sim.moments()[0], sim.distributions()))
+    for name, rho, f in outs[1:]:
+        np.testing.assert_array_equal(rho, outs[0][1], err_msg=name)
+        np.testing.assert_array_equal(f, outs[0][2], err_msg=name)
