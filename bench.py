@@ -325,6 +325,96 @@ def serving_mode(args):
     return 0
 
 
+def truncation_mode(args):
+    """Point-source convergence study (Sec. II.B, Figs. 1-2) on the FP64 path:
+    E_rho over a (D, kappa) grid at D t = 8 on 100^2 sites, and a diffusive
+    refinement from 50^2 to 800^2; every run is a request to one FP64 server
+    (batched launches).  The value is the study's species-site updates per
+    second of wall time, submit to results on the host."""
+    import torch
+    from paper_1007_3109_gb300 import studies
+    torch.cuda.set_device(0)
+    Ds = [float(d) for d in np.geomspace(0.004, 0.3, 40)]
+    kappas = (0.0025, 0.005, 0.0075, 0.01, 0.015, 0.02, 0.033)
+    studies.truncation_sweep(Ds[-4:], kappas[:1], L=100, Dt=8.0)  # warm-up: library load, pools
+    sw = studies.truncation_sweep(Ds, kappas, L=100, Dt=8.0)
+    rf = studies.diffusive_refinement(0.05, 0.04, L0=50, t0=40, levels=5)
+    E = sw["E"]
+    branch = {}
+    for a, kap in enumerate(kappas):
+        loc = [i for i in range(1, len(Ds) - 1) if E[a, i] < E[a, i - 1] and E[a, i] < E[a, i + 1]]
+        branch[str(kap)] = [{"D": Ds[i], "E": float(E[a, i])} for i in loc]
+    slopes = {}
+    for D in (0.02, 0.05, 0.1):
+        b = int(np.argmin(np.abs(np.array(Ds) - D)))
+        slopes[f"{Ds[b]:.4f}"] = studies.loglog_slope(kappas, E[:, b])
+    ssu = 2 * (sw["site_steps"] + rf["site_steps"])
+    wall = sw["wall_s"] + rf["wall_s"]
+    line = {"metric": "MLUPS", "value": ssu / wall / 1e6, "unit": "MLUPS (species-site updates/s / 1e6)",
+            "n_gpus": 1, "steps": int(sum(sw["steps"]) * len(kappas) + sum(rf["steps"])), "warmup": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "point_source_sweep", "L": 100, "Dt": 8.0, "D": [Ds[0], Ds[-1], len(Ds)],
+                       "kappa": list(kappas), "refinement_L": rf["L"], "runs": len(Ds) * len(kappas) + len(rf["L"]),
+                       "timing": "wall clock, submit of the first request to the last result on the host"},
+            "study": {"E_min_global": {str(k): {"D": sw["D_min"][a], "E": sw["E_min"][a]} for a, k in enumerate(kappas)},
+                      "local_minima": branch, "slope_E_vs_kappa": slopes,
+                      "refinement": {"L": rf["L"], "E": rf["E"], "ratio": rf["ratio"], "order": rf["order"]}},
+            "gpu_launches": int(sw["launches"])}
+    if not args.no_cpu:
+        import oracle as orc
+        from oracle import Reaction
+        t0 = time.perf_counter()
+        cpu_ssu = 0
+        for D in Ds[12:]:
+            t = max(1, int(round(8.0 / D)))
+            rho0 = np.zeros((2, 100, 100))
+            rho0[0, 50, 50] = 1.0
+            tau = float(orc.tau_from_diffusion(D))
+            orc.density("D2Q9", orc.run("D2Q9", [tau, tau], Reaction("linear", kappa=0.01), orc.init("D2Q9", rho0), t))
+            cpu_ssu += 2 * 100 * 100 * t
+        cpu_s = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": cpu_ssu / cpu_s / 1e6, "unit": line["unit"], "cores": orc.threads(),
+                                "kind": "oracle",
+                                "sample": f"kappa = 0.01 row, {len(Ds) - 12} D values >= {Ds[12]:.4f}, 100^2, FP64"}
+    print(json.dumps(line))
+    return 0
+
+
+def phase_mode(args):
+    """gs_sweep_256 as a phase diagram (Sec. III.B-D, Fig. 6): the 1024-instance
+    (F, k) sweep for its full 10000 steps in one batch per storage format;
+    every instance labelled by linear theory and by its simulated outcome.
+    The value is the FP32 batch's MLUPS over the stepping (CUDA events)."""
+    import torch
+    from paper_1007_3109_gb300 import studies
+    torch.cuda.set_device(0)
+    steps = args.phase_steps
+    res = {p: studies.phase_diagram(p, steps) for p in ("fp32", "fp32_bf16dev", "fp32_fp16dev")}
+    ref = res["fp32"]
+    table = {}
+    for lab, o in zip(ref["label"], ref["outcome"]):
+        table.setdefault(lab, {}).setdefault(o["outcome"], 0)
+        table[lab][o["outcome"]] += 1
+    agree = {}
+    for p in ("fp32_bf16dev", "fp32_fp16dev"):
+        same = sum(a["outcome"] == b["outcome"] for a, b in zip(ref["outcome"], res[p]["outcome"]))
+        rel = [abs(a["wavelength"] - b["wavelength"]) / a["wavelength"]
+               for a, b in zip(ref["outcome"], res[p]["outcome"]) if a["outcome"] == b["outcome"] == "pattern"]
+        agree[p] = {"same_outcome": same, "pattern_instances": len(rel),
+                    "wavelength_rel_diff": {"median": float(np.median(rel)), "p90": float(np.percentile(rel, 90)),
+                                            "within_2pct": float(np.mean(np.array(rel) <= 0.02))}}
+    ssu = 2 * ref["site_steps"]
+    line = {"metric": "MLUPS", "value": ssu / ref["step_s"] / 1e6, "unit": "MLUPS (species-site updates/s / 1e6)",
+            "n_gpus": 1, "steps": steps, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "gs_sweep_256", "instances": len(ref["F"]), "steps": steps},
+            "by_precision_mlups": {p: 2 * r["site_steps"] / r["step_s"] / 1e6 for p, r in res.items()},
+            "theory_vs_outcome": table, "precision_agreement": agree,
+            "map": studies.outcome_map(ref), "gpu_launches": int(steps)}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -341,7 +431,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--tune-iters", type=int, default=10)
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serving"])
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serving", "truncation", "phase"])
+    ap.add_argument("--phase-steps", type=int, default=10000)
     ap.add_argument("--variant", default="", help="force a launch variant by name (after the autotune sweep)")
     ap.add_argument("--instances", type=int, default=0)
     ap.add_argument("--requests", type=int, default=64)
@@ -360,6 +451,10 @@ def main():
         return batch_mode(args)
     if args.mode == "serving":
         return serving_mode(args)
+    if args.mode == "truncation":
+        return truncation_mode(args)
+    if args.mode == "phase":
+        return phase_mode(args)
 
     import torch
     from paper_1007_3109_gb300 import binding as B

@@ -222,8 +222,9 @@ LB_RD_API int lb_rd_debug_inject_wait_timeout(lb_rd_handle *h, int32_t enable);
  * step is ONE launch of a persistent kernel that walks the combined
  * (instance x tile) work list; lb_rd_batch_step replays the steps as CUDA
  * graphs.  Every instance computes exactly what a single handle with its
- * config computes (bitwise: same kernel body, same arithmetic).  Supported
- * precisions: FP32 and the 16-bit deviation formats. */
+ * config computes (bitwise: same kernel body, same arithmetic).  Every
+ * precision is supported (FP64 runs the FP64 per-site update, e.g. for a
+ * point-source convergence sweep over D and kappa, Sec. II.B). */
 typedef struct lb_rd_batch lb_rd_batch;
 
 /* Allocate n >= 1 instances (two state copies each plus density caches).
@@ -261,10 +262,10 @@ LB_RD_API int lb_rd_batch_get_time(const lb_rd_batch *b, int64_t *t, int64_t *la
  * over all of them; requests that arrive meanwhile are admitted between ticks
  * as slots and memory free up.  A finished request's densities and mass are
  * copied to host memory and its device memory is released.  Each result is
- * bitwise what a single handle with the same config computes.  FP32 and the
- * 16-bit deviation formats; all requests of a server share lattice, species
- * count and precision (given in the server config).  submit and poll are
- * thread safe. */
+ * bitwise what a single handle with the same config computes.  Any
+ * precision; all requests of a server share lattice, species count and
+ * precision (given in the server config).  submit and poll are thread
+ * safe. */
 typedef struct {
     size_t hbm_budget_bytes;  /* device memory the resident requests may hold */
     int32_t max_slots;        /* resident requests at most, >= 1 */

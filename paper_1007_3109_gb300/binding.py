@@ -13,6 +13,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import time
 from ctypes import POINTER, c_double, c_int, c_int32, c_int64, c_size_t, c_void_p, c_char_p
 
 import numpy as np
@@ -358,6 +359,68 @@ def lb_rd_server_stats(s: int):
     a, b, c = c_int64(0), c_int64(0), c_int64(0)
     _check(lib().lb_rd_server_stats(s, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return {"launches": a.value, "ticks": b.value, "finished": c.value}
+
+
+class Server:
+    """Owner of one lb_rd_server (continuous batching of simulation requests)."""
+
+    def __init__(self, hbm_budget_bytes, max_slots=64, steps_per_tick=64, lattice="D2Q9", nspecies=2,
+                 precision="fp32", stream=None):
+        self.nspecies = int(nspecies)
+        self.s = lb_rd_server_create(hbm_budget_bytes, max_slots, steps_per_tick, lattice, nspecies, precision,
+                                     stream)
+        self._shape = {}
+
+    def submit(self, rho0, nsteps, **config) -> int:
+        """Queue a request (make_config kwargs); returns its ticket."""
+        rho0 = np.ascontiguousarray(rho0, dtype=np.float64)
+        t = lb_rd_submit(self.s, make_config(**config), rho0, nsteps)
+        self._shape[t] = rho0.shape
+        return t
+
+    def result(self, ticket, timeout_s=600.0):
+        """Block until the request finishes; returns (rho, mass, stats).
+        A failed request raises LbRdError with its status."""
+        shape = self._shape[ticket]
+        rho = np.empty(shape)
+        mass = np.empty(shape[0])
+        deadline = time.monotonic() + timeout_s
+        delay = 1e-4
+        while True:
+            rc, st = lb_rd_poll(self.s, ticket, rho, mass)
+            if rc != LB_RD_EPENDING:
+                del self._shape[ticket]
+                if rc != LB_RD_OK:
+                    raise LbRdError(rc, f"request {ticket} failed with status {rc}")
+                return rho, mass, st
+            if time.monotonic() > deadline:
+                raise LbRdError(LB_RD_ETIMEOUT, f"request {ticket} did not finish in {timeout_s} s")
+            time.sleep(delay)
+            delay = min(delay * 2, 0.01)
+
+    def drain(self, timeout_s=600.0):
+        lb_rd_server_drain(self.s, int(timeout_s * 1000))
+        return self
+
+    def stats(self):
+        return lb_rd_server_stats(self.s)
+
+    def close(self):
+        if self.s:
+            lb_rd_server_destroy(self.s)
+            self.s = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:

@@ -15,6 +15,7 @@
 #include "lb_rd.h"
 #include "lbrd_kernels.h"
 #include "step_f32_kernel.cuh"
+#include "step_f64_kernel.cuh"
 #include "step_half_kernel.cuh"
 
 namespace lbrd {
@@ -25,7 +26,10 @@ namespace {
 constexpr int kBX = 64, kBY = 2, kNT = kBX * kBY;  // the tile shape of both tile bodies
 static_assert(half::kBX == kBX && half::kBY == kBY, "tile shapes must agree");
 
-template <int Q, int S, int MODE>  // MODE 0: FP32 storage, 1: bf16 deviations, 2: fp16 deviations
+// MODE 0: FP32 storage, 1: bf16 deviations, 2: fp16 deviations, 3: FP64.
+// An FP64 tile covers the same 256 x 2 sites; a thread updates the sites
+// x = x_tile + threadIdx.x + 64 j, j < 4 (coalesced), one at a time.
+template <int Q, int S, int MODE>
 __global__ void __launch_bounds__(kNT, 4) batch_kernel(const BatchItem *__restrict__ items, int nitems,
                                                        int64_t total_tiles) {
     const int lane = threadIdx.x & 31;
@@ -38,9 +42,20 @@ __global__ void __launch_bounds__(kNT, 4) batch_kernel(const BatchItem *__restri
         const BatchItem &b = items[it];
         const int64_t local = t - b.tile_begin;
         const int64_t ty = local / b.tiles_x, tx = local - ty * b.tiles_x;
-        const int64_t x0 = (tx * kBX + threadIdx.x) * 4, y = ty * kBY + threadIdx.y;
-        if (MODE == 0) f32::tile_f32<Q, S, 0>(b.a, x0, y, lane, acc);
-        else half::tile_half<Q, S, MODE - 1>(b.a, x0, y, lane, acc);
+        const int64_t y = ty * kBY + threadIdx.y;
+        if constexpr (MODE == 3) {
+            if (y < b.a.ny) {
+#pragma unroll 1
+                for (int j = 0; j < 4; ++j) {
+                    const int64_t x = tx * kBX * 4 + threadIdx.x + j * kBX;
+                    if (x < b.a.nx) f64::site_f64<Q, S>(b.a, x, y, acc);
+                }
+            }
+        } else {
+            const int64_t x0 = (tx * kBX + threadIdx.x) * 4;
+            if constexpr (MODE == 0) f32::tile_f32<Q, S, 0>(b.a, x0, y, lane, acc);
+            else half::tile_half<Q, S, MODE - 1>(b.a, x0, y, lane, acc);
+        }
     }
 }
 
@@ -67,6 +82,21 @@ size_t align256(size_t n) { return (n + 255) / 256 * 256; }
 
 }  // namespace
 
+int batch_mode(int precision) {
+    switch (precision) {
+        case LB_RD_FP32: return 0;
+        case LB_RD_FP32_BF16DEV: return 1;
+        case LB_RD_FP32_FP16DEV: return 2;
+        default: return 3;
+    }
+}
+
+cudaError_t launch_batch_init(int mode, int Q, int S, const InitArgs &a, cudaStream_t st) {
+    if (mode == 0) return launch_init_f32(Q, S, a, st);
+    if (mode == 3) return launch_init_f64(Q, S, a, st);
+    return launch_init_half(Q, S, mode == 2, a, st);
+}
+
 int64_t batch_tiles_x(int64_t nx) { return ((nx + 3) / 4 + kBX - 1) / kBX; }
 
 int64_t batch_tiles(int64_t nx, int64_t ny) { return batch_tiles_x(nx) * ((ny + kBY - 1) / kBY); }
@@ -77,6 +107,7 @@ cudaError_t launch_batch_step(int mode, int Q, int S, const BatchItem *items, in
         case 0: return dispatch_batch<0>(Q, S, items, n, total_tiles, st);
         case 1: return dispatch_batch<1>(Q, S, items, n, total_tiles, st);
         case 2: return dispatch_batch<2>(Q, S, items, n, total_tiles, st);
+        case 3: return dispatch_batch<3>(Q, S, items, n, total_tiles, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -160,9 +191,7 @@ int lb_rd_batch_create(const lb_rd_config *cfgs, int32_t n, lb_rd_batch **out) {
                                                   " differs from instance 0 in lattice, nspecies or precision");
     }
     const int prec = cfgs[0].precision;
-    if (prec == LB_RD_FP64)
-        return report_error(LB_RD_EINVAL, "lb_rd_batch_create: batches support fp32 and 16-bit deviation storage");
-    const bool half = prec != LB_RD_FP32;
+    const bool half = prec == LB_RD_FP32_BF16DEV || prec == LB_RD_FP32_FP16DEV;
     for (int i = 0; i < n; ++i)
         if (half && cfgs[i].nx % 4)
             return report_error(LB_RD_EINVAL, "lb_rd_batch_create: 16-bit deviation storage needs nx % 4 == 0");
@@ -174,7 +203,7 @@ int lb_rd_batch_create(const lb_rd_config *cfgs, int32_t n, lb_rd_batch **out) {
     b->Q = cfgs[0].lattice == LB_RD_D2Q9 ? 9 : 5;
     b->S = cfgs[0].nspecies;
     b->prec = prec;
-    b->mode = prec == LB_RD_FP32 ? 0 : (prec == LB_RD_FP32_BF16DEV ? 1 : 2);
+    b->mode = lbrd::batch_mode(prec);
     b->stream = static_cast<cudaStream_t>(cfgs[0].stream);
     b->inited.assign(n, false);
     size_t max_parts = 0;
@@ -186,7 +215,7 @@ int lb_rd_batch_create(const lb_rd_config *cfgs, int32_t n, lb_rd_batch **out) {
         b->state_off.push_back(b->state_total);
         b->rho_off.push_back(b->rho_total);
         b->state_total += lbrd::align256(lbrd::state_plane_bytes(prec, b->Q, b->S, c.ny, pitch));
-        b->rho_total += lbrd::align256((size_t)b->S * c.ny * pitch * 4);
+        b->rho_total += lbrd::align256((size_t)b->S * c.ny * pitch * (prec == LB_RD_FP64 ? 8 : 4));
         const size_t parts = lbrd::mass_partials_needed(c.nx, c.ny);
         if (parts > max_parts) max_parts = parts;
         lbrd::BatchItem &it = items[i];
@@ -274,8 +303,7 @@ int lb_rd_batch_init(lb_rd_batch *b, int32_t idx, const double *rho0, int is_dev
     a.F = c.reaction.F;
     a.k = c.reaction.k;
     a.rho_out = b->rho + b->rho_off[idx];
-    cudaError_t e = b->prec == LB_RD_FP32 ? lbrd::launch_init_f32(b->Q, b->S, a, b->stream)
-                                          : lbrd::launch_init_half(b->Q, b->S, b->mode == 2, a, b->stream);
+    cudaError_t e = lbrd::launch_batch_init(b->mode, b->Q, b->S, a, b->stream);
     if (e) return cuda_err(e, "batch init kernel");
     b->launches++;
     if (!is_device) {

@@ -92,7 +92,9 @@ struct BatchItem {
 };
 int64_t batch_tiles_x(int64_t nx);
 int64_t batch_tiles(int64_t nx, int64_t ny);
-// mode: 0 FP32 storage, 1 bf16 deviations, 2 fp16 deviations.
+// mode: 0 FP32 storage, 1 bf16 deviations, 2 fp16 deviations, 3 FP64.
+int batch_mode(int precision);
+cudaError_t launch_batch_init(int mode, int Q, int S, const InitArgs &a, cudaStream_t st);
 cudaError_t launch_batch_step(int mode, int Q, int S, const BatchItem *items, int n, int64_t total_tiles,
                              cudaStream_t st);
 

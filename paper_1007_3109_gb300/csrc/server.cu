@@ -62,7 +62,7 @@ struct Request {
 
 size_t request_bytes(const lb_rd_config &c, int Q, int64_t pitch, size_t *state_bytes, size_t *rho_bytes) {
     *state_bytes = lbrd::state_plane_bytes(c.precision, Q, c.nspecies, c.ny, pitch);
-    *rho_bytes = (size_t)c.nspecies * c.ny * pitch * 4;
+    *rho_bytes = (size_t)c.nspecies * c.ny * pitch * (c.precision == LB_RD_FP64 ? 8 : 4);
     return 2 * *state_bytes + *rho_bytes;
 }
 
@@ -142,8 +142,7 @@ bool start_request(lb_rd_server *s, Request *r) {
         a.F = c.reaction.F;
         a.k = c.reaction.k;
         a.rho_out = r->rho;
-        e = s->mode == 0 ? lbrd::launch_init_f32(s->Q, c.nspecies, a, s->stream)
-                         : lbrd::launch_init_half(s->Q, c.nspecies, s->mode == 2, a, s->stream);
+        e = lbrd::launch_batch_init(s->mode, s->Q, c.nspecies, a, s->stream);
     }
     if (stage) cudaFreeAsync(stage, s->stream);
     if (e) {
@@ -318,12 +317,12 @@ int lb_rd_server_create(const lb_rd_server_config *cfg, lb_rd_server **out) {
         return lbrd::report_error(LB_RD_EINVAL, "lb_rd_server_create: unknown lattice");
     if (cfg->nspecies < 1 || cfg->nspecies > 2)
         return lbrd::report_error(LB_RD_EINVAL, "lb_rd_server_create: nspecies must be 1 or 2");
-    if (cfg->precision < LB_RD_FP32 || cfg->precision > LB_RD_FP32_FP16DEV)
-        return lbrd::report_error(LB_RD_EINVAL, "lb_rd_server_create: serving supports fp32 and 16-bit deviation storage");
+    if (cfg->precision < LB_RD_FP64 || cfg->precision > LB_RD_FP32_FP16DEV)
+        return lbrd::report_error(LB_RD_EINVAL, "lb_rd_server_create: unknown precision");
     lb_rd_server *s = new lb_rd_server();
     s->cfg = *cfg;
     s->Q = cfg->lattice == LB_RD_D2Q9 ? 9 : 5;
-    s->mode = cfg->precision == LB_RD_FP32 ? 0 : (cfg->precision == LB_RD_FP32_BF16DEV ? 1 : 2);
+    s->mode = lbrd::batch_mode(cfg->precision);
     cudaError_t e = cudaGetDevice(&s->device);
     if (!e) {
         if (cfg->stream) {
@@ -389,7 +388,7 @@ int lb_rd_submit(lb_rd_server *s, const lb_rd_config *cfg, const double *rho0, i
     if (rc) return rc;
     if (cfg->lattice != s->cfg.lattice || cfg->nspecies != s->cfg.nspecies || cfg->precision != s->cfg.precision)
         return lbrd::report_error(LB_RD_EINVAL, "lb_rd_submit: lattice, nspecies and precision must match the server");
-    if (s->mode != 0 && cfg->nx % 4)
+    if ((s->mode == 1 || s->mode == 2) && cfg->nx % 4)
         return lbrd::report_error(LB_RD_EINVAL, "lb_rd_submit: 16-bit deviation storage needs nx % 4 == 0");
     if (nsteps < 1) return lbrd::report_error(LB_RD_EINVAL, "lb_rd_submit: nsteps must be >= 1");
     Request *r = new Request();

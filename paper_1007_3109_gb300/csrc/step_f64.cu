@@ -1,11 +1,8 @@
-// FP64 step: one thread per site, every floating-point operation rounded on
-// its own (__dadd_rn / __dmul_rn are never contracted into FMA), in the
-// operation order of Eq. relax:
-//   post = f + (w_i rho - f) * omega + w_i R,   rho = sum_i f_i (index order)
-// This path exists for the convergence study and for bit-level agreement with
-// a plain FP64 implementation of the method; GB300's FP64 rate, not HBM,
-// bounds it.
+// FP64 step kernels: a persistent grid over 32 x 4 site tiles running the
+// per-site update of step_f64_kernel.cuh.  GB300's FP64 rate, not HBM, bounds
+// them.
 #include "lbrd_kernels.h"
+#include "step_f64_kernel.cuh"
 
 namespace lbrd {
 
@@ -15,9 +12,6 @@ constexpr int kBX = 32, kBY = 4, kNT = kBX * kBY;
 
 template <int Q, int S>
 __global__ void __launch_bounds__(kNT) step_f64_kernel(StepArgs a, int64_t tiles_x, int64_t ntiles) {
-    using L = Lattice<Q>;
-    const double *__restrict__ src = static_cast<const double *>(a.src);
-    double *__restrict__ dst = static_cast<double *>(a.dst);
     double acc[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[s] = 0.0;
@@ -27,37 +21,7 @@ __global__ void __launch_bounds__(kNT) step_f64_kernel(StepArgs a, int64_t tiles
         const int64_t x = tx * kBX + threadIdx.x;
         const int64_t y = ty * kBY + threadIdx.y;
         if (x >= a.nx || y >= a.ny) continue;
-        double f[S][Q], rho[S];
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                // pull: f_i(x, t + 1) = f*_i(x - e_i, t), periodic
-                const int64_t xs = wrap(x - L::ex(i), a.nx);
-                const int64_t ys = wrap(y - L::ey(i), a.ny);
-                f[s][i] = src[(int64_t)(s * Q + i) * a.plane + ys * a.pitch + xs];
-            }
-            double r = f[s][0];
-#pragma unroll
-            for (int i = 1; i < Q; ++i) r = __dadd_rn(r, f[s][i]);
-            rho[s] = r;
-        }
-        double R[S];
-        reaction_f64<S>(a.rkind, a.kappa, a.F, a.k, rho, R);
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-            const double om = a.omega[s];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const double w = weight<Q, double>(i);
-                const double feq = __dmul_rn(w, rho[s]);
-                const double post =
-                    __dadd_rn(__dadd_rn(f[s][i], __dmul_rn(__dsub_rn(feq, f[s][i]), om)), __dmul_rn(w, R[s]));
-                dst[(int64_t)(s * Q + i) * a.plane + y * a.pitch + x] = post;
-            }
-            if (a.rho_out) static_cast<double *>(a.rho_out)[(int64_t)s * a.plane + y * a.pitch + x] = rho[s];
-            acc[s] = __dadd_rn(acc[s], rho[s]);
-        }
+        f64::site_f64<Q, S>(a, x, y, acc);
     }
     if (a.mass_out) block_mass_reduce<S, kNT>(acc, a.partials, a.counter, a.mass_out);
 }

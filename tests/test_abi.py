@@ -88,7 +88,9 @@ def test_server_and_batch_reject_bad_configs_on_the_host(lib):
     cfg = B.lb_rd_server_config(0, 4, 8, 0, 2, 1, None)
     out = B.c_void_p()
     assert lib.lb_rd_server_create(B.ctypes.byref(cfg), B.ctypes.byref(out)) == B.LB_RD_EINVAL
-    cfg = B.lb_rd_server_config(1 << 30, 4, 8, 0, 2, 0, None)  # fp64 serving is not offered
+    cfg = B.lb_rd_server_config(1 << 30, 4, 8, 0, 2, 7, None)  # unknown precision
+    assert lib.lb_rd_server_create(B.ctypes.byref(cfg), B.ctypes.byref(out)) == B.LB_RD_EINVAL
+    cfg = B.lb_rd_server_config(1 << 30, 4, 8, 0, 3, 0, None)  # three species
     assert lib.lb_rd_server_create(B.ctypes.byref(cfg), B.ctypes.byref(out)) == B.LB_RD_EINVAL
     assert lib.lb_rd_batch_create(None, 0, B.ctypes.byref(out)) == B.LB_RD_EINVAL
     assert lib.lb_rd_poll(None, 1, None, None, None) == B.LB_RD_EINVAL

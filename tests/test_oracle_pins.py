@@ -480,3 +480,54 @@ def test_point_source_normalisation_and_error_metric():
     assert rho.sum() == pytest.approx(math.exp(-4.0), rel=1e-9)
     assert orc.relative_error(rho, rho) == 0.0
     assert orc.relative_error(rho, 1.01 * rho) == pytest.approx(0.01, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Order of accuracy of the point-source problem (Sec. II.B, appendix)
+# ---------------------------------------------------------------------------
+
+def _point_source_error(L, D, kappa, t, lat="D2Q9"):
+    rho0 = np.zeros((1, L, L))
+    rho0[0, L // 2, L // 2] = 1.0
+    f = orc.run(lat, [float(orc.tau_from_diffusion(D))], Reaction("linear", kappa=kappa), orc.init(lat, rho0), t)
+    an = orc.point_source(L, L, L // 2, L // 2, D, kappa, t)
+    return orc.relative_error(an, orc.density(lat, f)[0])
+
+
+@pytest.mark.parametrize("D,kappa", [(0.02, 0.0), (0.05, 0.04), (0.1, 0.132), (1.0 / 6.0, 0.04)])
+def test_point_source_second_order_under_diffusive_refinement(D, kappa):
+    """The Chapman-Enskog expansion of the appendix makes the scheme a
+    second-order approximation of Eq. reac_diff3 under diffusive scaling
+    (dx -> dx/2, dt -> dt/4: D fixed in lattice units, kappa/4, 4 t steps).
+    E_rho of one physical problem must fall by 4 per level (a wrong weight,
+    tau map or source term leaves an O(1) error that does not converge)."""
+    L0, t0 = 50, int(round(2.0 / D))
+    e = [_point_source_error(L0 * 2 ** l, D, kappa / 4 ** l, t0 * 4 ** l) for l in range(3)]
+    assert e[0] / e[1] == pytest.approx(4.0, rel=0.06), e
+    assert e[1] / e[2] == pytest.approx(4.0, rel=0.03), e
+
+
+def test_point_source_fourth_order_at_tau_one():
+    """At tau = 1 without reaction the update is rho(t + 1) = sum_i w_i rho(x - e_i)
+    whose symbol (2/3 + cos(k_x)/3)(2/3 + cos(k_y)/3) agrees with
+    exp(-D |k|^2) for D = 1/6 through |k|^4 (the first difference is the k^6
+    term: 1/2160 against 1/1296), so under diffusive refinement the error
+    falls by 2^4 = 16 per level, not 4."""
+    kx = 1e-2
+    sym = 2.0 / 3.0 + math.cos(kx) / 3.0
+    assert abs(sym - math.exp(-kx * kx / 6.0)) < 2e-13  # O(k^6) ~ 1e-12 * (1/1296 - 1/2160)
+    D = 1.0 / 6.0
+    e = [_point_source_error(50 * 2 ** l, D, 0.0, 12 * 4 ** l) for l in range(3)]
+    assert e[0] / e[1] > 14.0 and e[1] / e[2] > 14.0, e
+
+
+def test_point_source_decay_error_is_kappa_squared_t():
+    """Reading of Eq. relax for the source: the mass of A follows
+    (1 - kappa)^t, while Eq. reac_diff5 decays as exp(-kappa t).  At
+    D = 1/6 the diffusion error is fourth order and small, so E_rho is
+    dominated by |1 - (1 - kappa)^t exp(kappa t)| ~ kappa^2 t / 2."""
+    D, L, t = 1.0 / 6.0, 100, 48
+    for kappa in (0.01, 0.02, 0.04):
+        e = _point_source_error(L, D, kappa, t)
+        amp = abs(1.0 - (1.0 - kappa) ** t * math.exp(kappa * t))
+        assert e == pytest.approx(amp, rel=0.05), (kappa, e, amp)

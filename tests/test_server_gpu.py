@@ -115,3 +115,34 @@ def test_destroy_with_requests_in_flight():
         B.lb_rd_submit(srv, B.make_config(**kw), rho0, 2000)
     time.sleep(0.05)
     B.lb_rd_server_destroy(srv)  # must not hang or fault
+
+
+def test_fp64_server_equals_oracle_bitwise():
+    """An FP64 server: requests of different sizes, relaxation times and step
+    counts (a point-source sweep over D at D t = const, Sec. II.B) finish at
+    different ticks; each result equals the oracle element by element."""
+    import oracle as orc
+    from oracle import Reaction
+
+    srv = B.lb_rd_server_create(hbm_budget_bytes=1 << 28, max_slots=3, steps_per_tick=16, precision="fp64")
+    try:
+        jobs = []
+        for j, D in enumerate((0.02, 0.04, 0.1, 1.0 / 6.0)):
+            L = 40 + 10 * j
+            rho0 = np.zeros((2, L, L))
+            rho0[0, L // 2, L // 2] = 1.0
+            tau = 3.0 * D + 0.5
+            kw = dict(lattice="D2Q9", nspecies=2, nx=L, ny=L, tau=[tau, tau], reaction="linear", kappa=0.01,
+                      precision="fp64")
+            steps = int(round(2.0 / D))
+            jobs.append((kw, rho0, steps, B.lb_rd_submit(srv, B.make_config(**kw), rho0, steps)))
+        for kw, rho0, steps, t in jobs:
+            rc, rho, mass, st = _wait(srv, t, 2, kw["nx"])
+            assert rc == B.LB_RD_OK and st["steps"] == steps
+            ref = orc.density("D2Q9", orc.run("D2Q9", kw["tau"], Reaction("linear", kappa=0.01),
+                                              orc.init("D2Q9", rho0), steps))
+            np.testing.assert_array_equal(rho, ref)
+            # A -> B conserves the total: sum of both species stays 1
+            assert abs(mass.sum() - 1.0) < 1e-13
+    finally:
+        B.lb_rd_server_destroy(srv)
