@@ -41,6 +41,13 @@
  *   kind 2, Gray-Scott (Sec. III, Eq. reac_diff10 / reac_diff11) in Pearson's
  *     lattice form with A0 = k1 = 1, k_f = F, k_0 = k_f, k_2 = k, u = A, v = B:
  *     R_u = -u v^2 + F (1 - u),  R_v = u v^2 - (F + k) v.
+ *   kind 3, a mass-action network of up to ORC_MAX_R reaction steps among
+ *     S <= ORC_MAX_S species (Eq. reac_diff1 is written for N species; the
+ *     paper's own systems are built from such steps, e.g. U + 2V -> 3V):
+ *     step r proceeds at rate_r = k_r prod_j rho_j^a_rj and changes species
+ *     s by nu_rs per event, so R_s = sum_r nu_rs rate_r.  Evaluated as
+ *     p = k_r, then p = p * rho_j repeated a_rj times for j = 0 .. S-1, then
+ *     R_s = R_s + nu_rs * p for every s with nu_rs != 0, reactions in order.
  */
 #include <stddef.h>
 #include <stdint.h>
@@ -51,6 +58,19 @@
 
 #define ORC_OK 0
 #define ORC_EINVAL 1
+#define ORC_MAX_S 4
+#define ORC_MAX_R 8
+
+/* A reaction source: kind 0..2 with (kappa, F, k), or kind 3 with a network
+ * (order[r][s] = a_rs >= 0, change[r][s] = nu_rs). */
+typedef struct {
+    int kind;
+    double kappa, F, k;
+    int nr;
+    double rate[ORC_MAX_R];
+    int order[ORC_MAX_R][ORC_MAX_S];
+    int change[ORC_MAX_R][ORC_MAX_S];
+} orc_source;
 
 /* Velocity sets and weights (Eq. Weights for D2Q9; D2Q5 by the reading
  * above).  Returns Q, or 0 for an unknown lattice. */
@@ -105,13 +125,60 @@ void orc_reaction(int kind, double kappa, double F, double k, int S,
     }
 }
 
+/* Mass-action source of one site (kind 3, see the header). */
+static void network_reaction(const orc_source *src, int S, const double *rho, double *R)
+{
+    int r, j, e, s;
+    for (s = 0; s < S; ++s)
+        R[s] = 0.0;
+    for (r = 0; r < src->nr; ++r) {
+        double p = src->rate[r];
+        for (j = 0; j < S; ++j)
+            for (e = 0; e < src->order[r][j]; ++e)
+                p = p * rho[j];
+        for (s = 0; s < S; ++s)
+            if (src->change[r][s] != 0)
+                R[s] = R[s] + (double)src->change[r][s] * p;
+    }
+}
+
+static void source_eval(const orc_source *src, int S, const double *rho, double *R)
+{
+    if (src->kind == 3)
+        network_reaction(src, S, rho, R);
+    else
+        orc_reaction(src->kind, src->kappa, src->F, src->k, S, rho, R);
+}
+
+/* R of one site under a network given as flat arrays (rate[nr],
+ * order[nr * S], change[nr * S], row r = reaction step). */
+int orc_network_reaction(int S, int nr, const double *rate, const int *order, const int *change,
+                         const double *rho, double *R)
+{
+    orc_source src;
+    int r, s;
+    if (S < 1 || S > ORC_MAX_S || nr < 0 || nr > ORC_MAX_R)
+        return ORC_EINVAL;
+    src.kind = 3;
+    src.nr = nr;
+    for (r = 0; r < nr; ++r) {
+        src.rate[r] = rate[r];
+        for (s = 0; s < S; ++s) {
+            src.order[r][s] = order[r * S + s];
+            src.change[r][s] = change[r * S + s];
+        }
+    }
+    network_reaction(&src, S, rho, R);
+    return ORC_OK;
+}
+
 static int check_args(int lattice, int S, int64_t nx, int64_t ny, int kind)
 {
     if (lattice != 0 && lattice != 1)
         return ORC_EINVAL;
-    if (S < 1 || S > 2 || nx < 1 || ny < 1)
+    if (S < 1 || S > ORC_MAX_S || nx < 1 || ny < 1)
         return ORC_EINVAL;
-    if (kind < 0 || kind > 2 || (kind == 2 && S != 2))
+    if (kind < 0 || kind > 3 || (kind == 2 && S != 2) || (kind == 1 && S > 2))
         return ORC_EINVAL;
     return ORC_OK;
 }
@@ -165,16 +232,15 @@ int orc_density(int lattice, int S, int64_t nx, int64_t ny, const double *f, dou
 /* One time step t -> t+1: collide every site, then push each post-collision
  * value to its neighbour x + e_i with periodic wrap in x and y (periodic
  * boundaries as in Sec. II.B and Sec. IV).  f_in and f_out must not alias. */
-int orc_step(int lattice, int S, int64_t nx, int64_t ny, const double *tau,
-             int kind, double kappa, double F, double k,
-             const double *f_in, double *f_out)
+static int step_impl(int lattice, int S, int64_t nx, int64_t ny, const double *tau, const orc_source *src,
+                     const double *f_in, double *f_out)
 {
     int ex[9], ey[9];
     double w[9];
-    double omega[2];
+    double omega[ORC_MAX_S];
     int Q, s;
     int64_t y;
-    if (check_args(lattice, S, nx, ny, kind))
+    if (check_args(lattice, S, nx, ny, src->kind))
         return ORC_EINVAL;
     for (s = 0; s < S; ++s) {
         if (!(tau[s] > 0.5))
@@ -186,7 +252,7 @@ int orc_step(int lattice, int S, int64_t nx, int64_t ny, const double *tau,
     for (y = 0; y < ny; ++y) {
         int64_t x;
         for (x = 0; x < nx; ++x) {
-            double rho[2], R[2];
+            double rho[ORC_MAX_S], R[ORC_MAX_S];
             int ss, i;
             for (ss = 0; ss < S; ++ss) {
                 double r = 0.0;
@@ -194,7 +260,7 @@ int orc_step(int lattice, int S, int64_t nx, int64_t ny, const double *tau,
                     r += f_in[at(nx, ny, Q, ss, i, y, x)];
                 rho[ss] = r;
             }
-            orc_reaction(kind, kappa, F, k, S, rho, R);
+            source_eval(src, S, rho, R);
             for (ss = 0; ss < S; ++ss) {
                 for (i = 0; i < Q; ++i) {
                     double fi = f_in[at(nx, ny, Q, ss, i, y, x)];
@@ -210,11 +276,29 @@ int orc_step(int lattice, int S, int64_t nx, int64_t ny, const double *tau,
     return ORC_OK;
 }
 
-/* nsteps steps on f; tmp is a caller buffer of the same size.  The two
- * buffers alternate, and the final state is left in f. */
-int orc_run(int lattice, int S, int64_t nx, int64_t ny, const double *tau,
-            int kind, double kappa, double F, double k, int64_t nsteps,
-            double *f, double *tmp)
+static orc_source simple_source(int kind, double kappa, double F, double k)
+{
+    orc_source src;
+    src.kind = kind;
+    src.kappa = kappa;
+    src.F = F;
+    src.k = k;
+    src.nr = 0;
+    return src;
+}
+
+int orc_step(int lattice, int S, int64_t nx, int64_t ny, const double *tau,
+             int kind, double kappa, double F, double k,
+             const double *f_in, double *f_out)
+{
+    orc_source src = simple_source(kind, kappa, F, k);
+    if (kind == 3)
+        return ORC_EINVAL;
+    return step_impl(lattice, S, nx, ny, tau, &src, f_in, f_out);
+}
+
+static int run_impl(int lattice, int S, int64_t nx, int64_t ny, const double *tau, const orc_source *src,
+                    int64_t nsteps, double *f, double *tmp)
 {
     int64_t t;
     int Q = (lattice == 0) ? 9 : 5;
@@ -222,7 +306,7 @@ int orc_run(int lattice, int S, int64_t nx, int64_t ny, const double *tau,
     double *a = f, *b = tmp;
     for (t = 0; t < nsteps; ++t) {
         double *c;
-        int rc = orc_step(lattice, S, nx, ny, tau, kind, kappa, F, k, a, b);
+        int rc = step_impl(lattice, S, nx, ny, tau, src, a, b);
         if (rc)
             return rc;
         c = a;
@@ -235,6 +319,39 @@ int orc_run(int lattice, int S, int64_t nx, int64_t ny, const double *tau,
             f[j] = a[j];
     }
     return ORC_OK;
+}
+
+/* nsteps steps on f; tmp is a caller buffer of the same size.  The two
+ * buffers alternate, and the final state is left in f. */
+int orc_run(int lattice, int S, int64_t nx, int64_t ny, const double *tau,
+            int kind, double kappa, double F, double k, int64_t nsteps,
+            double *f, double *tmp)
+{
+    orc_source src = simple_source(kind, kappa, F, k);
+    if (kind == 3)
+        return ORC_EINVAL;
+    return run_impl(lattice, S, nx, ny, tau, &src, nsteps, f, tmp);
+}
+
+/* orc_run with a mass-action network (kind 3) given as flat arrays as in
+ * orc_network_reaction. */
+int orc_run_network(int lattice, int S, int64_t nx, int64_t ny, const double *tau,
+                    int nr, const double *rate, const int *order, const int *change, int64_t nsteps,
+                    double *f, double *tmp)
+{
+    orc_source src = simple_source(3, 0.0, 0.0, 0.0);
+    int r, s;
+    if (S < 1 || S > ORC_MAX_S || nr < 0 || nr > ORC_MAX_R)
+        return ORC_EINVAL;
+    src.nr = nr;
+    for (r = 0; r < nr; ++r) {
+        src.rate[r] = rate[r];
+        for (s = 0; s < S; ++s) {
+            src.order[r][s] = order[r * S + s];
+            src.change[r][s] = change[r * S + s];
+        }
+    }
+    return run_impl(lattice, S, nx, ny, tau, &src, nsteps, f, tmp);
 }
 
 /* Number of threads the parallel loops use. */

@@ -33,7 +33,7 @@ _SRC = os.path.join(_HERE, "lbrd_oracle.c")
 _LIB = os.path.join(_HERE, "liblbrd_oracle.so")
 
 LATTICES = {"D2Q9": 0, "D2Q5": 1}
-REACTIONS = {"none": 0, "linear": 1, "gray_scott": 2}
+REACTIONS = {"none": 0, "linear": 1, "gray_scott": 2, "mass_action": 3}
 CS2 = 1.0 / 3.0  # lattice sound speed squared, c_s^2 = dx^2 / (3 dt^2) (Sec. II.A)
 
 __all__ = [
@@ -63,10 +63,32 @@ class Reaction:
     kappa: float = 0.0
     F: float = 0.0
     k: float = 0.0
+    rates: tuple = ()
+    order: tuple = ()
+    change: tuple = ()
 
     @property
     def code(self) -> int:
         return REACTIONS[self.kind]
+
+    @staticmethod
+    def network(rates, order, change) -> "Reaction":
+        """Mass-action network (Eq. reac_diff1 for N species built from
+        reaction steps): step r runs at rate_r = k_r prod_j rho_j^order[r][j]
+        and changes species s by change[r][s], R_s = sum_r change[r][s] rate_r.
+        Evaluated in the compiled oracle as p = k_r, p *= rho_j (order[r][j]
+        times, j ascending), R_s += change[r][s] * p (reactions in order,
+        zero changes skipped)."""
+        return Reaction("mass_action", rates=tuple(float(r) for r in rates),
+                        order=tuple(tuple(int(a) for a in row) for row in order),
+                        change=tuple(tuple(int(c) for c in row) for row in change))
+
+    def _arrays(self, S):
+        nr = len(self.rates)
+        rate = np.ascontiguousarray(self.rates, dtype=np.float64)
+        order = np.ascontiguousarray(np.asarray(self.order, dtype=np.int32).reshape(nr, S))
+        change = np.ascontiguousarray(np.asarray(self.change, dtype=np.int32).reshape(nr, S))
+        return nr, rate, order, change
 
 
 def build(out: str = _LIB, src: str = _SRC, cc: str = "gcc") -> str:
@@ -79,6 +101,10 @@ def build(out: str = _LIB, src: str = _SRC, cc: str = "gcc") -> str:
 
 def _dptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _iptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
 
 
 class OracleLib:
@@ -102,6 +128,11 @@ class OracleLib:
         L.orc_step.restype = i32
         L.orc_run.argtypes = [i32, i32, i64, i64, dp, i32, f64, f64, f64, i64, dp, dp]
         L.orc_run.restype = i32
+        ip32 = ctypes.POINTER(ctypes.c_int32)
+        L.orc_network_reaction.argtypes = [i32, i32, dp, ip32, ip32, dp, dp]
+        L.orc_network_reaction.restype = i32
+        L.orc_run_network.argtypes = [i32, i32, i64, i64, dp, i32, dp, ip32, ip32, i64, dp, dp]
+        L.orc_run_network.restype = i32
         L.orc_threads.argtypes = []
         L.orc_threads.restype = i32
         self.L = L
@@ -121,6 +152,11 @@ class OracleLib:
     def reaction(self, reaction: Reaction, rho):
         rho = np.ascontiguousarray(rho, dtype=np.float64)
         R = np.zeros_like(rho)
+        if reaction.kind == "mass_action":
+            nr, rate, order, change = reaction._arrays(len(rho))
+            _check(self.L.orc_network_reaction(len(rho), nr, _dptr(rate), _iptr(order), _iptr(change),
+                                               _dptr(rho), _dptr(R)))
+            return R
         self.L.orc_reaction(reaction.code, reaction.kappa, reaction.F, reaction.k, len(rho), _dptr(rho), _dptr(R))
         return R
 
@@ -145,6 +181,8 @@ class OracleLib:
 
     def step(self, lat, taus, reaction: Reaction, f):
         """One LB time step (Eq. relax, multi-species form); returns a new array."""
+        if reaction.kind == "mass_action":
+            return self.run(lat, taus, reaction, f, 1)
         f = np.ascontiguousarray(f, dtype=np.float64)
         S, Q, ny, nx = f.shape
         tau = np.ascontiguousarray(np.broadcast_to(np.asarray(taus, dtype=np.float64), (S,)))
@@ -159,6 +197,11 @@ class OracleLib:
         S, Q, ny, nx = f.shape
         tau = np.ascontiguousarray(np.broadcast_to(np.asarray(taus, dtype=np.float64), (S,)))
         tmp = np.empty_like(f)
+        if reaction.kind == "mass_action":
+            nr, rate, order, change = reaction._arrays(S)
+            _check(self.L.orc_run_network(_code(lat), S, nx, ny, _dptr(tau), nr, _dptr(rate), _iptr(order),
+                                          _iptr(change), int(nsteps), _dptr(f), _dptr(tmp)))
+            return f
         _check(self.L.orc_run(_code(lat), S, nx, ny, _dptr(tau), reaction.code, reaction.kappa,
                               reaction.F, reaction.k, int(nsteps), _dptr(f), _dptr(tmp)))
         return f

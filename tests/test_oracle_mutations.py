@@ -33,6 +33,10 @@ PINS = [
     ("P_decay", pins.test_gs_P_decay_eq_reac_diff21, ()),
     ("fixed_points", pins.test_gs_steady_states_are_fixed_points, ()),
     ("growth", pins.test_linear_growth_rate_vs_exact_symbol, ("-", 2.0, 22, "turing", (1e-6, 1e-6), 300, 200)),
+    ("net_linear", pins.test_network_transformation_equals_linear_kind_bitwise, ()),
+    ("net_gs", pins.test_network_gray_scott_matches_eqs_reac_diff10_11, ()),
+    ("net_euler3", pins.test_network_three_species_uniform_field_is_forward_euler, ()),
+    ("net_cycle", pins.test_network_conservative_cycle_keeps_total_mass, ()),
 ]
 
 MUTATIONS = {
@@ -48,6 +52,10 @@ MUTATIONS = {
     "linear_product_sign": ("R[1] = kappa * rho[0];", "R[1] = -kappa * rho[0];"),
     "velocity_table": ("{0, 0, 1, 0, -1, 1, 1, -1, -1}", "{0, 0, 1, 0, -1, 1, -1, -1, 1}"),
     "init_weight": ("f[at(nx, ny, Q, s, i, y, x)] = w[i] * rho0", "f[at(nx, ny, Q, s, i, y, x)] = w[0] * rho0"),
+    "network_order_off_by_one": ("for (e = 0; e < src->order[r][j]; ++e)", "for (e = 0; e <= src->order[r][j]; ++e)"),
+    "network_change_sign": ("R[s] = R[s] + (double)src->change[r][s] * p;", "R[s] = R[s] - (double)src->change[r][s] * p;"),
+    "network_species_index": ("p = p * rho[j];", "p = p * rho[0];"),
+    "network_rate_dropped": ("double p = src->rate[r];", "double p = 1.0;"),
 }
 
 

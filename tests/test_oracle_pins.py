@@ -531,3 +531,137 @@ def test_point_source_decay_error_is_kappa_squared_t():
         e = _point_source_error(L, D, kappa, t)
         amp = abs(1.0 - (1.0 - kappa) ** t * math.exp(kappa * t))
         assert e == pytest.approx(amp, rel=0.05), (kappa, e, amp)
+
+
+# ---------------------------------------------------------------------------
+# Mass-action networks (Eq. reac_diff1 for N species, built from reaction
+# steps like those of Sec. III: U + 2V -> 3V, V -> P, feed and removal)
+# ---------------------------------------------------------------------------
+
+def _mass_action_R(rates, order, change, rho):
+    """R_s = sum_r change[r][s] k_r prod_j rho_j^order[r][j], written out with
+    numpy powers (the test's own evaluation)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    R = np.zeros_like(rho)
+    for kr, a, nu in zip(rates, order, change):
+        p = kr * np.prod([rho[j] ** a[j] for j in range(len(a))], axis=0)
+        for s in range(len(nu)):
+            R[s] = R[s] + nu[s] * p
+    return R
+
+
+GS_NET = dict(order=[(1, 2), (0, 0), (1, 0), (0, 1)], change=[(-1, 1), (1, 0), (-1, 0), (0, -1)])
+
+
+def _gs_network(F, k):
+    return Reaction.network([1.0, F, F, F + k], GS_NET["order"], GS_NET["change"])
+
+
+def test_network_transformation_equals_linear_kind_bitwise():
+    """A -> B as a one-step network evaluates -kappa rho_A and +kappa rho_A
+    exactly as the transformation source does."""
+    rng = np.random.default_rng(11)
+    rho0 = 1.0 + 0.3 * rng.random((2, 12, 17))
+    taus = [0.8, 1.3]
+    net = Reaction.network([0.02], [(1, 0)], [(-1, 1)])
+    a = orc.run("D2Q9", taus, net, orc.init("D2Q9", rho0), 40)
+    b = orc.run("D2Q9", taus, Reaction("linear", kappa=0.02), orc.init("D2Q9", rho0), 40)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_network_gray_scott_matches_eqs_reac_diff10_11():
+    """Gray-Scott from its reaction steps (U + 2V -> 3V at rate 1, feed of U
+    at F, removal of U at F, V -> P at F + k) gives R_u = -u v^2 + F (1 - u),
+    R_v = u v^2 - (F + k) v up to rounding, and the same trajectory."""
+    F, k = 0.04, 0.06
+    rng = np.random.default_rng(12)
+    rho = rng.random((2, 50))
+    R = np.stack([orc.default().reaction(_gs_network(F, k), rho[:, j]) for j in range(rho.shape[1])], axis=1)
+    u, v = rho
+    np.testing.assert_allclose(R[0], -u * v * v + F * (1 - u), rtol=1e-13, atol=1e-16)
+    np.testing.assert_allclose(R[1], u * v * v - (F + k) * v, rtol=1e-13, atol=1e-16)
+    rho0 = inputs.rho0_square(32, 32, seed=3, side=8)
+    taus = [float(t) for t in orc.tau_from_diffusion(np.array([0.1, 0.05]))]
+    a = orc.density("D2Q9", orc.run("D2Q9", taus, _gs_network(F, k), orc.init("D2Q9", rho0), 200))
+    b = orc.density("D2Q9", orc.run("D2Q9", taus, Reaction("gray_scott", F=F, k=k), orc.init("D2Q9", rho0), 200))
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-12)
+
+
+def test_network_three_species_uniform_field_is_forward_euler():
+    """A uniform field does not stream: rho(t + 1) = rho + R(rho), the forward
+    Euler step of the kinetics (A + B <-> C, C -> 0, 0 -> A, 2 B -> B)."""
+    rates = [0.3, 0.05, 0.02, 0.01, 0.07]
+    order = [(1, 1, 0), (0, 0, 1), (0, 0, 1), (0, 0, 0), (0, 2, 0)]
+    change = [(-1, -1, 1), (1, 1, -1), (0, 0, -1), (1, 0, 0), (0, -1, 0)]
+    net = Reaction.network(rates, order, change)
+    r = np.array([0.7, 0.4, 0.2])
+    f = orc.init("D2Q9", np.broadcast_to(r[:, None, None], (3, 5, 6)).copy())
+    taus = [0.7, 0.9, 1.4]
+    for _ in range(30):
+        f = orc.step("D2Q9", taus, net, f)
+        r = r + _mass_action_R(rates, order, change, r)
+        np.testing.assert_allclose(orc.density("D2Q9", f)[:, 2, 3], r, rtol=1e-13)
+
+
+def test_network_conservative_cycle_keeps_total_mass():
+    """Four species in a cycle A -> B -> C -> D -> A plus 2 A -> A + B: every
+    step has sum_s nu_rs = 0, so the total over species is conserved while
+    each species' own mass changes."""
+    rates = [0.02, 0.03, 0.05, 0.01, 0.04]
+    order = [(1, 0, 0, 0), (0, 1, 0, 0), (0, 0, 1, 0), (0, 0, 0, 1), (2, 0, 0, 0)]
+    change = [(-1, 1, 0, 0), (0, -1, 1, 0), (0, 0, -1, 1), (1, 0, 0, -1), (-1, 1, 0, 0)]
+    net = Reaction.network(rates, order, change)
+    rng = np.random.default_rng(13)
+    rho0 = 0.5 + rng.random((4, 20, 24))
+    f = orc.run("D2Q5", [0.6, 0.8, 1.0, 1.7], net, orc.init("D2Q5", rho0), 150)
+    m0, m1 = rho0.sum(axis=(1, 2)), orc.density("D2Q5", f).sum(axis=(1, 2))
+    assert m1.sum() == pytest.approx(m0.sum(), rel=1e-13)
+    assert np.max(np.abs(m1 - m0)) > 1.0
+
+
+def test_network_three_species_mode_growth_matches_symbol():
+    """A small cosine mode about a uniform state of a linear three-species
+    network (A -> B -> C -> A) evolves with the leading eigenvalue of the
+    3Q x 3Q linearised step (the exact amplification matrix)."""
+    rates = [0.03, 0.02, 0.05]
+    order = [(1, 0, 0), (0, 1, 0), (0, 0, 1)]
+    change = [(-1, 1, 0), (0, -1, 1), (1, 0, -1)]
+    net = Reaction.network(rates, order, change)
+    J = np.zeros((3, 3))
+    for kr, a, nu in zip(rates, order, change):
+        j = int(np.argmax(a))
+        for s in range(3):
+            J[s, j] += nu[s] * kr
+    L, n = 64, 3
+    taus = [0.9, 0.7, 1.2]
+    x = np.arange(L)
+    base = np.array([1.0, 1.5, 0.6])  # J base = 0: 0.03 = 0.02 * 1.5 = 0.05 * 0.6
+    vec = np.array([1.0, -0.4, 0.3])
+    rho0 = base[:, None, None] + 1e-6 * vec[:, None, None] * np.cos(2 * np.pi * n * x / L)[None, None, :]
+    rho0 = np.broadcast_to(rho0, (3, 4, L)).copy()
+    kvec = (2 * np.pi * n / L, 0.0)
+    lam = np.max(np.abs(np.linalg.eigvals(orc.lb_symbol("D2Q9", taus, J, kvec))))
+    f = orc.init("D2Q9", rho0)
+    amps = []
+    for t in range(400):
+        f = orc.step("D2Q9", taus, net, f)
+        if t >= 200:
+            d = orc.density("D2Q9", f)[0, 0] - base[0]
+            amps.append(np.abs(np.fft.rfft(d)[n]))
+    rate = (amps[-1] / amps[0]) ** (1.0 / (len(amps) - 1))
+    assert rate == pytest.approx(lam, rel=1e-6)
+
+
+def test_network_schnakenberg_fixed_point():
+    """Schnakenberg kinetics u' = c (a - u + u^2 v), v' = c (b - u^2 v) from
+    its steps (0 -> U at c a, U -> 0 at c, 2U + V -> 3U at c, 0 -> V at c b):
+    the uniform state u = a + b, v = b / (a + b)^2 is a fixed point of the
+    step (c = 0.05 keeps the per-step Euler map stable there, so rounding does
+    not grow)."""
+    a, b, c = 0.1, 0.9, 0.05
+    net = Reaction.network([c * a, c, c, c * b], [(0, 0), (1, 0), (2, 1), (0, 0)], [(1, 0), (-1, 0), (1, -1), (0, 1)])
+    u, v = a + b, b / (a + b) ** 2
+    f = orc.init("D2Q9", np.stack([np.full((6, 7), u), np.full((6, 7), v)]))
+    f = orc.run("D2Q9", [0.8, 1.1], net, f, 50)
+    rho = orc.density("D2Q9", f)
+    assert np.max(np.abs(rho[0] - u)) < 1e-13 and np.max(np.abs(rho[1] - v)) < 1e-13
