@@ -380,6 +380,69 @@ def truncation_mode(args):
     return 0
 
 
+def network_mode(args):
+    """gs2x_8192: four species (two Gray-Scott pairs exchanging v) as a
+    mass-action network of 10 steps, FP32, through the general kernel (one
+    thread per site), K steps timed with CUDA events on the launching stream."""
+    import torch
+    from paper_1007_3109_gb300 import binding as B
+    torch.cuda.set_device(0)
+    w = inputs.WORKLOADS["gs2x_8192"]
+    n = args.n or w["nx"]
+    S = w["nspecies"]
+    taus = [float(B.lb_rd_tau_from_diffusion(D)) for D in w["D"]]
+    net = inputs.coupled_gs_network()
+    prec = args.precision if args.precision in ("fp32", "fp64") else "fp32"
+    rho0 = inputs.initial_density("gs2x_8192", nx=n, ny=n)
+    stream = torch.cuda.current_stream()
+    sim = B.Simulation("D2Q9", S, n, n, taus, "mass_action", precision=prec, track_mass=True,
+                       stream=stream.cuda_stream, network=net)
+    sim.init(torch.from_numpy(rho0).cuda())
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    launches0 = B.lb_rd_launch_count(sim.h)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clocks:
+        ev0.record(stream)
+        B.lb_rd_step(sim.h, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = B.lb_rd_launch_count(sim.h) - launches0
+    mass = sim.mass()
+    assert np.all(np.isfinite(mass))
+    sim.close()
+    bps = S * 9 * (8 if prec == "fp64" else 4) * 2
+    peak, peak_kind = measured_peaks()
+    achieved = bps * n * n / (ms / 1e3 / args.steps) / 1e9
+    line = {"metric": "MLUPS", "value": S * n * n * args.steps / (ms / 1e3) / 1e6,
+            "unit": "MLUPS (species-site updates/s / 1e6)", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": "gs2x_8192", "nx": n, "ny": n, "species": S, "reaction_steps": len(net[0]),
+                       "precision": prec, "variant": "general",
+                       "l2": f"no flush: two state copies of {bps * n * n / 1e9:.1f} GB >> 129 MB L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": f"step_general_kernel<{prec}, Q9, S{S}>",
+                         "bytes_per_site_per_launch": bps, "peak_kind": peak_kind},
+            "gpu_launches": int(launches), "clocks": clocks.summary()}
+    if not args.no_cpu:
+        import oracle as orc
+        from oracle import Reaction
+        win = args.cpu_window // 2
+        r0 = np.ascontiguousarray(rho0[:, :win, :win])
+        reac = Reaction.network(*net)
+        f = orc.init("D2Q9", r0)
+        t0 = time.perf_counter()
+        orc.run("D2Q9", taus, reac, f, args.cpu_steps)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": S * win * win * args.cpu_steps / dt / 1e6, "unit": "MLUPS",
+                                "cores": orc.threads(), "kind": "oracle",
+                                "sample": f"{win}x{win} periodic window, {args.cpu_steps} FP64 oracle steps"}
+    print(json.dumps(line))
+    return 0
+
+
 def phase_mode(args):
     """gs_sweep_256 as a phase diagram (Sec. III.B-D, Fig. 6): the 1024-instance
     (F, k) sweep for its full 10000 steps in one batch per storage format;
@@ -431,7 +494,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--tune-iters", type=int, default=10)
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serving", "truncation", "phase"])
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serving", "truncation", "phase", "network"])
     ap.add_argument("--phase-steps", type=int, default=10000)
     ap.add_argument("--variant", default="", help="force a launch variant by name (after the autotune sweep)")
     ap.add_argument("--instances", type=int, default=0)
@@ -455,6 +518,8 @@ def main():
         return truncation_mode(args)
     if args.mode == "phase":
         return phase_mode(args)
+    if args.mode == "network":
+        return network_mode(args)
 
     import torch
     from paper_1007_3109_gb300 import binding as B

@@ -83,32 +83,51 @@ typedef enum {
     LB_RD_FP32_FP16DEV = 3
 } lb_rd_precision;
 
+/* Species and reaction-step capacity of one simulation. */
+#define LB_RD_MAX_SPECIES 4
+#define LB_RD_MAX_REACTIONS 16
+
 /* Reactions R_s(rho).
  *  NONE:        R = 0 (pure diffusion).
  *  LINEAR:      transformation A -> B at rate kappa (Sec. II.B):
  *               R_A = -kappa rho_A; with a second species R_B = +kappa rho_A.
+ *               1 or 2 species.
  *  GRAY_SCOTT:  2 species u = A, v = B, Eqs. reac_diff10/11 with
  *               A0 = k1 = 1, k_f = k_0 = F, k_2 = k:
- *               R_u = -u v^2 + F (1 - u),  R_v = u v^2 - (F + k) v. */
+ *               R_u = -u v^2 + F (1 - u),  R_v = u v^2 - (F + k) v.
+ *  MASS_ACTION: a network of nreactions reaction steps among the species
+ *               (Eq. reac_diff1 is written for N species; the paper's systems
+ *               are built from such steps, e.g. U + 2V -> 3V, V -> P): step r
+ *               proceeds at rate_r = rate[r] prod_j rho_j^order[r][j] and
+ *               changes species s by change[r][s] per event, so
+ *               R_s = sum_r change[r][s] rate_r.  FP64 evaluates
+ *               p = rate[r], p = p * rho_j (order[r][j] times, j ascending),
+ *               R_s = R_s + change[r][s] * p (steps in order, zero changes
+ *               skipped), every operation rounded on its own. */
 typedef enum {
     LB_RD_REACTION_NONE = 0,
     LB_RD_REACTION_LINEAR = 1,
-    LB_RD_REACTION_GRAY_SCOTT = 2
+    LB_RD_REACTION_GRAY_SCOTT = 2,
+    LB_RD_REACTION_MASS_ACTION = 3
 } lb_rd_reaction_kind;
 
 typedef struct {
-    int32_t kind; /* lb_rd_reaction_kind */
-    double kappa; /* LINEAR rate */
-    double F;     /* GRAY_SCOTT feed rate */
-    double k;     /* GRAY_SCOTT kill rate */
+    int32_t kind;       /* lb_rd_reaction_kind */
+    double kappa;       /* LINEAR rate */
+    double F;           /* GRAY_SCOTT feed rate */
+    double k;           /* GRAY_SCOTT kill rate */
+    int32_t nreactions; /* MASS_ACTION: number of steps, 1 .. LB_RD_MAX_REACTIONS */
+    double rate[LB_RD_MAX_REACTIONS];                      /* rate constants, finite, >= 0 */
+    int8_t order[LB_RD_MAX_REACTIONS][LB_RD_MAX_SPECIES];  /* reactant exponents, 0 .. 3 */
+    int8_t change[LB_RD_MAX_REACTIONS][LB_RD_MAX_SPECIES]; /* net change per event, -4 .. 4 */
 } lb_rd_reaction;
 
 /* One simulation: the paper's statement of the problem. */
 typedef struct {
     int32_t lattice;         /* lb_rd_lattice */
-    int32_t nspecies;        /* 1 or 2 (GRAY_SCOTT needs 2) */
+    int32_t nspecies;        /* 1 .. LB_RD_MAX_SPECIES (GRAY_SCOTT needs 2, LINEAR at most 2) */
     int64_t nx, ny;          /* periodic grid, 1 .. 65535 each */
-    double tau[2];           /* relaxation time per species, > 1/2 (D = (tau - 1/2)/3) */
+    double tau[LB_RD_MAX_SPECIES]; /* relaxation time per species, > 1/2 (D = (tau - 1/2)/3) */
     lb_rd_reaction reaction;
     int32_t precision;       /* lb_rd_precision */
     int32_t track_mass;      /* nonzero: every step also reduces sum_x rho_s in FP64 */

@@ -59,7 +59,7 @@
 #define ORC_OK 0
 #define ORC_EINVAL 1
 #define ORC_MAX_S 4
-#define ORC_MAX_R 8
+#define ORC_MAX_R 16
 
 /* A reaction source: kind 0..2 with (kappa, F, k), or kind 3 with a network
  * (order[r][s] = a_rs >= 0, change[r][s] = nu_rs). */

@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EPENDING", 5:
 LATTICES = {"D2Q9": 0, "D2Q5": 1}
 Q_OF = {"D2Q9": 9, "D2Q5": 5}
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_bf16dev": 2, "fp32_fp16dev": 3}
-REACTIONS = {"none": 0, "linear": 1, "gray_scott": 2}
+REACTIONS = {"none": 0, "linear": 1, "gray_scott": 2, "mass_action": 3}
 
 
 class LbRdError(RuntimeError):
@@ -37,13 +37,19 @@ class LbRdError(RuntimeError):
         self.status = status
 
 
+MAX_SPECIES, MAX_REACTIONS = 4, 16
+
+
 class lb_rd_reaction(ctypes.Structure):
-    _fields_ = [("kind", c_int32), ("kappa", c_double), ("F", c_double), ("k", c_double)]
+    _fields_ = [("kind", c_int32), ("kappa", c_double), ("F", c_double), ("k", c_double),
+                ("nreactions", c_int32), ("rate", c_double * MAX_REACTIONS),
+                ("order", (ctypes.c_int8 * MAX_SPECIES) * MAX_REACTIONS),
+                ("change", (ctypes.c_int8 * MAX_SPECIES) * MAX_REACTIONS)]
 
 
 class lb_rd_config(ctypes.Structure):
     _fields_ = [("lattice", c_int32), ("nspecies", c_int32), ("nx", c_int64), ("ny", c_int64),
-                ("tau", c_double * 2), ("reaction", lb_rd_reaction), ("precision", c_int32),
+                ("tau", c_double * MAX_SPECIES), ("reaction", lb_rd_reaction), ("precision", c_int32),
                 ("track_mass", c_int32), ("stream", c_void_p)]
 
 
@@ -130,16 +136,33 @@ def _ptr(buf, writable: bool = False):
 
 
 def make_config(lattice="D2Q9", nspecies=1, nx=64, ny=64, tau=(1.0, 1.0), reaction="none", kappa=0.0, F=0.0,
-                k=0.0, precision="fp32", track_mass=False, stream=None) -> lb_rd_config:
+                k=0.0, precision="fp32", track_mass=False, stream=None, network=None) -> lb_rd_config:
+    """Config struct.  ``network`` = (rates, order, change) for
+    reaction="mass_action": rate constants per step and the per-step
+    reactant exponents and net changes per species (lists of rows)."""
     cfg = lb_rd_config()
     cfg.lattice = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
     cfg.nspecies = int(nspecies)
     cfg.nx, cfg.ny = int(nx), int(ny)
     taus = [float(t) for t in np.atleast_1d(tau)]
-    taus += [1.0] * (2 - len(taus))
-    cfg.tau[0], cfg.tau[1] = float(taus[0]), float(taus[1])
+    if len(taus) > MAX_SPECIES:
+        raise ValueError(f"at most {MAX_SPECIES} relaxation times")
+    taus += [1.0] * (MAX_SPECIES - len(taus))
+    for s, t in enumerate(taus):
+        cfg.tau[s] = t
     cfg.reaction.kind = REACTIONS[reaction] if isinstance(reaction, str) else int(reaction)
     cfg.reaction.kappa, cfg.reaction.F, cfg.reaction.k = float(kappa), float(F), float(k)
+    if network is not None:
+        rates, order, change = network
+        if len(rates) > MAX_REACTIONS or len(order) != len(rates) or len(change) != len(rates):
+            raise ValueError(f"a network has 1 .. {MAX_REACTIONS} steps with one order and change row each")
+        cfg.reaction.nreactions = len(rates)
+        for r, (kr, a, nu) in enumerate(zip(rates, order, change)):
+            cfg.reaction.rate[r] = float(kr)
+            for j, x in enumerate(a):
+                cfg.reaction.order[r][j] = int(x)
+            for j, x in enumerate(nu):
+                cfg.reaction.change[r][j] = int(x)
     cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     cfg.track_mass = 1 if track_mass else 0
     cfg.stream = stream
@@ -478,8 +501,9 @@ class Simulation:
     """Owner of one lb_rd handle (a convenience over the functions above)."""
 
     def __init__(self, lattice="D2Q9", nspecies=1, nx=64, ny=64, tau=(1.0, 1.0), reaction="none", kappa=0.0,
-                 F=0.0, k=0.0, precision="fp32", track_mass=False, stream=None):
-        self.cfg = make_config(lattice, nspecies, nx, ny, tau, reaction, kappa, F, k, precision, track_mass, stream)
+                 F=0.0, k=0.0, precision="fp32", track_mass=False, stream=None, network=None):
+        self.cfg = make_config(lattice, nspecies, nx, ny, tau, reaction, kappa, F, k, precision, track_mass, stream,
+                               network)
         self.lattice = lattice
         self.S, self.nx, self.ny = int(nspecies), int(nx), int(ny)
         self.Q = Q_OF[lattice] if isinstance(lattice, str) else (9 if lattice == 0 else 5)

@@ -133,19 +133,25 @@ size_t mass_partials_needed(int64_t nx, int64_t ny) {
     return (size_t)g.x * g.y;
 }
 
+template <typename T>
+static cudaError_t mass_dispatch(int S, const T *r, dim3 g, dim3 b, int64_t nx, int64_t ny, int64_t pitch,
+                                 double *partials, unsigned int *counter, double *mass, cudaStream_t st) {
+    switch (S) {
+        case 1: mass_kernel<T, 1><<<g, b, 0, st>>>(r, nx, ny, pitch, partials, counter, mass); break;
+        case 2: mass_kernel<T, 2><<<g, b, 0, st>>>(r, nx, ny, pitch, partials, counter, mass); break;
+        case 3: mass_kernel<T, 3><<<g, b, 0, st>>>(r, nx, ny, pitch, partials, counter, mass); break;
+        case 4: mass_kernel<T, 4><<<g, b, 0, st>>>(r, nx, ny, pitch, partials, counter, mass); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_mass(int prec, int S, const void *rho, int64_t nx, int64_t ny, int64_t pitch, double *partials,
                         unsigned int *counter, double *mass, cudaStream_t st) {
     const dim3 g = mass_grid(nx, ny), b(kMassNT);
-    if (prec == LB_RD_FP64) {
-        const double *r = static_cast<const double *>(rho);
-        if (S == 1) mass_kernel<double, 1><<<g, b, 0, st>>>(r, nx, ny, pitch, partials, counter, mass);
-        else mass_kernel<double, 2><<<g, b, 0, st>>>(r, nx, ny, pitch, partials, counter, mass);
-    } else {
-        const float *r = static_cast<const float *>(rho);
-        if (S == 1) mass_kernel<float, 1><<<g, b, 0, st>>>(r, nx, ny, pitch, partials, counter, mass);
-        else mass_kernel<float, 2><<<g, b, 0, st>>>(r, nx, ny, pitch, partials, counter, mass);
-    }
-    return cudaGetLastError();
+    if (prec == LB_RD_FP64) return mass_dispatch<double>(S, static_cast<const double *>(rho), g, b, nx, ny, pitch,
+                                                         partials, counter, mass, st);
+    return mass_dispatch<float>(S, static_cast<const float *>(rho), g, b, nx, ny, pitch, partials, counter, mass, st);
 }
 
 }  // namespace lbrd

@@ -45,6 +45,12 @@ int64_t pitch_for(int64_t nx) { return (nx + kPitchAlign - 1) / kPitchAlign * kP
 
 size_t rho_elem(int prec) { return prec == LB_RD_FP64 ? 8 : 4; }
 
+// Configurations the specialised kernels do not cover run the general kernel
+// (one thread per site, up to four species, mass-action networks).
+bool needs_general(const lb_rd_config &c) {
+    return c.nspecies > 2 || c.reaction.kind == LB_RD_REACTION_MASS_ACTION;
+}
+
 }  // namespace
 
 namespace lbrd {
@@ -77,6 +83,7 @@ struct lb_rd_handle {
     int inject_timeout = 0;  // one-shot test switch for the bounded-wait error path
     int variant = 0;      // single-step launch variant of the step kernel
     int tb_variant = -1;  // two-step (temporal blocking) variant, or -1
+    bool general = false; // runs the general kernel (no launch variants)
 };
 
 namespace {
@@ -95,13 +102,18 @@ int variant_count(int prec) {
     return prec == LB_RD_FP32 ? lbrd::kF32VariantCount : (prec == LB_RD_FP64 ? 1 : lbrd::kHalfVariantCount);
 }
 
-int variant_steps(int prec, int v) { return prec == LB_RD_FP32 ? lbrd::kF32Variants[v].steps : 1; }
+int handle_variant_count(const lb_rd_handle *h) { return h->general ? 1 : variant_count(h->prec); }
+
+int variant_steps(const lb_rd_handle *h, int v) {
+    return h->prec == LB_RD_FP32 && !h->general ? lbrd::kF32Variants[v].steps : 1;
+}
 
 bool variant_fits(const lb_rd_handle *h, int v) {
-    return h->prec != LB_RD_FP32 || h->cfg.nx % lbrd::kF32Variants[v].nx_multiple == 0;
+    return h->general || h->prec != LB_RD_FP32 || h->cfg.nx % lbrd::kF32Variants[v].nx_multiple == 0;
 }
 
 cudaError_t launch_step(const lb_rd_handle *h, const lbrd::StepArgs &a, int variant) {
+    if (h->general) return lbrd::launch_step_general(h->prec == LB_RD_FP64 ? 0 : 1, h->Q, h->S, a, h->stream);
     switch (h->prec) {
         case LB_RD_FP64: return lbrd::launch_step_f64(h->Q, h->S, a, h->stream);
         case LB_RD_FP32: return lbrd::launch_step_f32_variant(variant, h->Q, h->S, a, h->stream);
@@ -123,25 +135,46 @@ int lb_rd_check_config(const lb_rd_config *cfg, size_t *bytes) {
     if (!cfg) return fail(LB_RD_EINVAL, "config is NULL");
     const int Q = lattice_q(cfg->lattice);
     if (!Q) return fail(LB_RD_EINVAL, "lattice: unknown value " + std::to_string(cfg->lattice));
-    if (cfg->nspecies < 1 || cfg->nspecies > 2)
-        return fail(LB_RD_EINVAL, "nspecies must be 1 or 2, got " + std::to_string(cfg->nspecies));
+    if (cfg->nspecies < 1 || cfg->nspecies > LB_RD_MAX_SPECIES)
+        return fail(LB_RD_EINVAL, "nspecies must be in [1, 4], got " + std::to_string(cfg->nspecies));
     if (cfg->nx < 1 || cfg->ny < 1 || cfg->nx > kMaxSide || cfg->ny > kMaxSide)
         return fail(LB_RD_EINVAL, "nx and ny must be in [1, 65535]");
     for (int s = 0; s < cfg->nspecies; ++s)
         if (!(cfg->tau[s] > 0.5) || !(cfg->tau[s] < 1e6))
             return fail(LB_RD_EINVAL, "tau[" + std::to_string(s) + "] must be in (1/2, 1e6) (D = (tau - 1/2)/3 > 0)");
     const lb_rd_reaction &r = cfg->reaction;
-    if (r.kind < LB_RD_REACTION_NONE || r.kind > LB_RD_REACTION_GRAY_SCOTT)
+    if (r.kind < LB_RD_REACTION_NONE || r.kind > LB_RD_REACTION_MASS_ACTION)
         return fail(LB_RD_EINVAL, "reaction.kind: unknown value " + std::to_string(r.kind));
     if (r.kind == LB_RD_REACTION_GRAY_SCOTT && cfg->nspecies != 2)
         return fail(LB_RD_EINVAL, "Gray-Scott needs nspecies = 2");
+    if (r.kind == LB_RD_REACTION_LINEAR && cfg->nspecies > 2)
+        return fail(LB_RD_EINVAL, "the transformation A -> B takes 1 or 2 species (use a mass-action network)");
+    if (r.kind == LB_RD_REACTION_MASS_ACTION) {
+        if (r.nreactions < 1 || r.nreactions > LB_RD_MAX_REACTIONS)
+            return fail(LB_RD_EINVAL, "reaction.nreactions must be in [1, 16]");
+        for (int q = 0; q < r.nreactions; ++q) {
+            const std::string at = "reaction step " + std::to_string(q) + ": ";
+            if (!(r.rate[q] >= 0.0) || !(r.rate[q] < 1e300)) return fail(LB_RD_EINVAL, at + "rate must be finite and >= 0");
+            for (int j = 0; j < LB_RD_MAX_SPECIES; ++j) {
+                const bool used = j < cfg->nspecies;
+                if (r.order[q][j] < 0 || r.order[q][j] > 3 || (!used && r.order[q][j] != 0))
+                    return fail(LB_RD_EINVAL, at + "order must be in [0, 3] (0 for species beyond nspecies)");
+                if (r.change[q][j] < -4 || r.change[q][j] > 4 || (!used && r.change[q][j] != 0))
+                    return fail(LB_RD_EINVAL, at + "change must be in [-4, 4] (0 for species beyond nspecies)");
+            }
+        }
+    }
     if (cfg->precision < LB_RD_FP64 || cfg->precision > LB_RD_FP32_FP16DEV)
         return fail(LB_RD_EINVAL, "precision: unknown value " + std::to_string(cfg->precision));
+    if (needs_general(*cfg) && cfg->precision != LB_RD_FP64 && cfg->precision != LB_RD_FP32)
+        return fail(LB_RD_EINVAL, "more than two species or a mass-action network: FP64 or FP32 storage only");
     if (bytes) {
         const int64_t pitch = pitch_for(cfg->nx);
         const size_t st = lbrd::state_plane_bytes(cfg->precision, Q, cfg->nspecies, cfg->ny, pitch);
         const size_t rb = (size_t)cfg->nspecies * cfg->ny * pitch * rho_elem(cfg->precision);
-        *bytes = 2 * st + rb + (size_t)lbrd::max_persistent_blocks() * 2 * sizeof(double) + 64;
+        const size_t np1 = lbrd::max_persistent_blocks(), np2 = lbrd::mass_partials_needed(cfg->nx, cfg->ny);
+        *bytes = 2 * st + rb + (np1 > np2 ? np1 : np2) * cfg->nspecies * sizeof(double) +
+                 LB_RD_MAX_SPECIES * sizeof(double) + 2 * sizeof(int);
     }
     return LB_RD_OK;
 }
@@ -180,6 +213,7 @@ int lb_rd_create(const lb_rd_config *cfg, lb_rd_handle **out) {
     h->Q = lattice_q(cfg->lattice);
     h->S = cfg->nspecies;
     h->prec = cfg->precision;
+    h->general = needs_general(*cfg);
     h->pitch = pitch_for(cfg->nx);
     h->plane = cfg->ny * h->pitch;
     h->stream = static_cast<cudaStream_t>(cfg->stream);
@@ -194,7 +228,7 @@ int lb_rd_create(const lb_rd_config *cfg, lb_rd_handle **out) {
     if (!err) err = cudaMalloc(&h->rho, h->rho_bytes);
     if (!err) err = cudaMalloc(&h->partials, parts * sizeof(double));
     if (!err) err = cudaMalloc(&h->counter, sizeof(unsigned int));
-    if (!err) err = cudaMalloc(&h->mass, 2 * sizeof(double));
+    if (!err) err = cudaMalloc(&h->mass, LB_RD_MAX_SPECIES * sizeof(double));
     if (!err) err = cudaMalloc(&h->status, sizeof(int));
     if (!err) err = cudaMemset(h->status, 0, sizeof(int));
     if (!err) err = cudaMemset(h->counter, 0, sizeof(unsigned int));
@@ -206,7 +240,7 @@ int lb_rd_create(const lb_rd_config *cfg, lb_rd_handle **out) {
         lb_rd_destroy(h);
         return rc;
     }
-    {
+    if (!h->general) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(tune_key(h));
         if (it != g_tune_cache.end()) {
@@ -231,13 +265,6 @@ static int ensure_stage(lb_rd_handle *h, size_t elems) {
     return LB_RD_OK;
 }
 
-static void fill_common(const lb_rd_handle *h, double omega[2], int *rkind, double *kappa, double *F, double *k) {
-    for (int s = 0; s < 2; ++s) omega[s] = s < h->S ? 1.0 / h->cfg.tau[s] : 0.0;
-    *rkind = h->cfg.reaction.kind;
-    *kappa = h->cfg.reaction.kappa;
-    *F = h->cfg.reaction.F;
-    *k = h->cfg.reaction.k;
-}
 
 int lb_rd_init(lb_rd_handle *h, const double *rho0, int is_device) {
     if (!h || !rho0) return fail(LB_RD_EINVAL, "handle or rho0 is NULL");
@@ -257,10 +284,11 @@ int lb_rd_init(lb_rd_handle *h, const double *rho0, int is_device) {
     a.ny = h->cfg.ny;
     a.pitch = h->pitch;
     a.plane = h->plane;
-    fill_common(h, a.omega, &a.rkind, &a.kappa, &a.F, &a.k);
+    lbrd::fill_reaction(h->cfg, a.omega, &a.rkind, &a.kappa, &a.F, &a.k, &a.net);
     a.rho_out = h->rho;
     cudaError_t e;
-    switch (h->prec) {
+    if (h->general) e = lbrd::launch_init_general(h->prec == LB_RD_FP64 ? 0 : 1, h->Q, h->S, a, h->stream);
+    else switch (h->prec) {
         case LB_RD_FP64: e = lbrd::launch_init_f64(h->Q, h->S, a, h->stream); break;
         case LB_RD_FP32: e = lbrd::launch_init_f32(h->Q, h->S, a, h->stream); break;
         default: e = lbrd::launch_init_half(h->Q, h->S, h->prec == LB_RD_FP32_FP16DEV, a, h->stream); break;
@@ -296,7 +324,7 @@ int lb_rd_step(lb_rd_handle *h, int64_t nsteps) {
     a.ny = h->cfg.ny;
     a.pitch = h->pitch;
     a.plane = h->plane;
-    fill_common(h, a.omega, &a.rkind, &a.kappa, &a.F, &a.k);
+    lbrd::fill_reaction(h->cfg, a.omega, &a.rkind, &a.kappa, &a.F, &a.k, &a.net);
     a.partials = h->partials;
     a.counter = h->counter;
     a.status = h->status;
@@ -519,6 +547,11 @@ const char *lb_rd_variant_name(int32_t precision, int32_t variant) {
 
 int lb_rd_set_variant(lb_rd_handle *h, int32_t variant) {
     if (!h) return fail(LB_RD_EINVAL, "handle is NULL");
+    if (variant == -1 && h->general) {
+        h->variant = 0;
+        h->tb_variant = -1;
+        return LB_RD_OK;
+    }
     if (variant == -1) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(tune_key(h));
@@ -526,12 +559,12 @@ int lb_rd_set_variant(lb_rd_handle *h, int32_t variant) {
         h->tb_variant = it != g_tune_cache.end() ? it->second.second : -1;
         return LB_RD_OK;
     }
-    if (variant < 0 || variant >= variant_count(h->prec))
-        return fail(LB_RD_EINVAL, "variant out of range for this precision");
+    if (variant < 0 || variant >= handle_variant_count(h))
+        return fail(LB_RD_EINVAL, "variant out of range for this configuration");
     if (!variant_fits(h, variant))
         return fail(LB_RD_EINVAL, std::string("variant ") + lb_rd_variant_name(h->prec, variant) + " needs nx to be a multiple of " +
                                       std::to_string(lbrd::kF32Variants[variant].nx_multiple));
-    if (variant_steps(h->prec, variant) == 2) {
+    if (variant_steps(h, variant) == 2) {
         h->tb_variant = variant;
     } else {
         h->variant = variant;
@@ -559,12 +592,12 @@ int lb_rd_autotune(lb_rd_handle *h, int32_t iters, int32_t *best, double *times_
     a.ny = h->cfg.ny;
     a.pitch = h->pitch;
     a.plane = h->plane;
-    fill_common(h, a.omega, &a.rkind, &a.kappa, &a.F, &a.k);
+    lbrd::fill_reaction(h->cfg, a.omega, &a.rkind, &a.kappa, &a.F, &a.k, &a.net);
     a.status = h->status;
     cudaEvent_t e0, e1;
     LBRD_CUDA(cudaEventCreate(&e0), "event create");
     LBRD_CUDA(cudaEventCreate(&e1), "event create");
-    const int n = variant_count(h->prec);
+    const int n = handle_variant_count(h);
     int best1 = -1, best2 = -1;
     double ms1 = 0.0, ms2 = 0.0;
     for (int v = 0; v < n; ++v) {
@@ -587,7 +620,7 @@ int lb_rd_autotune(lb_rd_handle *h, int32_t iters, int32_t *best, double *times_
             return cuda_fail(e, "autotune launch");
         }
         h->launches += iters + 1;
-        const int steps = variant_steps(h->prec, v);
+        const int steps = variant_steps(h, v);
         const double per = ms / iters / steps;  // per time step
         if (times_ms && v < max_times) times_ms[v] = per;
         if (steps == 1 && (best1 < 0 || per < ms1)) {
@@ -604,7 +637,7 @@ int lb_rd_autotune(lb_rd_handle *h, int32_t iters, int32_t *best, double *times_
     h->variant = best1 >= 0 ? best1 : 0;
     h->tb_variant = (best2 >= 0 && ms2 < ms1) ? best2 : -1;
     const int arg = h->tb_variant >= 0 ? h->tb_variant : h->variant;
-    {
+    if (!h->general) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tune_cache[tune_key(h)] = std::make_pair(h->variant, h->tb_variant);
     }

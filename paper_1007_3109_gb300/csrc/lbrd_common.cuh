@@ -70,7 +70,19 @@ __host__ __device__ constexpr T weight(int i) {
 // ---------------------------------------------------------------------------
 // Reactions (Sec. II.B and Sec. III)
 // ---------------------------------------------------------------------------
-enum ReactionKind : int { kNone = 0, kLinear = 1, kGrayScott = 2 };
+enum ReactionKind : int { kNone = 0, kLinear = 1, kGrayScott = 2, kMassAction = 3 };
+
+constexpr int kMaxSpecies = 4;     // species of one simulation
+constexpr int kMaxReactions = 16;  // steps of a mass-action network
+
+// Mass-action network: step r runs at rate[r] prod_j rho_j^order[r][j] and
+// changes species s by change[r][s] (Eq. reac_diff1 for N species).
+struct Network {
+    int nr;
+    double rate[kMaxReactions];
+    signed char order[kMaxReactions][kMaxSpecies];
+    signed char change[kMaxReactions][kMaxSpecies];
+};
 
 // FP32 and faster paths: plain expression, contraction allowed.
 template <int S>
@@ -116,9 +128,10 @@ struct StepArgs {
     int64_t nx, ny;
     int64_t pitch;      // row pitch in elements (a multiple of 32)
     int64_t plane;      // ny * pitch
-    double omega[2];    // 1 / tau_s
+    double omega[kMaxSpecies];  // 1 / tau_s
     int rkind;
     double kappa, F, k;
+    Network net;        // kMassAction only
     void *rho_out;      // optional rho(t + 1), [s][y][pitch] in the compute type
     double *partials;   // optional per-block mass partials [nblocks][S]
     unsigned int *counter;  // arrival counter for the last-block finalisation
@@ -133,9 +146,10 @@ struct InitArgs {
     const double *rho0;  // [S][ny][nx]
     void *dst;
     int64_t nx, ny, pitch, plane;
-    double omega[2];
+    double omega[kMaxSpecies];
     int rkind;
     double kappa, F, k;
+    Network net;
     void *rho_out;       // rho(0), [s][y][pitch]
 };
 

@@ -5,9 +5,35 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "lb_rd.h"
 #include "lbrd_common.cuh"
 
 namespace lbrd {
+
+static_assert(kMaxSpecies == LB_RD_MAX_SPECIES && kMaxReactions == LB_RD_MAX_REACTIONS, "capacities must agree");
+
+// Relaxation rates and reaction constants of a configuration in kernel form:
+// omega_s = 1 / tau_s (0 beyond nspecies) and the network of a mass-action
+// source (zeroed otherwise).
+inline void fill_reaction(const lb_rd_config &c, double *omega, int *rkind, double *kappa, double *F, double *k,
+                          Network *net) {
+    for (int s = 0; s < kMaxSpecies; ++s) omega[s] = s < c.nspecies ? 1.0 / c.tau[s] : 0.0;
+    *rkind = c.reaction.kind;
+    *kappa = c.reaction.kappa;
+    *F = c.reaction.F;
+    *k = c.reaction.k;
+    *net = Network{};
+    if (c.reaction.kind == LB_RD_REACTION_MASS_ACTION) {
+        net->nr = c.reaction.nreactions;
+        for (int r = 0; r < c.reaction.nreactions && r < kMaxReactions; ++r) {
+            net->rate[r] = c.reaction.rate[r];
+            for (int j = 0; j < kMaxSpecies; ++j) {
+                net->order[r][j] = c.reaction.order[r][j];
+                net->change[r][j] = c.reaction.change[r][j];
+            }
+        }
+    }
+}
 
 // Resident blocks per SM of a kernel at a block size (cached per device and
 // kernel) times the SM count, capped by the work.  Persistent kernels walk
@@ -26,6 +52,11 @@ unsigned max_persistent_blocks();
 struct StepShape {
     dim3 grid, block;
 };
+
+// General step: 1 .. 4 species, mass-action networks; prec 0 = FP64 (no FMA
+// contraction, bit-reproducible), otherwise FP32.  One thread per site.
+cudaError_t launch_step_general(int prec, int Q, int S, const StepArgs &a, cudaStream_t st);
+cudaError_t launch_init_general(int prec, int Q, int S, const InitArgs &a, cudaStream_t st);
 
 // FP64: one thread per site, no FMA contraction (bit-reproducible).
 StepShape step_shape_f64(int64_t nx, int64_t ny);

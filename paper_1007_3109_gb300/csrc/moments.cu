@@ -119,6 +119,11 @@ cudaError_t launch_pull_rho(int prec, int Q, int S, const void *prev_state, int6
     if (Q == 9 && S == 2) return dispatch<9, 2>(prec, prev_state, nx, ny, pitch, rho, st);
     if (Q == 5 && S == 1) return dispatch<5, 1>(prec, prev_state, nx, ny, pitch, rho, st);
     if (Q == 5 && S == 2) return dispatch<5, 2>(prec, prev_state, nx, ny, pitch, rho, st);
+    if (prec != LB_RD_FP64 && prec != LB_RD_FP32) return cudaErrorInvalidValue;  // 16-bit storage: S <= 2
+    if (Q == 9 && S == 3) return dispatch<9, 3>(prec, prev_state, nx, ny, pitch, rho, st);
+    if (Q == 9 && S == 4) return dispatch<9, 4>(prec, prev_state, nx, ny, pitch, rho, st);
+    if (Q == 5 && S == 3) return dispatch<5, 3>(prec, prev_state, nx, ny, pitch, rho, st);
+    if (Q == 5 && S == 4) return dispatch<5, 4>(prec, prev_state, nx, ny, pitch, rho, st);
     return cudaErrorInvalidValue;
 }
 

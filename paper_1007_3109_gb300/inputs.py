@@ -27,6 +27,10 @@ gs_serving         Poisson stream of Gray-Scott requests, side in
 gs_8192            Gray-Scott F = 0.037, k = 0.06, D_u = 0.1, D_v = 0.05,
                    8192^2, 256 random 16x16 spots u = 0.5, v = 0.25 on
                    u = 1, v = 0, plus U(-0.01, 0.01)
+gs2x_8192          4 species: two Gray-Scott pairs (F, k) = (0.037, 0.06)
+                   and (0.03, 0.055) exchanging v at rate 0.001, as a
+                   mass-action network of 10 steps; D = (0.1, 0.05) per
+                   pair; 8192^2, spot init per pair (seeds 1240, 1241)
 =================  =====================================================
 """
 from __future__ import annotations
@@ -161,7 +165,35 @@ WORKLOADS = {
     "gs_8192": dict(lattice="D2Q9", nspecies=2, nx=8192, ny=8192, D=(0.1, 0.05),
                     reaction=dict(kind="gray_scott", F=0.037, k=0.06), steps=10000, seed=1239,
                     init="spots"),
+    "gs2x_8192": dict(lattice="D2Q9", nspecies=4, nx=8192, ny=8192, D=(0.1, 0.05, 0.1, 0.05),
+                      reaction=dict(kind="mass_action"), steps=10000, seed=1240,
+                      init="spots2"),
 }
+
+
+def coupled_gs_network(F1=0.037, k1=0.06, F2=0.03, k2=0.055, c=0.001):
+    """Reaction steps of two Gray-Scott pairs (u1, v1, u2, v2) coupled by a
+    slow exchange of the autocatalyst, as (rates, order, change) rows:
+    U + 2V -> 3V at 1, 0 -> U at F, U -> 0 at F, V -> 0 at F + k for each pair
+    (the steps of Sec. III), then V1 -> V2 and V2 -> V1 at c."""
+    rates, order, change = [], [], []
+    for p, (F, k) in enumerate(((F1, k1), (F2, k2))):
+        u, v = 2 * p, 2 * p + 1
+        for kr, a, nu in ((1.0, {u: 1, v: 2}, {u: -1, v: 1}), (F, {}, {u: 1}), (F, {u: 1}, {u: -1}),
+                          (F + k, {v: 1}, {v: -1})):
+            rates.append(kr)
+            order.append(tuple(a.get(j, 0) for j in range(4)))
+            change.append(tuple(nu.get(j, 0) for j in range(4)))
+    rates += [c, c]
+    order += [(0, 1, 0, 0), (0, 0, 0, 1)]
+    change += [(0, -1, 0, 1), (0, 1, 0, -1)]
+    return rates, order, change
+
+
+def rho0_spots2(nx: int, ny: int, seed: int) -> np.ndarray:
+    """Two independent spot fields (``rho0_spots`` with seeds seed and
+    seed + 1), stacked as (u1, v1, u2, v2); shape (4, ny, nx)."""
+    return np.concatenate([rho0_spots(nx, ny, seed), rho0_spots(nx, ny, seed + 1)])
 
 
 def initial_density(name: str, nx: int | None = None, ny: int | None = None, seed: int | None = None) -> np.ndarray:
@@ -176,4 +208,6 @@ def initial_density(name: str, nx: int | None = None, ny: int | None = None, see
         return rho0_square(nx, ny, seed)
     if w["init"] == "spots":
         return rho0_spots(nx, ny, seed)
+    if w["init"] == "spots2":
+        return rho0_spots2(nx, ny, seed)
     raise KeyError(w["init"])

@@ -58,8 +58,18 @@ def _cfg(**kw):
 @pytest.mark.parametrize("kw,msg", [
     (dict(tau=(0.5, 0.65)), "tau[0]"),
     (dict(tau=(0.8, 0.4)), "tau[1]"),
-    (dict(nspecies=3), "nspecies"),
+    (dict(nspecies=5, tau=(0.8,) * 4), "nspecies"),
+    (dict(nspecies=3, tau=(0.8,) * 3), "Gray-Scott"),
+    (dict(nspecies=3, tau=(0.8,) * 3, reaction="linear"), "A -> B"),
+    (dict(nspecies=3, tau=(0.8, 0.7, 0.4)), "tau[2]"),
     (dict(nspecies=1, reaction="gray_scott"), "Gray-Scott"),
+    (dict(reaction="mass_action"), "nreactions"),
+    (dict(reaction="mass_action", network=([-1.0], [(1, 0)], [(-1, 1)])), "rate"),
+    (dict(reaction="mass_action", network=([1.0], [(4, 0)], [(-1, 1)])), "order"),
+    (dict(reaction="mass_action", network=([1.0], [(1, 0)], [(-5, 1)])), "change"),
+    (dict(reaction="mass_action", network=([1.0], [(1, 0, 1)], [(-1, 1, 0)])), "beyond nspecies"),
+    (dict(reaction="mass_action", network=([1.0], [(1, 0)], [(-1, 1)]), precision="fp32_bf16dev"), "FP64 or FP32"),
+    (dict(nspecies=4, tau=(0.8,) * 4, reaction="none", precision="fp32_fp16dev"), "FP64 or FP32"),
     (dict(nx=0), "nx"),
     (dict(ny=70000), "nx and ny"),
     (dict(lattice=7), "lattice"),
@@ -71,6 +81,14 @@ def test_config_validation_rejects(lib, kw, msg):
         B.lb_rd_check_config(_cfg(**kw))
     assert ei.value.status == B.LB_RD_EINVAL
     assert msg in str(ei.value)
+
+
+def test_config_validation_accepts_networks_and_four_species(lib):
+    net = ([0.3, 0.01], [(1, 1, 0, 0), (0, 0, 1, 0)], [(-1, -1, 1, 0), (0, 0, -1, 1)])
+    n4 = B.lb_rd_check_config(_cfg(nspecies=4, tau=(0.8, 0.7, 0.9, 1.2), reaction="mass_action", network=net))
+    n2 = B.lb_rd_check_config(_cfg())
+    assert n4 > 1.9 * n2
+    B.lb_rd_check_config(_cfg(nspecies=3, tau=(0.8,) * 3, reaction="none", precision="fp64"))
 
 
 def test_config_validation_accepts_and_sizes(lib):
