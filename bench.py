@@ -399,6 +399,11 @@ def network_mode(args):
                        stream=stream.cuda_stream, network=net)
     sim.init(torch.from_numpy(rho0).cuda())
     sim.step(args.warmup)
+    nvar = B.lb_rd_handle_variant_count(sim.h)
+    names = [B.lb_rd_handle_variant_name(sim.h, v) for v in range(nvar)]
+    best, times = B.lb_rd_autotune(sim.h, iters=args.tune_iters or 5)
+    tuning = {names[v]: (round(times[v], 4) if times[v] >= 0 else None) for v in range(nvar)}
+    sim.step(3)
     torch.cuda.synchronize()
     launches0 = B.lb_rd_launch_count(sim.h)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -420,10 +425,10 @@ def network_mode(args):
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": "gs2x_8192", "nx": n, "ny": n, "species": S, "reaction_steps": len(net[0]),
-                       "precision": prec, "variant": "general",
+                       "precision": prec, "variant": names[best], "autotune_ms_per_launch": tuning,
                        "l2": f"no flush: two state copies of {bps * n * n / 1e9:.1f} GB >> 129 MB L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "kernel": f"step_general_kernel<{prec}, Q9, S{S}>",
+                         "traffic": None, "kernel": f"general:{names[best]} ({prec}, D2Q9, {S} species)",
                          "bytes_per_site_per_launch": bps, "peak_kind": peak_kind},
             "gpu_launches": int(launches), "clocks": clocks.summary()}
     if not args.no_cpu:
@@ -496,6 +501,7 @@ def main():
     ap.add_argument("--tune-iters", type=int, default=10)
     ap.add_argument("--mode", default="step", choices=["step", "batch", "serving", "truncation", "phase", "network"])
     ap.add_argument("--phase-steps", type=int, default=10000)
+    ap.add_argument("--inplace", action="store_true", help="one state copy (AA streaming)")
     ap.add_argument("--variant", default="", help="force a launch variant by name (after the autotune sweep)")
     ap.add_argument("--instances", type=int, default=0)
     ap.add_argument("--requests", type=int, default=64)
@@ -544,16 +550,18 @@ def main():
     rho0 = inputs.initial_density(args.workload, nx=n, ny=n)
     stream = torch.cuda.current_stream()
     sim = B.Simulation(args.lattice, 2, n, n, taus, "gray_scott", F=F, k=k, precision=args.precision,
-                       track_mass=True, stream=stream.cuda_stream)
+                       track_mass=True, stream=stream.cuda_stream, inplace=args.inplace)
     rho0_dev = torch.from_numpy(rho0).cuda()
     sim.init(rho0_dev)
-    nvar = B.lb_rd_variant_count(args.precision)
-    names = [B.lb_rd_variant_name(args.precision, v) for v in range(nvar)]
+    nvar = B.lb_rd_handle_variant_count(sim.h)
+    names = [B.lb_rd_handle_variant_name(sim.h, v) for v in range(nvar)]
+    if args.inplace:
+        names = ["inplace_aa"]
     if args.variant:
         B.lb_rd_set_variant(sim.h, names.index(args.variant))
     sim.step(args.warmup)
     tuning = {}
-    if args.tune_iters > 0:
+    if args.tune_iters > 0 and not args.inplace:
         # project autotuner: every launch variant timed on this state (not advanced)
         best, times = B.lb_rd_autotune(sim.h, iters=args.tune_iters)
         tuning = {names[v]: (round(times[v], 4) if times[v] >= 0 else None) for v in range(nvar)}
@@ -593,7 +601,7 @@ def main():
     # so its per-launch figure is HBM use and the per-step figure exceeds it.
     achieved = bps * sites / avg_launch_s / 1e9
     effective = bps * sites * args.steps / (ms_total / 1e3) / 1e9
-    variant_name = B.lb_rd_variant_name(args.precision, best)
+    variant_name = names[best]
     traffic = None
     if os.path.exists(TRAFFIC_FILE):
         with open(TRAFFIC_FILE) as fh:
@@ -638,9 +646,10 @@ def main():
         "config": {"workload": args.workload, "lattice": args.lattice, "nx": n, "ny": n, "species": 2,
                    "precision": args.precision, "lb_steps_per_step": 1,
                    "mass_diagnostic": "fused into every launch (every step, or every second step with temporal blocking)",
-                   "l2": f"no flush: state of {2 * sim_state_bytes(args.lattice, args.precision, n) / 1e9:.2f} GB >> 129 MB L2",
+                   "l2": f"no flush: state of {(1 if args.inplace else 2) * sim_state_bytes(args.lattice, args.precision, n) / 1e9:.2f} GB >> 129 MB L2",
                    "parallelism": f"replicas x{world}",
-                   "variant": B.lb_rd_variant_name(args.precision, best), "autotune_ms_per_launch": tuning},
+                   "variant": variant_name, "autotune_ms_per_launch": tuning,
+                   "streaming": "in-place (AA), one state copy" if args.inplace else "ping-pong, two state copies"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "kernel": f"step_{args.precision}:{variant_name}",
                      "steps_per_launch": steps_per_launch, "bytes_per_site_per_launch": bps,

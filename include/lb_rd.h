@@ -122,6 +122,16 @@ typedef struct {
     int8_t change[LB_RD_MAX_REACTIONS][LB_RD_MAX_SPECIES]; /* net change per event, -4 .. 4 */
 } lb_rd_reaction;
 
+/* Storage of the state.
+ *  PINGPONG: two copies; each step pulls f*(t) from one into the other.
+ *  INPLACE:  one copy (half the device memory): steps alternate between
+ *            reading neighbours and writing the swapped slots back to them
+ *            (t even) and reading and writing a site's own slots (t odd), the
+ *            "AA" pattern; the same bits as PINGPONG.  FP64 and FP32 storage;
+ *            one launch variant; the last step of every lb_rd_step call also
+ *            writes rho.  Not for batches, servers or lb_rd_step_noalloc. */
+typedef enum { LB_RD_STREAM_PINGPONG = 0, LB_RD_STREAM_INPLACE = 1 } lb_rd_streaming;
+
 /* One simulation: the paper's statement of the problem. */
 typedef struct {
     int32_t lattice;         /* lb_rd_lattice */
@@ -131,6 +141,7 @@ typedef struct {
     lb_rd_reaction reaction;
     int32_t precision;       /* lb_rd_precision */
     int32_t track_mass;      /* nonzero: every step also reduces sum_x rho_s in FP64 */
+    int32_t streaming;       /* lb_rd_streaming */
     void *stream;            /* cudaStream_t for all work; NULL = legacy default stream */
 } lb_rd_config;
 
@@ -219,6 +230,12 @@ LB_RD_API int lb_rd_launch_count(const lb_rd_handle *h, int64_t *launches);
  * returns the variant used for the bulk of the steps. */
 LB_RD_API int lb_rd_variant_count(int32_t precision, int32_t *count);
 LB_RD_API const char *lb_rd_variant_name(int32_t precision, int32_t variant);
+/* The variants of one handle's configuration: configurations with more than
+ * two species or a mass-action network run the general kernel, whose FP32
+ * variants update 1, 2 or 4 consecutive sites per thread (nx a multiple of
+ * that) and whose FP64 form has one variant.  Bitwise-equal results. */
+LB_RD_API int lb_rd_handle_variant_count(const lb_rd_handle *h, int32_t *count);
+LB_RD_API const char *lb_rd_handle_variant_name(const lb_rd_handle *h, int32_t variant);
 LB_RD_API int lb_rd_autotune(lb_rd_handle *h, int32_t iters, int32_t *best, double *times_ms, int32_t max_times);
 LB_RD_API int lb_rd_set_variant(lb_rd_handle *h, int32_t variant);
 LB_RD_API int lb_rd_get_variant(const lb_rd_handle *h, int32_t *variant);

@@ -50,7 +50,7 @@ class lb_rd_reaction(ctypes.Structure):
 class lb_rd_config(ctypes.Structure):
     _fields_ = [("lattice", c_int32), ("nspecies", c_int32), ("nx", c_int64), ("ny", c_int64),
                 ("tau", c_double * MAX_SPECIES), ("reaction", lb_rd_reaction), ("precision", c_int32),
-                ("track_mass", c_int32), ("stream", c_void_p)]
+                ("track_mass", c_int32), ("streaming", c_int32), ("stream", c_void_p)]
 
 
 _LIB = None
@@ -76,6 +76,8 @@ _SIGNATURES = {
     "lb_rd_step_noalloc": ([POINTER(lb_rd_config), c_void_p, c_void_p, c_void_p], c_int),
     "lb_rd_variant_count": ([c_int32, POINTER(c_int32)], c_int),
     "lb_rd_variant_name": ([c_int32, c_int32], c_char_p),
+    "lb_rd_handle_variant_count": ([c_void_p, POINTER(c_int32)], c_int),
+    "lb_rd_handle_variant_name": ([c_void_p, c_int32], c_char_p),
     "lb_rd_autotune": ([c_void_p, c_int32, POINTER(c_int32), POINTER(c_double), c_int32], c_int),
     "lb_rd_set_variant": ([c_void_p, c_int32], c_int),
     "lb_rd_get_variant": ([c_void_p, POINTER(c_int32)], c_int),
@@ -136,7 +138,8 @@ def _ptr(buf, writable: bool = False):
 
 
 def make_config(lattice="D2Q9", nspecies=1, nx=64, ny=64, tau=(1.0, 1.0), reaction="none", kappa=0.0, F=0.0,
-                k=0.0, precision="fp32", track_mass=False, stream=None, network=None) -> lb_rd_config:
+                k=0.0, precision="fp32", track_mass=False, stream=None, network=None,
+                inplace=False) -> lb_rd_config:
     """Config struct.  ``network`` = (rates, order, change) for
     reaction="mass_action": rate constants per step and the per-step
     reactant exponents and net changes per species (lists of rows)."""
@@ -165,6 +168,7 @@ def make_config(lattice="D2Q9", nspecies=1, nx=64, ny=64, tau=(1.0, 1.0), reacti
                 cfg.reaction.change[r][j] = int(x)
     cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     cfg.track_mass = 1 if track_mass else 0
+    cfg.streaming = 1 if inplace else 0
     cfg.stream = stream
     return cfg
 
@@ -279,6 +283,16 @@ def lb_rd_autotune(h: int, iters: int = 20, max_times: int = 64):
     times = (c_double * max_times)()
     _check(lib().lb_rd_autotune(h, int(iters), ctypes.byref(best), times, max_times))
     return best.value, list(times)
+
+
+def lb_rd_handle_variant_count(h: int) -> int:
+    n = c_int32(0)
+    _check(lib().lb_rd_handle_variant_count(h, ctypes.byref(n)))
+    return n.value
+
+
+def lb_rd_handle_variant_name(h: int, variant: int) -> str:
+    return lib().lb_rd_handle_variant_name(h, int(variant)).decode()
 
 
 def lb_rd_set_variant(h: int, variant: int):
@@ -501,9 +515,9 @@ class Simulation:
     """Owner of one lb_rd handle (a convenience over the functions above)."""
 
     def __init__(self, lattice="D2Q9", nspecies=1, nx=64, ny=64, tau=(1.0, 1.0), reaction="none", kappa=0.0,
-                 F=0.0, k=0.0, precision="fp32", track_mass=False, stream=None, network=None):
+                 F=0.0, k=0.0, precision="fp32", track_mass=False, stream=None, network=None, inplace=False):
         self.cfg = make_config(lattice, nspecies, nx, ny, tau, reaction, kappa, F, k, precision, track_mass, stream,
-                               network)
+                               network, inplace)
         self.lattice = lattice
         self.S, self.nx, self.ny = int(nspecies), int(nx), int(ny)
         self.Q = Q_OF[lattice] if isinstance(lattice, str) else (9 if lattice == 0 else 5)

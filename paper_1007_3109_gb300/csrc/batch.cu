@@ -185,9 +185,9 @@ int lb_rd_batch_create(const lb_rd_config *cfgs, int32_t n, lb_rd_batch **out) {
     for (int i = 0; i < n; ++i) {
         int rc = lb_rd_check_config(&cfgs[i], nullptr);
         if (rc) return rc;
-        if (cfgs[i].nspecies > 2 || cfgs[i].reaction.kind == LB_RD_REACTION_MASS_ACTION)
-            return report_error(LB_RD_EINVAL, "lb_rd_batch_create: batches take at most two species and no "
-                                              "mass-action network (instance " + std::to_string(i) + ")");
+        if (cfgs[i].nspecies > 2 || cfgs[i].reaction.kind == LB_RD_REACTION_MASS_ACTION || cfgs[i].streaming != 0)
+            return report_error(LB_RD_EINVAL, "lb_rd_batch_create: batches take at most two species, no "
+                                              "mass-action network and two state copies (instance " + std::to_string(i) + ")");
         if (cfgs[i].lattice != cfgs[0].lattice || cfgs[i].nspecies != cfgs[0].nspecies ||
             cfgs[i].precision != cfgs[0].precision)
             return report_error(LB_RD_EINVAL, "lb_rd_batch_create: instance " + std::to_string(i) +

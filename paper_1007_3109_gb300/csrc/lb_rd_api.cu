@@ -83,7 +83,8 @@ struct lb_rd_handle {
     int inject_timeout = 0;  // one-shot test switch for the bounded-wait error path
     int variant = 0;      // single-step launch variant of the step kernel
     int tb_variant = -1;  // two-step (temporal blocking) variant, or -1
-    bool general = false; // runs the general kernel (no launch variants)
+    bool general = false; // runs the general kernel
+    bool inplace = false; // one state copy, AA pattern (buf[1] unused)
 };
 
 namespace {
@@ -95,25 +96,30 @@ std::map<std::tuple<int, int, int, int, int64_t, int64_t>, std::pair<int, int>> 
 std::tuple<int, int, int, int, int64_t, int64_t> tune_key(const lb_rd_handle *h) {
     int dev = 0;
     cudaGetDevice(&dev);
-    return std::make_tuple(dev, h->prec, h->Q, h->S, h->cfg.nx, h->cfg.ny);
+    return std::make_tuple(dev, h->prec + (h->general ? 16 : 0), h->Q, h->S, h->cfg.nx, h->cfg.ny);
 }
 
 int variant_count(int prec) {
     return prec == LB_RD_FP32 ? lbrd::kF32VariantCount : (prec == LB_RD_FP64 ? 1 : lbrd::kHalfVariantCount);
 }
 
-int handle_variant_count(const lb_rd_handle *h) { return h->general ? 1 : variant_count(h->prec); }
+int handle_variant_count(const lb_rd_handle *h) {
+    if (h->inplace) return 1;
+    if (h->general) return h->prec == LB_RD_FP64 ? 1 : lbrd::kGeneralVariantCount;
+    return variant_count(h->prec);
+}
 
 int variant_steps(const lb_rd_handle *h, int v) {
     return h->prec == LB_RD_FP32 && !h->general ? lbrd::kF32Variants[v].steps : 1;
 }
 
 bool variant_fits(const lb_rd_handle *h, int v) {
-    return h->general || h->prec != LB_RD_FP32 || h->cfg.nx % lbrd::kF32Variants[v].nx_multiple == 0;
+    if (h->general) return h->prec == LB_RD_FP64 || h->cfg.nx % lbrd::kGeneralVariants[v].sites == 0;
+    return h->prec != LB_RD_FP32 || h->cfg.nx % lbrd::kF32Variants[v].nx_multiple == 0;
 }
 
 cudaError_t launch_step(const lb_rd_handle *h, const lbrd::StepArgs &a, int variant) {
-    if (h->general) return lbrd::launch_step_general(h->prec == LB_RD_FP64 ? 0 : 1, h->Q, h->S, a, h->stream);
+    if (h->general) return lbrd::launch_step_general(h->prec == LB_RD_FP64 ? 0 : 1, h->Q, h->S, a, h->stream, variant);
     switch (h->prec) {
         case LB_RD_FP64: return lbrd::launch_step_f64(h->Q, h->S, a, h->stream);
         case LB_RD_FP32: return lbrd::launch_step_f32_variant(variant, h->Q, h->S, a, h->stream);
@@ -168,12 +174,17 @@ int lb_rd_check_config(const lb_rd_config *cfg, size_t *bytes) {
         return fail(LB_RD_EINVAL, "precision: unknown value " + std::to_string(cfg->precision));
     if (needs_general(*cfg) && cfg->precision != LB_RD_FP64 && cfg->precision != LB_RD_FP32)
         return fail(LB_RD_EINVAL, "more than two species or a mass-action network: FP64 or FP32 storage only");
+    if (cfg->streaming != LB_RD_STREAM_PINGPONG && cfg->streaming != LB_RD_STREAM_INPLACE)
+        return fail(LB_RD_EINVAL, "streaming: unknown value " + std::to_string(cfg->streaming));
+    if (cfg->streaming == LB_RD_STREAM_INPLACE && cfg->precision != LB_RD_FP64 && cfg->precision != LB_RD_FP32)
+        return fail(LB_RD_EINVAL, "in-place streaming: FP64 or FP32 storage only");
     if (bytes) {
         const int64_t pitch = pitch_for(cfg->nx);
         const size_t st = lbrd::state_plane_bytes(cfg->precision, Q, cfg->nspecies, cfg->ny, pitch);
         const size_t rb = (size_t)cfg->nspecies * cfg->ny * pitch * rho_elem(cfg->precision);
         const size_t np1 = lbrd::max_persistent_blocks(), np2 = lbrd::mass_partials_needed(cfg->nx, cfg->ny);
-        *bytes = 2 * st + rb + (np1 > np2 ? np1 : np2) * cfg->nspecies * sizeof(double) +
+        const size_t copies = cfg->streaming == LB_RD_STREAM_INPLACE ? 1 : 2;
+        *bytes = copies * st + rb + (np1 > np2 ? np1 : np2) * cfg->nspecies * sizeof(double) +
                  LB_RD_MAX_SPECIES * sizeof(double) + 2 * sizeof(int);
     }
     return LB_RD_OK;
@@ -214,6 +225,7 @@ int lb_rd_create(const lb_rd_config *cfg, lb_rd_handle **out) {
     h->S = cfg->nspecies;
     h->prec = cfg->precision;
     h->general = needs_general(*cfg);
+    h->inplace = cfg->streaming == LB_RD_STREAM_INPLACE;
     h->pitch = pitch_for(cfg->nx);
     h->plane = cfg->ny * h->pitch;
     h->stream = static_cast<cudaStream_t>(cfg->stream);
@@ -224,7 +236,7 @@ int lb_rd_create(const lb_rd_config *cfg, lb_rd_handle **out) {
     const size_t parts = (nparts > nparts2 ? nparts : nparts2) * h->S;
     cudaError_t err = cudaSuccess;
     if (!err) err = cudaMalloc(&h->buf[0], h->state_bytes);
-    if (!err) err = cudaMalloc(&h->buf[1], h->state_bytes);
+    if (!err && !h->inplace) err = cudaMalloc(&h->buf[1], h->state_bytes);
     if (!err) err = cudaMalloc(&h->rho, h->rho_bytes);
     if (!err) err = cudaMalloc(&h->partials, parts * sizeof(double));
     if (!err) err = cudaMalloc(&h->counter, sizeof(unsigned int));
@@ -233,14 +245,14 @@ int lb_rd_create(const lb_rd_config *cfg, lb_rd_handle **out) {
     if (!err) err = cudaMemset(h->status, 0, sizeof(int));
     if (!err) err = cudaMemset(h->counter, 0, sizeof(unsigned int));
     if (!err) err = cudaMemset(h->buf[0], 0, h->state_bytes);
-    if (!err) err = cudaMemset(h->buf[1], 0, h->state_bytes);
+    if (!err && !h->inplace) err = cudaMemset(h->buf[1], 0, h->state_bytes);
     if (!err) err = cudaMemset(h->rho, 0, h->rho_bytes);
     if (err) {
         rc = cuda_fail(err, "lb_rd_create allocation");
         lb_rd_destroy(h);
         return rc;
     }
-    if (!h->general) {
+    {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(tune_key(h));
         if (it != g_tune_cache.end()) {
@@ -307,6 +319,7 @@ int lb_rd_init(lb_rd_handle *h, const double *rho0, int is_device) {
 // state, f*(t - 1), is still intact and its pull-sum is rho(t).
 static int ensure_rho(lb_rd_handle *h) {
     if (h->rho_t == h->t) return LB_RD_OK;
+    if (h->inplace) return fail(LB_RD_EINVAL, "in-place handle: the density cache is out of date");
     cudaError_t e = lbrd::launch_pull_rho(h->prec, h->Q, h->S, h->buf[h->cur ^ 1], h->cfg.nx, h->cfg.ny, h->pitch,
                                           h->rho, h->stream);
     if (e) return cuda_fail(e, "density kernel");
@@ -328,6 +341,35 @@ int lb_rd_step(lb_rd_handle *h, int64_t nsteps) {
     a.partials = h->partials;
     a.counter = h->counter;
     a.status = h->status;
+    if (h->inplace) {
+        // one copy: phase by the parity of t; the last launch writes rho(t)
+        for (int64_t n = 0; n < nsteps; ++n) {
+            a.src = a.dst = h->buf[0];
+            a.rho_out = n == nsteps - 1 ? h->rho : nullptr;
+            a.mass_out = h->cfg.track_mass ? h->mass : nullptr;
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (h->timing) {
+                LBRD_CUDA(cudaEventCreate(&e0), "event create");
+                LBRD_CUDA(cudaEventCreate(&e1), "event create");
+                LBRD_CUDA(cudaEventRecord(e0, h->stream), "event record");
+            }
+            cudaError_t e = lbrd::launch_step_aa(h->prec == LB_RD_FP64 ? 0 : 1, h->Q, h->S, (int)(h->t & 1), a,
+                                                 h->stream);
+            if (e) return cuda_fail(e, "in-place step kernel");
+            h->launches++;
+            if (h->timing) {
+                LBRD_CUDA(cudaEventRecord(e1, h->stream), "event record");
+                h->events.push_back(e0);
+                h->events.push_back(e1);
+            }
+            h->t += 1;
+        }
+        if (nsteps > 0) {
+            h->rho_t = h->t;
+            h->mass_fresh = h->cfg.track_mass != 0;
+        }
+        return LB_RD_OK;
+    }
     // With a two-step variant, all but the last one or two steps go two at a
     // time; the last launch is always a single step, so that the other state
     // copy holds f*(t - 1) and rho(t) can be recomputed from it on demand.
@@ -419,8 +461,11 @@ int lb_rd_get_distributions(lb_rd_handle *h, double *f_out, int is_device) {
         if (rc) return rc;
         dst = h->stage;
     }
-    cudaError_t e = lbrd::launch_export(h->prec, h->Q, h->S, h->buf[h->cur], h->cfg.nx, h->cfg.ny, h->pitch, dst,
-                                        h->stream);
+    cudaError_t e = h->inplace && (h->t & 1)
+                         ? lbrd::launch_export_swapped(h->prec == LB_RD_FP64 ? 0 : 1, h->Q, h->S, h->buf[0], h->cfg.nx,
+                                                       h->cfg.ny, h->pitch, dst, h->stream)
+                         : lbrd::launch_export(h->prec, h->Q, h->S, h->buf[h->cur], h->cfg.nx, h->cfg.ny, h->pitch,
+                                               dst, h->stream);
     if (e) return cuda_fail(e, "export kernel");
     h->launches++;
     if (!is_device)
@@ -433,7 +478,7 @@ int lb_rd_get_distributions(lb_rd_handle *h, double *f_out, int is_device) {
 // Checkpoint layout: header, then the current state copy, then the rho cache.
 struct CkptHeader {
     char magic[8];
-    int32_t prec, Q, S, pad;
+    int32_t prec, Q, S, pad;  // pad: 1 for the in-place state layout
     int64_t nx, ny, pitch, t;
 };
 
@@ -456,6 +501,7 @@ int lb_rd_save(lb_rd_handle *h, void *host_buf, size_t bytes) {
     hd.prec = h->prec;
     hd.Q = h->Q;
     hd.S = h->S;
+    hd.pad = h->inplace ? 1 : 0;  // state layout
     hd.nx = h->cfg.nx;
     hd.ny = h->cfg.ny;
     hd.pitch = h->pitch;
@@ -478,7 +524,7 @@ int lb_rd_restore(lb_rd_handle *h, const void *host_buf, size_t bytes) {
     CkptHeader hd;
     std::memcpy(&hd, host_buf, sizeof(hd));
     if (std::memcmp(hd.magic, "LBRDCKP1", 8) != 0 || hd.prec != h->prec || hd.Q != h->Q || hd.S != h->S ||
-        hd.nx != h->cfg.nx || hd.ny != h->cfg.ny || hd.pitch != h->pitch)
+        hd.nx != h->cfg.nx || hd.ny != h->cfg.ny || hd.pitch != h->pitch || hd.pad != (h->inplace ? 1 : 0))
         return fail(LB_RD_EINVAL, "checkpoint does not match this handle's configuration");
     const char *p = static_cast<const char *>(host_buf);
     LBRD_CUDA(cudaMemcpyAsync(h->buf[h->cur], p + sizeof(hd), h->state_bytes, cudaMemcpyHostToDevice, h->stream),
@@ -545,13 +591,20 @@ const char *lb_rd_variant_name(int32_t precision, int32_t variant) {
     return "";
 }
 
+int lb_rd_handle_variant_count(const lb_rd_handle *h, int32_t *count) {
+    if (!h || !count) return fail(LB_RD_EINVAL, "handle or count is NULL");
+    *count = handle_variant_count(h);
+    return LB_RD_OK;
+}
+
+const char *lb_rd_handle_variant_name(const lb_rd_handle *h, int32_t variant) {
+    if (!h || variant < 0 || variant >= handle_variant_count(h)) return "";
+    if (!h->general) return lb_rd_variant_name(h->prec, variant);
+    return h->prec == LB_RD_FP64 ? "general_f64" : lbrd::kGeneralVariants[variant].name;
+}
+
 int lb_rd_set_variant(lb_rd_handle *h, int32_t variant) {
     if (!h) return fail(LB_RD_EINVAL, "handle is NULL");
-    if (variant == -1 && h->general) {
-        h->variant = 0;
-        h->tb_variant = -1;
-        return LB_RD_OK;
-    }
     if (variant == -1) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(tune_key(h));
@@ -562,8 +615,10 @@ int lb_rd_set_variant(lb_rd_handle *h, int32_t variant) {
     if (variant < 0 || variant >= handle_variant_count(h))
         return fail(LB_RD_EINVAL, "variant out of range for this configuration");
     if (!variant_fits(h, variant))
-        return fail(LB_RD_EINVAL, std::string("variant ") + lb_rd_variant_name(h->prec, variant) + " needs nx to be a multiple of " +
-                                      std::to_string(lbrd::kF32Variants[variant].nx_multiple));
+        return fail(LB_RD_EINVAL, std::string("variant ") + lb_rd_handle_variant_name(h, variant) +
+                                      " needs nx to be a multiple of " +
+                                      std::to_string(h->general ? lbrd::kGeneralVariants[variant].sites
+                                                                : lbrd::kF32Variants[variant].nx_multiple));
     if (variant_steps(h, variant) == 2) {
         h->tb_variant = variant;
     } else {
@@ -583,6 +638,11 @@ int lb_rd_autotune(lb_rd_handle *h, int32_t iters, int32_t *best, double *times_
     if (!h) return fail(LB_RD_EINVAL, "handle is NULL");
     if (iters < 1) return fail(LB_RD_EINVAL, "iters must be >= 1");
     if (!h->initialized) return fail(LB_RD_EINVAL, "lb_rd_init has not been called");
+    if (h->inplace) {  // one variant, and no spare copy to time it on without advancing the state
+        if (best) *best = 0;
+        if (times_ms && max_times > 0) times_ms[0] = -1.0;
+        return LB_RD_OK;
+    }
     int rc = ensure_rho(h);  // the tuner overwrites f*(t - 1), from which rho(t) would be recomputed
     if (rc) return rc;
     lbrd::StepArgs a{};
@@ -637,7 +697,7 @@ int lb_rd_autotune(lb_rd_handle *h, int32_t iters, int32_t *best, double *times_
     h->variant = best1 >= 0 ? best1 : 0;
     h->tb_variant = (best2 >= 0 && ms2 < ms1) ? best2 : -1;
     const int arg = h->tb_variant >= 0 ? h->tb_variant : h->variant;
-    if (!h->general) {
+    {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tune_cache[tune_key(h)] = std::make_pair(h->variant, h->tb_variant);
     }

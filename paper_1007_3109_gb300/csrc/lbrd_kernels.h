@@ -55,8 +55,21 @@ struct StepShape {
 
 // General step: 1 .. 4 species, mass-action networks; prec 0 = FP64 (no FMA
 // contraction, bit-reproducible), otherwise FP32.  One thread per site.
-cudaError_t launch_step_general(int prec, int Q, int S, const StepArgs &a, cudaStream_t st);
+struct GeneralVariant {
+    const char *name;
+    int sites;  // consecutive sites per thread; the variant needs nx % sites == 0
+};
+extern const GeneralVariant kGeneralVariants[];
+extern const int kGeneralVariantCount;  // FP32; FP64 has variant 0 only
+cudaError_t launch_step_general(int prec, int Q, int S, const StepArgs &a, cudaStream_t st, int variant);
 cudaError_t launch_init_general(int prec, int Q, int S, const InitArgs &a, cudaStream_t st);
+
+// In-place (AA) step: phase 0 for t even (natural in, pushed-and-swapped
+// out), 1 for t odd; a.src == a.dst.  prec 0 = FP64, otherwise FP32.  And the
+// export of a pushed-and-swapped state as packed FP64 [s][i][y][x].
+cudaError_t launch_step_aa(int prec, int Q, int S, int phase, const StepArgs &a, cudaStream_t st);
+cudaError_t launch_export_swapped(int prec, int Q, int S, const void *state, int64_t nx, int64_t ny, int64_t pitch,
+                                  double *out, cudaStream_t st);
 
 // FP64: one thread per site, no FMA contraction (bit-reproducible).
 StepShape step_shape_f64(int64_t nx, int64_t ny);

@@ -64,8 +64,9 @@ extern "C" int lb_rd_step_noalloc(const lb_rd_config *cfg, const void *state_in,
         return lbrd::report_error(LB_RD_EINVAL, "lb_rd_step_noalloc: state_in, state_out and mass_out must be device pointers");
     if (state_in == state_out)
         return lbrd::report_error(LB_RD_EINVAL, "lb_rd_step_noalloc: state_in and state_out must be different buffers");
-    if (cfg->nspecies > 2 || cfg->reaction.kind == LB_RD_REACTION_MASS_ACTION)
-        return lbrd::report_error(LB_RD_EINVAL, "lb_rd_step_noalloc: at most two species and no mass-action network");
+    if (cfg->nspecies > 2 || cfg->reaction.kind == LB_RD_REACTION_MASS_ACTION || cfg->streaming != 0)
+        return lbrd::report_error(LB_RD_EINVAL,
+                                  "lb_rd_step_noalloc: at most two species, no mass-action network, two state buffers");
     const int Q = cfg->lattice == LB_RD_D2Q9 ? 9 : 5;
     const int S = cfg->nspecies;
     const int prec = cfg->precision;

@@ -388,8 +388,8 @@ int lb_rd_submit(lb_rd_server *s, const lb_rd_config *cfg, const double *rho0, i
     if (rc) return rc;
     if (cfg->lattice != s->cfg.lattice || cfg->nspecies != s->cfg.nspecies || cfg->precision != s->cfg.precision)
         return lbrd::report_error(LB_RD_EINVAL, "lb_rd_submit: lattice, nspecies and precision must match the server");
-    if (cfg->reaction.kind == LB_RD_REACTION_MASS_ACTION)
-        return lbrd::report_error(LB_RD_EINVAL, "lb_rd_submit: serving takes no mass-action network");
+    if (cfg->reaction.kind == LB_RD_REACTION_MASS_ACTION || cfg->streaming != 0)
+        return lbrd::report_error(LB_RD_EINVAL, "lb_rd_submit: serving takes no mass-action network and no in-place state");
     if ((s->mode == 1 || s->mode == 2) && cfg->nx % 4)
         return lbrd::report_error(LB_RD_EINVAL, "lb_rd_submit: 16-bit deviation storage needs nx % 4 == 0");
     if (nsteps < 1) return lbrd::report_error(LB_RD_EINVAL, "lb_rd_submit: nsteps must be >= 1");

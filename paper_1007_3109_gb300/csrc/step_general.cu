@@ -10,8 +10,9 @@
 //   p = rate_r;  p = p * rho_j  (order[r][j] times, j ascending);
 //   R_s = R_s + change[r][s] * p  (steps in order, zero changes skipped).
 // FP32 uses post = (1 - omega) f + w (omega rho + R) and plain float
-// arithmetic.  The network is copied to shared memory once per block (its
-// entries are indexed by the loop counters).
+// arithmetic; its launch variants update 1, 2 or 4 consecutive sites per
+// thread with the same per-site arithmetic.  The network is copied to shared
+// memory once per block (its entries are indexed by the loop counters).
 #include "lbrd_kernels.h"
 
 namespace lbrd {
@@ -130,6 +131,113 @@ __global__ void __launch_bounds__(kBX, 6) step_general_kernel(StepArgs a, int64_
     if (a.mass_out) block_mass_reduce<S, kBX>(acc, a.partials, a.counter, a.mass_out);
 }
 
+// FP32, V = 2 or 4 consecutive sites per thread (nx % V == 0): one aligned
+// V-wide load per (species, velocity) from the pulled row; the +-1 column
+// shift is a warp shuffle of the neighbouring lane's values, and only the
+// lanes at a warp edge or at the periodic edge load one extra float.  The
+// per-site arithmetic is the one-site kernel's, so every variant gives the
+// same bits.
+template <int V>
+__device__ __forceinline__ void ldvec(const float *p, float (&v)[V]) {
+    if constexpr (V == 2) {
+        const float2 q = __ldg(reinterpret_cast<const float2 *>(p));
+        v[0] = q.x; v[1] = q.y;
+    } else {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void stvec(float *p, const float (&v)[V]) {
+    if constexpr (V == 2) *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    else *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+template <int Q, int S, int V, int MINB>
+__global__ void __launch_bounds__(kBX, MINB) step_general_vec_kernel(StepArgs a, int64_t tiles_x, int64_t ntiles) {
+    using L = Lattice<Q>;
+    __shared__ SharedNet net;
+    load_net(a.net, net);
+    const float *__restrict__ src = static_cast<const float *>(a.src);
+    float *__restrict__ dst = static_cast<float *>(a.dst);
+    const int lane = threadIdx.x & 31;
+    const int64_t nx = a.nx, ny = a.ny, pitch = a.pitch, plane = a.plane;
+    double acc[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) acc[s] = 0.0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t y = tile / tiles_x, x0 = ((tile - y * tiles_x) * kBX + threadIdx.x) * V;
+        const bool live = x0 < nx;
+        const int64_t xc = live ? x0 : 0;  // dead lanes load valid data for the shuffles
+        const int64_t xl = xc == 0 ? nx - 1 : xc - 1;
+        const int64_t xr = xc + V < nx ? xc + V : xc + V - nx;
+        const bool need_l = lane == 0 || xc == 0;
+        const bool need_r = lane == 31 || xc + V >= nx;
+        float f[S][Q][V], rho[S][V];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const float *row = src + (int64_t)(s * Q + i) * plane + wrap(y - L::ey(i), ny) * pitch;
+                float v[V];
+                ldvec<V>(row + xc, v);
+                if (L::ex(i) == 0) {
+#pragma unroll
+                    for (int j = 0; j < V; ++j) f[s][i][j] = v[j];
+                } else if (L::ex(i) == 1) {  // pull from x - 1
+                    float left = __shfl_up_sync(kFullMask, v[V - 1], 1);
+                    if (need_l) left = __ldg(row + xl);
+                    f[s][i][0] = left;
+#pragma unroll
+                    for (int j = 1; j < V; ++j) f[s][i][j] = v[j - 1];
+                } else {  // pull from x + 1
+                    float right = __shfl_down_sync(kFullMask, v[0], 1);
+                    if (need_r) right = __ldg(row + xr);
+#pragma unroll
+                    for (int j = 0; j < V - 1; ++j) f[s][i][j] = v[j + 1];
+                    f[s][i][V - 1] = right;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                float r = f[s][0][j];
+#pragma unroll
+                for (int i = 1; i < Q; ++i) r = radd(r, f[s][i][j]);
+                rho[s][j] = r;
+            }
+        }
+        if (!live) continue;
+        float R[S][V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            float rj[S], Rj[S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) rj[s] = rho[s][j];
+            network_source<S>(net, a.rkind, rj, Rj);
+#pragma unroll
+            for (int s = 0; s < S; ++s) R[s][j] = Rj[s];
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const float om = (float)a.omega[s];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                float o[V];
+#pragma unroll
+                for (int j = 0; j < V; ++j) o[j] = relax(f[s][i][j], weight<Q, float>(i), rho[s][j], om, R[s][j]);
+                stvec<V>(dst + (int64_t)(s * Q + i) * plane + y * pitch + x0, o);
+            }
+            if (a.rho_out) stvec<V>(static_cast<float *>(a.rho_out) + (int64_t)s * plane + y * pitch + x0, rho[s]);
+            float part = 0.f;
+#pragma unroll
+            for (int j = 0; j < V; ++j) part += rho[s][j];
+            acc[s] += (double)part;
+        }
+    }
+    if (a.mass_out) block_mass_reduce<S, kBX>(acc, a.partials, a.counter, a.mass_out);
+}
+
 template <typename T, int Q, int S>
 __global__ void __launch_bounds__(kBX) init_general_kernel(InitArgs a) {
     __shared__ SharedNet net;
@@ -167,6 +275,36 @@ cudaError_t launch_general(const StepArgs &a, cudaStream_t st) {
     const unsigned grid = persistent_blocks(kern, kBX, ntiles);
     kern<<<grid, kBX, 0, st>>>(a, tiles_x, ntiles);
     return cudaGetLastError();
+}
+
+template <int Q, int S, int V, int MINB>
+cudaError_t launch_general_vec(const StepArgs &a, cudaStream_t st) {
+    if (a.nx % V) return cudaErrorInvalidValue;
+    const int64_t tiles_x = (a.nx / V + kBX - 1) / kBX, ntiles = tiles_x * a.ny;
+    auto kern = step_general_vec_kernel<Q, S, V, MINB>;
+    const unsigned grid = persistent_blocks(kern, kBX, ntiles);
+    kern<<<grid, kBX, 0, st>>>(a, tiles_x, ntiles);
+    return cudaGetLastError();
+}
+
+template <int V, int MINB>
+cudaError_t dispatch_vec(int Q, int S, const StepArgs &a, cudaStream_t st) {
+    if (Q == 9) {
+        switch (S) {
+            case 1: return launch_general_vec<9, 1, V, MINB>(a, st);
+            case 2: return launch_general_vec<9, 2, V, MINB>(a, st);
+            case 3: return launch_general_vec<9, 3, V, MINB>(a, st);
+            case 4: return launch_general_vec<9, 4, V, MINB>(a, st);
+        }
+    } else if (Q == 5) {
+        switch (S) {
+            case 1: return launch_general_vec<5, 1, V, MINB>(a, st);
+            case 2: return launch_general_vec<5, 2, V, MINB>(a, st);
+            case 3: return launch_general_vec<5, 3, V, MINB>(a, st);
+            case 4: return launch_general_vec<5, 4, V, MINB>(a, st);
+        }
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <typename T, int Q, int S>
@@ -218,8 +356,20 @@ cudaError_t dispatch_init(int Q, int S, const InitArgs &a, cudaStream_t st) {
 
 }  // namespace
 
-cudaError_t launch_step_general(int prec, int Q, int S, const StepArgs &a, cudaStream_t st) {
-    return prec == 0 ? dispatch_step<double>(Q, S, a, st) : dispatch_step<float>(Q, S, a, st);
+const GeneralVariant kGeneralVariants[] = {
+    {"general_1site", 1}, {"general_2site", 2}, {"general_4site", 4}, {"general_2site_minb3", 2},
+};
+const int kGeneralVariantCount = sizeof(kGeneralVariants) / sizeof(kGeneralVariants[0]);
+
+cudaError_t launch_step_general(int prec, int Q, int S, const StepArgs &a, cudaStream_t st, int variant) {
+    if (prec == 0) return variant == 0 ? dispatch_step<double>(Q, S, a, st) : cudaErrorInvalidValue;
+    switch (variant) {
+        case 0: return dispatch_step<float>(Q, S, a, st);
+        case 1: return dispatch_vec<2, 4>(Q, S, a, st);
+        case 2: return dispatch_vec<4, 2>(Q, S, a, st);
+        case 3: return dispatch_vec<2, 3>(Q, S, a, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_init_general(int prec, int Q, int S, const InitArgs &a, cudaStream_t st) {

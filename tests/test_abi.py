@@ -127,3 +127,21 @@ def test_null_arguments_are_errors_not_crashes(lib):
     assert lib.lb_rd_step(None, 1) == B.LB_RD_EINVAL
     assert lib.lb_rd_moments(None, None, None, 0) == B.LB_RD_EINVAL
     assert lib.lb_rd_destroy(None) == B.LB_RD_OK
+
+
+def test_inplace_config_validation_and_size(lib):
+    base = dict(lattice="D2Q9", nspecies=2, nx=512, ny=512, tau=[0.8, 0.65], reaction="gray_scott", F=0.04, k=0.06,
+                precision="fp32")
+    two = B.lb_rd_check_config(B.make_config(**base))
+    one = B.lb_rd_check_config(B.make_config(**base, inplace=True))
+    assert two - one == 2 * 9 * 512 * 512 * 4  # one state copy instead of two
+    with pytest.raises(B.LbRdError) as ei:
+        B.lb_rd_check_config(B.make_config(**dict(base, precision="fp32_bf16dev"), inplace=True))
+    assert "in-place" in str(ei.value)
+    cfg = B.make_config(**base)
+    cfg.streaming = 2
+    with pytest.raises(B.LbRdError):
+        B.lb_rd_check_config(cfg)
+    out = B.c_void_p()
+    cfgs = (B.lb_rd_config * 1)(B.make_config(**base, inplace=True))
+    assert lib.lb_rd_batch_create(cfgs, 1, B.ctypes.byref(out)) == B.LB_RD_EINVAL
