@@ -396,7 +396,7 @@ def network_mode(args):
     rho0 = inputs.initial_density("gs2x_8192", nx=n, ny=n)
     stream = torch.cuda.current_stream()
     sim = B.Simulation("D2Q9", S, n, n, taus, "mass_action", precision=prec, track_mass=True,
-                       stream=stream.cuda_stream, network=net)
+                       stream=stream.cuda_stream, network=net, inplace=args.inplace)
     sim.init(torch.from_numpy(rho0).cuda())
     sim.step(args.warmup)
     nvar = B.lb_rd_handle_variant_count(sim.h)
@@ -426,7 +426,8 @@ def network_mode(args):
             "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": "gs2x_8192", "nx": n, "ny": n, "species": S, "reaction_steps": len(net[0]),
                        "precision": prec, "variant": names[best], "autotune_ms_per_launch": tuning,
-                       "l2": f"no flush: two state copies of {bps * n * n / 1e9:.1f} GB >> 129 MB L2"},
+                       "streaming": "in-place (AA), one state copy" if args.inplace else "ping-pong, two state copies",
+                       "l2": f"no flush: state of {(0.5 if args.inplace else 1) * bps * n * n / 1e9:.1f} GB >> 129 MB L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "kernel": f"general:{names[best]} ({prec}, D2Q9, {S} species)",
                          "bytes_per_site_per_launch": bps, "peak_kind": peak_kind},
@@ -555,13 +556,11 @@ def main():
     sim.init(rho0_dev)
     nvar = B.lb_rd_handle_variant_count(sim.h)
     names = [B.lb_rd_handle_variant_name(sim.h, v) for v in range(nvar)]
-    if args.inplace:
-        names = ["inplace_aa"]
     if args.variant:
         B.lb_rd_set_variant(sim.h, names.index(args.variant))
     sim.step(args.warmup)
     tuning = {}
-    if args.tune_iters > 0 and not args.inplace:
+    if args.tune_iters > 0:
         # project autotuner: every launch variant timed on this state (not advanced)
         best, times = B.lb_rd_autotune(sim.h, iters=args.tune_iters)
         tuning = {names[v]: (round(times[v], 4) if times[v] >= 0 else None) for v in range(nvar)}

@@ -96,7 +96,8 @@ std::map<std::tuple<int, int, int, int, int64_t, int64_t>, std::pair<int, int>> 
 std::tuple<int, int, int, int, int64_t, int64_t> tune_key(const lb_rd_handle *h) {
     int dev = 0;
     cudaGetDevice(&dev);
-    return std::make_tuple(dev, h->prec + (h->general ? 16 : 0), h->Q, h->S, h->cfg.nx, h->cfg.ny);
+    return std::make_tuple(dev, h->prec + (h->general ? 16 : 0) + (h->inplace ? 32 : 0), h->Q, h->S, h->cfg.nx,
+                           h->cfg.ny);
 }
 
 int variant_count(int prec) {
@@ -104,7 +105,7 @@ int variant_count(int prec) {
 }
 
 int handle_variant_count(const lb_rd_handle *h) {
-    if (h->inplace) return 1;
+    if (h->inplace) return h->prec == LB_RD_FP64 ? 1 : lbrd::kAAVariantCount;
     if (h->general) return h->prec == LB_RD_FP64 ? 1 : lbrd::kGeneralVariantCount;
     return variant_count(h->prec);
 }
@@ -114,6 +115,7 @@ int variant_steps(const lb_rd_handle *h, int v) {
 }
 
 bool variant_fits(const lb_rd_handle *h, int v) {
+    if (h->inplace) return h->prec == LB_RD_FP64 || h->cfg.nx % lbrd::kAAVariants[v].sites == 0;
     if (h->general) return h->prec == LB_RD_FP64 || h->cfg.nx % lbrd::kGeneralVariants[v].sites == 0;
     return h->prec != LB_RD_FP32 || h->cfg.nx % lbrd::kF32Variants[v].nx_multiple == 0;
 }
@@ -354,7 +356,7 @@ int lb_rd_step(lb_rd_handle *h, int64_t nsteps) {
                 LBRD_CUDA(cudaEventRecord(e0, h->stream), "event record");
             }
             cudaError_t e = lbrd::launch_step_aa(h->prec == LB_RD_FP64 ? 0 : 1, h->Q, h->S, (int)(h->t & 1), a,
-                                                 h->stream);
+                                                 h->stream, h->variant);
             if (e) return cuda_fail(e, "in-place step kernel");
             h->launches++;
             if (h->timing) {
@@ -599,6 +601,7 @@ int lb_rd_handle_variant_count(const lb_rd_handle *h, int32_t *count) {
 
 const char *lb_rd_handle_variant_name(const lb_rd_handle *h, int32_t variant) {
     if (!h || variant < 0 || variant >= handle_variant_count(h)) return "";
+    if (h->inplace) return h->prec == LB_RD_FP64 ? "aa_f64" : lbrd::kAAVariants[variant].name;
     if (!h->general) return lb_rd_variant_name(h->prec, variant);
     return h->prec == LB_RD_FP64 ? "general_f64" : lbrd::kGeneralVariants[variant].name;
 }
@@ -617,8 +620,9 @@ int lb_rd_set_variant(lb_rd_handle *h, int32_t variant) {
     if (!variant_fits(h, variant))
         return fail(LB_RD_EINVAL, std::string("variant ") + lb_rd_handle_variant_name(h, variant) +
                                       " needs nx to be a multiple of " +
-                                      std::to_string(h->general ? lbrd::kGeneralVariants[variant].sites
-                                                                : lbrd::kF32Variants[variant].nx_multiple));
+                                      std::to_string(h->inplace   ? lbrd::kAAVariants[variant].sites
+                                                     : h->general ? lbrd::kGeneralVariants[variant].sites
+                                                                  : lbrd::kF32Variants[variant].nx_multiple));
     if (variant_steps(h, variant) == 2) {
         h->tb_variant = variant;
     } else {
@@ -634,15 +638,69 @@ int lb_rd_get_variant(const lb_rd_handle *h, int32_t *variant) {
     return LB_RD_OK;
 }
 
+// In-place handles have no spare copy: the variants are timed on a temporary
+// copy of the state (alternating the two phases from the handle's parity),
+// which is freed afterwards; the handle's own state is not touched.
+static int autotune_inplace(lb_rd_handle *h, int32_t iters, int32_t *best, double *times_ms, int32_t max_times) {
+    void *scratch = nullptr;
+    LBRD_CUDA(cudaMalloc(&scratch, h->state_bytes), "autotune scratch");
+    cudaError_t e = cudaMemcpyAsync(scratch, h->buf[0], h->state_bytes, cudaMemcpyDeviceToDevice, h->stream);
+    lbrd::StepArgs a{};
+    a.src = a.dst = scratch;
+    a.nx = h->cfg.nx;
+    a.ny = h->cfg.ny;
+    a.pitch = h->pitch;
+    a.plane = h->plane;
+    lbrd::fill_reaction(h->cfg, a.omega, &a.rkind, &a.kappa, &a.F, &a.k, &a.net);
+    a.status = h->status;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!e) e = cudaEventCreate(&e0);
+    if (!e) e = cudaEventCreate(&e1);
+    const int prec = h->prec == LB_RD_FP64 ? 0 : 1;
+    int64_t t = h->t;
+    int bestv = -1;
+    double bestms = 0.0;
+    for (int v = 0; v < handle_variant_count(h) && !e; ++v) {
+        if (!variant_fits(h, v)) {
+            if (times_ms && v < max_times) times_ms[v] = -1.0;
+            continue;
+        }
+        for (int k = 0; k < 2 && !e; ++k, ++t) e = lbrd::launch_step_aa(prec, h->Q, h->S, (int)(t & 1), a, h->stream, v);
+        if (!e) e = cudaEventRecord(e0, h->stream);
+        for (int k = 0; k < iters && !e; ++k, ++t) e = lbrd::launch_step_aa(prec, h->Q, h->S, (int)(t & 1), a, h->stream, v);
+        if (!e) e = cudaEventRecord(e1, h->stream);
+        if (!e) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (!e) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e) break;
+        h->launches += iters + 2;
+        const double per = ms / iters;
+        if (times_ms && v < max_times) times_ms[v] = per;
+        if (bestv < 0 || per < bestms) {
+            bestv = v;
+            bestms = per;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(scratch);
+    if (e) return cuda_fail(e, "in-place autotune");
+    h->variant = bestv >= 0 ? bestv : 0;
+    h->tb_variant = -1;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[tune_key(h)] = std::make_pair(h->variant, -1);
+    }
+    if (best) *best = h->variant;
+    return LB_RD_OK;
+}
+
 int lb_rd_autotune(lb_rd_handle *h, int32_t iters, int32_t *best, double *times_ms, int32_t max_times) {
     if (!h) return fail(LB_RD_EINVAL, "handle is NULL");
     if (iters < 1) return fail(LB_RD_EINVAL, "iters must be >= 1");
     if (!h->initialized) return fail(LB_RD_EINVAL, "lb_rd_init has not been called");
-    if (h->inplace) {  // one variant, and no spare copy to time it on without advancing the state
-        if (best) *best = 0;
-        if (times_ms && max_times > 0) times_ms[0] = -1.0;
-        return LB_RD_OK;
-    }
+    if (h->inplace) return autotune_inplace(h, iters, best, times_ms, max_times);
     int rc = ensure_rho(h);  // the tuner overwrites f*(t - 1), from which rho(t) would be recomputed
     if (rc) return rc;
     lbrd::StepArgs a{};

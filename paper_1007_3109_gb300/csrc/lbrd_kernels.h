@@ -67,7 +67,10 @@ cudaError_t launch_init_general(int prec, int Q, int S, const InitArgs &a, cudaS
 // In-place (AA) step: phase 0 for t even (natural in, pushed-and-swapped
 // out), 1 for t odd; a.src == a.dst.  prec 0 = FP64, otherwise FP32.  And the
 // export of a pushed-and-swapped state as packed FP64 [s][i][y][x].
-cudaError_t launch_step_aa(int prec, int Q, int S, int phase, const StepArgs &a, cudaStream_t st);
+// FP32 launch variants (sites per thread as in GeneralVariant); FP64 has 0.
+extern const GeneralVariant kAAVariants[];
+extern const int kAAVariantCount;
+cudaError_t launch_step_aa(int prec, int Q, int S, int phase, const StepArgs &a, cudaStream_t st, int variant);
 cudaError_t launch_export_swapped(int prec, int Q, int S, const void *state, int64_t nx, int64_t ny, int64_t pitch,
                                   double *out, cudaStream_t st);
 

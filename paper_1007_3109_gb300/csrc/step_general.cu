@@ -11,7 +11,8 @@
 //   R_s = R_s + change[r][s] * p  (steps in order, zero changes skipped).
 // FP32 uses post = (1 - omega) f + w (omega rho + R) and plain float
 // arithmetic; its launch variants update 1, 2 or 4 consecutive sites per
-// thread with the same per-site arithmetic.  The network is copied to shared
+// thread, or one site in two passes with few registers, all with the same
+// per-site arithmetic.  The network is copied to shared
 // memory once per block (its entries are indexed by the loop counters).
 #include "lbrd_kernels.h"
 
@@ -80,7 +81,42 @@ __device__ __forceinline__ void network_source(const SharedNet &n, int kind, con
     }
 }
 
-// Post-collision value of one population.
+// The network for V sites at once: each step's rate, orders and changes are
+// read once and applied to every site; per site the operations and their
+// order are exactly those of network_source.
+template <int S, int V>
+__device__ __forceinline__ void network_source_vec(const SharedNet &n, int kind, const float (&rho)[S][V],
+                                                   float (&R)[S][V]) {
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+        for (int v = 0; v < V; ++v) R[s][v] = 0.f;
+    if (kind != kMassAction) return;
+    for (int r = 0; r < n.nr; ++r) {
+        float p[V];
+        const float k = n.ratef[r];
+#pragma unroll
+        for (int v = 0; v < V; ++v) p[v] = k;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            const int o = n.order[r][j];
+            for (int e = 0; e < o; ++e)
+#pragma unroll
+                for (int v = 0; v < V; ++v) p[v] *= rho[j][v];
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int c = n.change[r][s];
+            if (c != 0) {
+                const float cf = (float)c;
+#pragma unroll
+                for (int v = 0; v < V; ++v) R[s][v] += cf * p[v];
+            }
+        }
+    }
+}
+
+// Post-collision value of one population.// Post-collision value of one population.
 __device__ __forceinline__ double relax(double f, double w, double rho, double om, double R) {
     return __dadd_rn(__dadd_rn(f, __dmul_rn(__dsub_rn(__dmul_rn(w, rho), f), om)), __dmul_rn(w, R));
 }
@@ -209,15 +245,7 @@ __global__ void __launch_bounds__(kBX, MINB) step_general_vec_kernel(StepArgs a,
         }
         if (!live) continue;
         float R[S][V];
-#pragma unroll
-        for (int j = 0; j < V; ++j) {
-            float rj[S], Rj[S];
-#pragma unroll
-            for (int s = 0; s < S; ++s) rj[s] = rho[s][j];
-            network_source<S>(net, a.rkind, rj, Rj);
-#pragma unroll
-            for (int s = 0; s < S; ++s) R[s][j] = Rj[s];
-        }
+        network_source_vec<S, V>(net, a.rkind, rho, R);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             const float om = (float)a.omega[s];
@@ -233,6 +261,54 @@ __global__ void __launch_bounds__(kBX, MINB) step_general_vec_kernel(StepArgs a,
 #pragma unroll
             for (int j = 0; j < V; ++j) part += rho[s][j];
             acc[s] += (double)part;
+        }
+    }
+    if (a.mass_out) block_mass_reduce<S, kBX>(acc, a.partials, a.counter, a.mass_out);
+}
+
+// FP32, one site per thread in two passes to keep few registers live: pass 1
+// loads the pulled f of every species only to sum rho, then the source is
+// evaluated, and pass 2 loads the same values again (L1 hits: the block's
+// rows were just read) for the collision.  Many more resident warps hide the
+// HBM latency; the arithmetic and its order are the one-site kernel's.
+template <int Q, int S, int MINB>
+__global__ void __launch_bounds__(kBX, MINB) step_general_2pass_kernel(StepArgs a, int64_t tiles_x, int64_t ntiles) {
+    using L = Lattice<Q>;
+    __shared__ SharedNet net;
+    load_net(a.net, net);
+    const float *__restrict__ src = static_cast<const float *>(a.src);
+    float *__restrict__ dst = static_cast<float *>(a.dst);
+    const int64_t nx = a.nx, ny = a.ny, pitch = a.pitch, plane = a.plane;
+    double acc[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) acc[s] = 0.0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t y = tile / tiles_x, x = (tile - y * tiles_x) * kBX + threadIdx.x;
+        if (x >= nx) continue;
+        // pulled rows y + 1, y, y - 1 and columns x + 1, x, x - 1 (periodic)
+        const int64_t rows[3] = {wrap(y + 1, ny) * pitch, y * pitch, wrap(y - 1, ny) * pitch};
+        const int64_t cols[3] = {wrap(x + 1, nx), x, wrap(x - 1, nx)};
+        auto off = [&](int i) { return (int64_t)i * plane + rows[1 + L::ey(i)] + cols[1 + L::ex(i)]; };
+        float rho[S], R[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const float *sp = src + (int64_t)s * Q * plane;
+            float r = __ldg(sp + off(0));
+#pragma unroll
+            for (int i = 1; i < Q; ++i) r = radd(r, __ldg(sp + off(i)));
+            rho[s] = r;
+        }
+        network_source<S>(net, a.rkind, rho, R);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const float *sp = src + (int64_t)s * Q * plane;
+            const float om = (float)a.omega[s];
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                dst[(int64_t)(s * Q + i) * plane + y * pitch + x] =
+                    relax(__ldg(sp + off(i)), weight<Q, float>(i), rho[s], om, R[s]);
+            if (a.rho_out) static_cast<float *>(a.rho_out)[(int64_t)s * plane + y * pitch + x] = rho[s];
+            acc[s] += (double)rho[s];
         }
     }
     if (a.mass_out) block_mass_reduce<S, kBX>(acc, a.partials, a.counter, a.mass_out);
@@ -285,6 +361,35 @@ cudaError_t launch_general_vec(const StepArgs &a, cudaStream_t st) {
     const unsigned grid = persistent_blocks(kern, kBX, ntiles);
     kern<<<grid, kBX, 0, st>>>(a, tiles_x, ntiles);
     return cudaGetLastError();
+}
+
+template <int Q, int S, int MINB>
+cudaError_t launch_general_2pass(const StepArgs &a, cudaStream_t st) {
+    const int64_t tiles_x = (a.nx + kBX - 1) / kBX, ntiles = tiles_x * a.ny;
+    auto kern = step_general_2pass_kernel<Q, S, MINB>;
+    const unsigned grid = persistent_blocks(kern, kBX, ntiles);
+    kern<<<grid, kBX, 0, st>>>(a, tiles_x, ntiles);
+    return cudaGetLastError();
+}
+
+template <int MINB>
+cudaError_t dispatch_2pass(int Q, int S, const StepArgs &a, cudaStream_t st) {
+    if (Q == 9) {
+        switch (S) {
+            case 1: return launch_general_2pass<9, 1, MINB>(a, st);
+            case 2: return launch_general_2pass<9, 2, MINB>(a, st);
+            case 3: return launch_general_2pass<9, 3, MINB>(a, st);
+            case 4: return launch_general_2pass<9, 4, MINB>(a, st);
+        }
+    } else if (Q == 5) {
+        switch (S) {
+            case 1: return launch_general_2pass<5, 1, MINB>(a, st);
+            case 2: return launch_general_2pass<5, 2, MINB>(a, st);
+            case 3: return launch_general_2pass<5, 3, MINB>(a, st);
+            case 4: return launch_general_2pass<5, 4, MINB>(a, st);
+        }
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <int V, int MINB>
@@ -358,6 +463,7 @@ cudaError_t dispatch_init(int Q, int S, const InitArgs &a, cudaStream_t st) {
 
 const GeneralVariant kGeneralVariants[] = {
     {"general_1site", 1}, {"general_2site", 2}, {"general_4site", 4}, {"general_2site_minb3", 2},
+    {"general_2pass_minb8", 1}, {"general_2pass_minb10", 1},
 };
 const int kGeneralVariantCount = sizeof(kGeneralVariants) / sizeof(kGeneralVariants[0]);
 
@@ -368,6 +474,8 @@ cudaError_t launch_step_general(int prec, int Q, int S, const StepArgs &a, cudaS
         case 1: return dispatch_vec<2, 4>(Q, S, a, st);
         case 2: return dispatch_vec<4, 2>(Q, S, a, st);
         case 3: return dispatch_vec<2, 3>(Q, S, a, st);
+        case 4: return dispatch_2pass<8>(Q, S, a, st);
+        case 5: return dispatch_2pass<10>(Q, S, a, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -77,3 +77,41 @@ def test_inplace_fp64_equals_oracle_and_checkpoints():
         c.init(rho0).step(13)
         with pytest.raises(B.LbRdError):
             c.restore(blob)  # the layouts differ
+
+
+@pytest.mark.parametrize("name,lat,S,kw,shape", [c for c in CASES if c[3]["precision"] == "fp32"],
+                         ids=[c[0] for c in CASES if c[3]["precision"] == "fp32"])
+@pytest.mark.parametrize("steps", [1, 6])
+def test_every_inplace_variant_equals_pingpong(name, lat, S, kw, shape, steps):
+    """Each FP32 in-place launch variant (1, 2 or 4 sites per thread; the
+    vector forms assemble the pushed columns with shuffles and edge-lane
+    scalar stores) gives the ping-pong bits, at odd and even times."""
+    nx, ny = shape
+    if nx % 4:
+        nx += 4 - nx % 4  # the vector variants need nx % 4 == 0
+    rho0 = _rho0(S, nx, ny, seed=steps)
+    with B.Simulation(lat, S, nx, ny, track_mass=True, **kw) as ref:
+        ref.init(rho0).step(steps)
+        want_rho, want_f = ref.moments()[0], ref.distributions()
+    with B.Simulation(lat, S, nx, ny, track_mass=True, inplace=True, **kw) as sim:
+        n = B.lb_rd_handle_variant_count(sim.h)
+        names = [B.lb_rd_handle_variant_name(sim.h, v) for v in range(n)]
+        assert names[0] == "aa_1site" and n >= 3
+        for v in range(n):
+            B.lb_rd_set_variant(sim.h, v)
+            sim.init(rho0).step(steps)
+            np.testing.assert_array_equal(sim.moments()[0], want_rho, err_msg=names[v])
+            np.testing.assert_array_equal(sim.distributions(), want_f, err_msg=names[v])
+
+
+def test_inplace_autotune_leaves_the_state_alone():
+    nx, ny = 256, 64
+    rho0 = _rho0(2, nx, ny, seed=5)
+    kw = dict(tau=[0.8, 0.65], reaction="gray_scott", F=0.04, k=0.06, precision="fp32")
+    with B.Simulation("D2Q9", 2, nx, ny, inplace=True, **kw) as sim, B.Simulation("D2Q9", 2, nx, ny, **kw) as ref:
+        sim.init(rho0).step(5)
+        best, times = B.lb_rd_autotune(sim.h, iters=3)
+        assert 0 <= best < B.lb_rd_handle_variant_count(sim.h) and times[best] > 0
+        sim.step(4)
+        ref.init(rho0).step(9)
+        np.testing.assert_array_equal(sim.moments()[0], ref.moments()[0])
