@@ -267,11 +267,13 @@ def serving_mode(args):
     arrivals = req["arrival_s"] / rate  # the seeded unit-rate stream, rescaled
     F, k = w["reaction"]["F"], w["reaction"]["k"]
 
-    def cfg(j):
+    def cfg(j, server=True):
         D = np.array(w["D"]) * scales[j]
+        # --inplace: the server keeps one state copy per request
+        inplace = bool(server and args.inplace)
         return dict(lattice="D2Q9", nspecies=2, nx=int(sides[j]), ny=int(sides[j]),
                     tau=[float(B.lb_rd_tau_from_diffusion(d)) for d in D], reaction="gray_scott", F=F, k=k,
-                    precision="fp32")
+                    precision="fp32", inplace=inplace)
 
     rho0s = [inputs.rho0_square(int(sides[j]), int(sides[j]), seed=w["seed"] + j) for j in range(nreq)]
 
@@ -303,7 +305,7 @@ def serving_mode(args):
         dt = arrivals[j] - (time.perf_counter() - t0)
         if dt > 0:
             time.sleep(dt)
-        with B.Simulation(**cfg(j)) as sim:
+        with B.Simulation(**cfg(j, server=False)) as sim:
             sim.init(rho0s[j]).step(int(steps[j]))
             sim.moments()
         lat_fifo.append(time.perf_counter() - t0 - arrivals[j])
@@ -314,7 +316,8 @@ def serving_mode(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "gs_serving", "requests": nreq, "steps_scale": args.steps_scale,
                        "load": args.load, "capacity_mlups": args.capacity_mlups, "budget_gb": args.budget_gb,
-                       "slots": args.slots, "steps_per_tick": args.tick, "arrival_rate_per_s": rate},
+                       "slots": args.slots, "steps_per_tick": args.tick, "arrival_rate_per_s": rate,
+                       "inplace_requests": int(sum(1 for j in range(nreq) if cfg(j)["inplace"]))},
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                           "max": float(np.max(lat))},
             "fifo_plain_loop": {"value": total / makespan_fifo / 1e6,

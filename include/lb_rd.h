@@ -128,8 +128,9 @@ typedef struct {
  *            reading neighbours and writing the swapped slots back to them
  *            (t even) and reading and writing a site's own slots (t odd), the
  *            "AA" pattern; the same bits as PINGPONG.  FP64 and FP32 storage;
- *            one launch variant; the last step of every lb_rd_step call also
- *            writes rho.  Not for batches, servers or lb_rd_step_noalloc. */
+ *            FP32 launch variants; the last step of every lb_rd_step call
+ *            also writes rho.  Batches and servers take in-place FP32
+ *            instances (one copy each); not for lb_rd_step_noalloc. */
 typedef enum { LB_RD_STREAM_PINGPONG = 0, LB_RD_STREAM_INPLACE = 1 } lb_rd_streaming;
 
 /* One simulation: the paper's statement of the problem. */

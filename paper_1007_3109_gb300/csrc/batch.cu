@@ -14,6 +14,7 @@
 
 #include "lb_rd.h"
 #include "lbrd_kernels.h"
+#include "step_aa_kernel.cuh"
 #include "step_f32_kernel.cuh"
 #include "step_f64_kernel.cuh"
 #include "step_half_kernel.cuh"
@@ -26,13 +27,16 @@ namespace {
 constexpr int kBX = 64, kBY = 2, kNT = kBX * kBY;  // the tile shape of both tile bodies
 static_assert(half::kBX == kBX && half::kBY == kBY, "tile shapes must agree");
 
-// MODE 0: FP32 storage, 1: bf16 deviations, 2: fp16 deviations, 3: FP64.
+// MODE 0: FP32 storage, 1: bf16 deviations, 2: fp16 deviations, 3: FP64,
+// 4: FP32 where some instances keep one copy updated in place (the AA tile
+// body of step_aa_kernel.cuh; BatchItem::aa selects the body per instance).
 // An FP64 tile covers the same 256 x 2 sites; a thread updates the sites
 // x = x_tile + threadIdx.x + 64 j, j < 4 (coalesced), one at a time.
 template <int Q, int S, int MODE>
 __global__ void __launch_bounds__(kNT, 4) batch_kernel(const BatchItem *__restrict__ items, int nitems,
                                                        int64_t total_tiles) {
     const int lane = threadIdx.x & 31;
+    __shared__ aa::AANet no_network;  // batched instances have no mass-action network; never read
     double acc[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[s] = 0.0;
@@ -53,8 +57,26 @@ __global__ void __launch_bounds__(kNT, 4) batch_kernel(const BatchItem *__restri
             }
         } else {
             const int64_t x0 = (tx * kBX + threadIdx.x) * 4;
-            if constexpr (MODE == 0) f32::tile_f32<Q, S, 0>(b.a, x0, y, lane, acc);
-            else half::tile_half<Q, S, MODE - 1>(b.a, x0, y, lane, acc);
+            if constexpr (MODE == 0) {
+                f32::tile_f32<Q, S, 0>(b.a, x0, y, lane, acc);
+            } else if constexpr (MODE == 4) {
+                if (b.aa == 0) {
+                    f32::tile_f32<Q, S, 0>(b.a, x0, y, lane, acc);
+                } else if (b.aa <= 2) {  // nx % 4 == 0: four sites per thread
+                    if (b.aa == 1) aa::tile_aa<Q, S, 4, 0>(b.a, no_network, x0, y, lane, acc);
+                    else aa::tile_aa<Q, S, 4, 1>(b.a, no_network, x0, y, lane, acc);
+                } else if (y < b.a.ny) {  // any nx: the tile's 256 x 2 sites one at a time, coalesced
+#pragma unroll 1
+                    for (int j = 0; j < 4; ++j) {
+                        const int64_t x = tx * kBX * 4 + threadIdx.x + j * kBX;
+                        if (x >= b.a.nx) continue;
+                        if (b.aa == 3) aa::site_aa<float, Q, S, 0>(b.a, no_network, x, y, acc);
+                        else aa::site_aa<float, Q, S, 1>(b.a, no_network, x, y, acc);
+                    }
+                }
+            } else {
+                half::tile_half<Q, S, MODE - 1>(b.a, x0, y, lane, acc);
+            }
         }
     }
 }
@@ -92,7 +114,7 @@ int batch_mode(int precision) {
 }
 
 cudaError_t launch_batch_init(int mode, int Q, int S, const InitArgs &a, cudaStream_t st) {
-    if (mode == 0) return launch_init_f32(Q, S, a, st);
+    if (mode == 0 || mode == 4) return launch_init_f32(Q, S, a, st);
     if (mode == 3) return launch_init_f64(Q, S, a, st);
     return launch_init_half(Q, S, mode == 2, a, st);
 }
@@ -108,6 +130,7 @@ cudaError_t launch_batch_step(int mode, int Q, int S, const BatchItem *items, in
         case 1: return dispatch_batch<1>(Q, S, items, n, total_tiles, st);
         case 2: return dispatch_batch<2>(Q, S, items, n, total_tiles, st);
         case 3: return dispatch_batch<3>(Q, S, items, n, total_tiles, st);
+        case 4: return dispatch_batch<4>(Q, S, items, n, total_tiles, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -118,7 +141,10 @@ struct lb_rd_batch {
     std::vector<lb_rd_config> cfgs;
     int Q = 0, S = 0, prec = 0, mode = 0;
     cudaStream_t stream = nullptr;
-    std::vector<size_t> state_off, rho_off;  // byte offsets of each instance
+    std::vector<size_t> state_off, rho_off;  // byte offsets of each instance (state: copy 0 in buf[0])
+    std::vector<size_t> state_off1;          // copy 1 in buf[1]; unused for in-place instances
+    std::vector<bool> inplace;
+    size_t state_total1 = 0;
     std::vector<int64_t> pitch;
     size_t state_total = 0, rho_total = 0;
     char *buf[2] = {nullptr, nullptr};
@@ -185,9 +211,12 @@ int lb_rd_batch_create(const lb_rd_config *cfgs, int32_t n, lb_rd_batch **out) {
     for (int i = 0; i < n; ++i) {
         int rc = lb_rd_check_config(&cfgs[i], nullptr);
         if (rc) return rc;
-        if (cfgs[i].nspecies > 2 || cfgs[i].reaction.kind == LB_RD_REACTION_MASS_ACTION || cfgs[i].streaming != 0)
-            return report_error(LB_RD_EINVAL, "lb_rd_batch_create: batches take at most two species, no "
-                                              "mass-action network and two state copies (instance " + std::to_string(i) + ")");
+        if (cfgs[i].nspecies > 2 || cfgs[i].reaction.kind == LB_RD_REACTION_MASS_ACTION)
+            return report_error(LB_RD_EINVAL, "lb_rd_batch_create: batches take at most two species and no "
+                                              "mass-action network (instance " + std::to_string(i) + ")");
+        if (cfgs[i].streaming == LB_RD_STREAM_INPLACE && cfgs[i].precision != LB_RD_FP32)
+            return report_error(LB_RD_EINVAL, "lb_rd_batch_create: in-place instances need FP32 storage "
+                                              "(instance " + std::to_string(i) + ")");
         if (cfgs[i].lattice != cfgs[0].lattice || cfgs[i].nspecies != cfgs[0].nspecies ||
             cfgs[i].precision != cfgs[0].precision)
             return report_error(LB_RD_EINVAL, "lb_rd_batch_create: instance " + std::to_string(i) +
@@ -207,6 +236,8 @@ int lb_rd_batch_create(const lb_rd_config *cfgs, int32_t n, lb_rd_batch **out) {
     b->S = cfgs[0].nspecies;
     b->prec = prec;
     b->mode = lbrd::batch_mode(prec);
+    for (int i = 0; i < n; ++i)
+        if (cfgs[i].streaming == LB_RD_STREAM_INPLACE) b->mode = 4;  // FP32 with in-place instances
     b->stream = static_cast<cudaStream_t>(cfgs[0].stream);
     b->inited.assign(n, false);
     size_t max_parts = 0;
@@ -215,9 +246,14 @@ int lb_rd_batch_create(const lb_rd_config *cfgs, int32_t n, lb_rd_batch **out) {
         const lb_rd_config &c = cfgs[i];
         const int64_t pitch = lbrd::pitch_for(c.nx);
         b->pitch.push_back(pitch);
+        const size_t sb = lbrd::align256(lbrd::state_plane_bytes(prec, b->Q, b->S, c.ny, pitch));
+        const bool ip = c.streaming == LB_RD_STREAM_INPLACE;
+        b->inplace.push_back(ip);
         b->state_off.push_back(b->state_total);
+        b->state_off1.push_back(ip ? 0 : b->state_total1);
         b->rho_off.push_back(b->rho_total);
-        b->state_total += lbrd::align256(lbrd::state_plane_bytes(prec, b->Q, b->S, c.ny, pitch));
+        b->state_total += sb;
+        if (!ip) b->state_total1 += sb;
         b->rho_total += lbrd::align256((size_t)b->S * c.ny * pitch * (prec == LB_RD_FP64 ? 8 : 4));
         const size_t parts = lbrd::mass_partials_needed(c.nx, c.ny);
         if (parts > max_parts) max_parts = parts;
@@ -238,7 +274,7 @@ int lb_rd_batch_create(const lb_rd_config *cfgs, int32_t n, lb_rd_batch **out) {
     }
     cudaError_t e = cudaSuccess;
     if (!e) e = cudaMalloc(&b->buf[0], b->state_total);
-    if (!e) e = cudaMalloc(&b->buf[1], b->state_total);
+    if (!e && b->state_total1) e = cudaMalloc(&b->buf[1], b->state_total1);
     if (!e) e = cudaMalloc(&b->rho, b->rho_total);
     if (!e) e = cudaMalloc(&b->partials, max_parts * b->S * sizeof(double));
     if (!e) e = cudaMalloc(&b->counter, sizeof(unsigned int));
@@ -249,8 +285,16 @@ int lb_rd_batch_create(const lb_rd_config *cfgs, int32_t n, lb_rd_batch **out) {
         const bool emit = k >= 2;
         std::vector<lbrd::BatchItem> v = items;
         for (int i = 0; i < n; ++i) {
-            v[i].a.src = b->buf[parity] + b->state_off[i];
-            v[i].a.dst = b->buf[parity ^ 1] + b->state_off[i];
+            char *c0 = b->buf[0] + b->state_off[i];
+            if (b->inplace[i]) {
+                v[i].a.src = v[i].a.dst = c0;
+                v[i].aa = (cfgs[i].nx % 4 == 0 ? 1 : 3) + parity;
+            } else {
+                char *c1 = b->buf[1] + b->state_off1[i];
+                v[i].a.src = parity ? c1 : c0;
+                v[i].a.dst = parity ? c0 : c1;
+                v[i].aa = 0;
+            }
             v[i].a.rho_out = emit ? b->rho + b->rho_off[i] : nullptr;
         }
         e = cudaMalloc(&b->d_items[k], n * sizeof(lbrd::BatchItem));
@@ -295,7 +339,7 @@ int lb_rd_batch_init(lb_rd_batch *b, int32_t idx, const double *rho0, int is_dev
     }
     lbrd::InitArgs a{};
     a.rho0 = src;
-    a.dst = b->buf[b->cur] + b->state_off[idx];
+    a.dst = b->buf[0] + b->state_off[idx];  // t == 0: copy 0 (the only copy of an in-place instance)
     a.nx = c.nx;
     a.ny = c.ny;
     a.pitch = b->pitch[idx];

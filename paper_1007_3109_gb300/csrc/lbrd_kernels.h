@@ -136,10 +136,13 @@ struct BatchItem {
     StepArgs a;          // per-instance grid, parameters and buffers
     int64_t tiles_x;     // tiles per row of tiles, ceil(ceil(nx / 4) / 64)
     int64_t tile_begin;  // first global tile of this instance
+    int aa;              // FP32: 0 two state copies; in place (a.src == a.dst), phase A (t even) / B:
+                         // 1 / 2 four sites per thread (nx % 4 == 0), 3 / 4 one site per thread
 };
 int64_t batch_tiles_x(int64_t nx);
 int64_t batch_tiles(int64_t nx, int64_t ny);
-// mode: 0 FP32 storage, 1 bf16 deviations, 2 fp16 deviations, 3 FP64.
+// mode: 0 FP32 storage, 1 bf16 deviations, 2 fp16 deviations, 3 FP64,
+// 4 FP32 with in-place instances (BatchItem::aa).
 int batch_mode(int precision);
 cudaError_t launch_batch_init(int mode, int Q, int S, const InitArgs &a, cudaStream_t st);
 cudaError_t launch_batch_step(int mode, int Q, int S, const BatchItem *items, int n, int64_t total_tiles,

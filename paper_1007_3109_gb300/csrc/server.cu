@@ -63,7 +63,8 @@ struct Request {
 size_t request_bytes(const lb_rd_config &c, int Q, int64_t pitch, size_t *state_bytes, size_t *rho_bytes) {
     *state_bytes = lbrd::state_plane_bytes(c.precision, Q, c.nspecies, c.ny, pitch);
     *rho_bytes = (size_t)c.nspecies * c.ny * pitch * (c.precision == LB_RD_FP64 ? 8 : 4);
-    return 2 * *state_bytes + *rho_bytes;
+    const size_t copies = c.streaming == LB_RD_STREAM_INPLACE ? 1 : 2;
+    return copies * *state_bytes + *rho_bytes;
 }
 
 }  // namespace
@@ -108,9 +109,9 @@ void finish(lb_rd_server *s, Request *r, int status) {
 }
 
 void release(lb_rd_server *s, Request *r) {
-    cudaFreeAsync(r->buf[0], s->stream);
-    cudaFreeAsync(r->buf[1], s->stream);
-    cudaFreeAsync(r->rho, s->stream);
+    if (r->buf[0]) cudaFreeAsync(r->buf[0], s->stream);
+    if (r->buf[1]) cudaFreeAsync(r->buf[1], s->stream);
+    if (r->rho) cudaFreeAsync(r->rho, s->stream);
     r->buf[0] = r->buf[1] = nullptr;
     r->rho = nullptr;
     std::lock_guard<std::mutex> lock(s->mu);
@@ -124,7 +125,7 @@ bool start_request(lb_rd_server *s, Request *r) {
     double *stage = nullptr;
     const size_t n = (size_t)c.nspecies * c.ny * c.nx;
     if (!e) e = cudaMallocAsync((void **)&r->buf[0], r->state_bytes, s->stream);
-    if (!e) e = cudaMallocAsync((void **)&r->buf[1], r->state_bytes, s->stream);
+    if (!e && c.streaming != LB_RD_STREAM_INPLACE) e = cudaMallocAsync((void **)&r->buf[1], r->state_bytes, s->stream);
     if (!e) e = cudaMallocAsync((void **)&r->rho, r->rho_bytes, s->stream);
     if (!e) e = cudaMallocAsync((void **)&stage, n * sizeof(double), s->stream);
     if (!e) e = cudaMemcpyAsync(stage, r->rho0.data(), n * sizeof(double), cudaMemcpyHostToDevice, s->stream);
@@ -212,6 +213,7 @@ void run_tick(lb_rd_server *s) {
     }
     // descriptor sets: [0] even steps, [1] odd steps, [2] the tick's last step (writes rho)
     int64_t total = 0;
+    bool any_inplace = false;
     for (size_t i = 0; i < n; ++i) {
         Request *r = act[i];
         const lb_rd_config &c = r->cfg;
@@ -231,8 +233,14 @@ void run_tick(lb_rd_server *s) {
         for (int set = 0; set < 3; ++set) {
             const int par = set < 2 ? (r->cur + set) & 1 : (int)((r->cur + tick - 1) & 1);
             lbrd::BatchItem v = it;
-            v.a.src = r->buf[par];
-            v.a.dst = r->buf[par ^ 1];
+            if (c.streaming == LB_RD_STREAM_INPLACE) {
+                v.a.src = v.a.dst = r->buf[0];
+                v.aa = (c.nx % 4 == 0 ? 1 : 3) + par;
+                any_inplace = true;
+            } else {
+                v.a.src = r->buf[par];
+                v.a.dst = r->buf[par ^ 1];
+            }
             v.a.rho_out = set == 2 ? r->rho : nullptr;
             s->h_items[set * n + i] = v;
         }
@@ -242,7 +250,7 @@ void run_tick(lb_rd_server *s) {
     const int S = s->cfg.nspecies;
     for (int64_t k = 0; k < tick && !e; ++k) {
         const lbrd::BatchItem *items = s->d_items + (k == tick - 1 ? 2 : (k & 1)) * n;
-        e = lbrd::launch_batch_step(s->mode, s->Q, S, items, (int)n, total, s->stream);
+        e = lbrd::launch_batch_step(any_inplace ? 4 : s->mode, s->Q, S, items, (int)n, total, s->stream);
         s->launches++;
     }
     if (!e) e = cudaStreamSynchronize(s->stream);  // the pinned descriptors are reused next tick
@@ -366,9 +374,9 @@ int lb_rd_server_destroy(lb_rd_server *s) {
     if (s->worker.joinable()) s->worker.join();
     cudaSetDevice(s->device);
     for (Request *r : s->active) {
-        cudaFreeAsync(r->buf[0], s->stream);
-        cudaFreeAsync(r->buf[1], s->stream);
-        cudaFreeAsync(r->rho, s->stream);
+        if (r->buf[0]) cudaFreeAsync(r->buf[0], s->stream);
+        if (r->buf[1]) cudaFreeAsync(r->buf[1], s->stream);
+        if (r->rho) cudaFreeAsync(r->rho, s->stream);
     }
     cudaStreamSynchronize(s->stream);
     for (auto &kv : s->all) delete kv.second;
@@ -388,8 +396,10 @@ int lb_rd_submit(lb_rd_server *s, const lb_rd_config *cfg, const double *rho0, i
     if (rc) return rc;
     if (cfg->lattice != s->cfg.lattice || cfg->nspecies != s->cfg.nspecies || cfg->precision != s->cfg.precision)
         return lbrd::report_error(LB_RD_EINVAL, "lb_rd_submit: lattice, nspecies and precision must match the server");
-    if (cfg->reaction.kind == LB_RD_REACTION_MASS_ACTION || cfg->streaming != 0)
-        return lbrd::report_error(LB_RD_EINVAL, "lb_rd_submit: serving takes no mass-action network and no in-place state");
+    if (cfg->reaction.kind == LB_RD_REACTION_MASS_ACTION)
+        return lbrd::report_error(LB_RD_EINVAL, "lb_rd_submit: serving takes no mass-action network");
+    if (cfg->streaming == LB_RD_STREAM_INPLACE && cfg->precision != LB_RD_FP32)
+        return lbrd::report_error(LB_RD_EINVAL, "lb_rd_submit: in-place requests need FP32 storage");
     if ((s->mode == 1 || s->mode == 2) && cfg->nx % 4)
         return lbrd::report_error(LB_RD_EINVAL, "lb_rd_submit: 16-bit deviation storage needs nx % 4 == 0");
     if (nsteps < 1) return lbrd::report_error(LB_RD_EINVAL, "lb_rd_submit: nsteps must be >= 1");

@@ -142,7 +142,12 @@ __device__ __forceinline__ void collide_site(const StepArgs &a, float (&f)[S][Q]
     }
 }
 
-template <int Q, int S, int NT, int TX, int NS, int MINB>
+// IL = 1 (needs NT >= TX + 2): thread t computes level-1 site t and level-2
+// site t of the iteration in one straight-line block (both sets of shared
+// loads issued before either collision, from clamped valid addresses; the
+// stores are predicated), instead of the items one after the other.  The
+// arithmetic of every site is unchanged.
+template <int Q, int S, int NT, int TX, int NS, int MINB, int IL>
 __global__ void __launch_bounds__(NT, MINB) step_tb2_kernel(StepArgs a, int64_t nstrips) {
     using L = Lattice<Q>;
     using G = TbGeom<Q, S, TX>;
@@ -202,7 +207,38 @@ __global__ void __launch_bounds__(NT, MINB) step_tb2_kernel(StepArgs a, int64_t 
             const float *rows1[3] = {ring + ((jm + 1u) & 3u) * G::kRow1, ring + ((jm + 2u) & 3u) * G::kRow1,
                                      ring + ((jm + 3u) & 3u) * G::kRow1};
             const int64_t y = y0 + j - 3;
-            for (int it = tid; it < kItems; it += NT) {
+            if constexpr (IL == 1) {
+                static_assert(NT >= kL1, "interleaved items need a thread per level-1 site");
+                const bool a1 = do1 && tid < kL1, a2 = do2 && tid < TX;
+                const int k1 = (tid < kL1 ? tid : kL1 - 1) + 3;
+                const int k2 = tid < TX ? tid : TX - 1;
+                float f1[S][Q], f2[S][Q], rho1[S], rho2[S];
+#pragma unroll
+                for (int s = 0; s < S; ++s)
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        f1[s][i] = st[(s * Q + i) * G::W0 + k1 - L::ex(i)];
+                        f2[s][i] = rows1[1 - L::ey(i)][(s * Q + i) * G::W1 + k2 + 4 - L::ex(i)];
+                    }
+                collide_site<Q, S>(a, f1, rho1);
+                collide_site<Q, S>(a, f2, rho2);
+                if (a1) {
+#pragma unroll
+                    for (int s = 0; s < S; ++s)
+#pragma unroll
+                        for (int i = 0; i < Q; ++i) r1[(s * Q + i) * G::W1 + k1] = f1[s][i];
+                }
+                if (a2) {
+                    const int64_t x = x0 + k2;
+#pragma unroll
+                    for (int s = 0; s < S; ++s) {
+#pragma unroll
+                        for (int i = 0; i < Q; ++i) dst[(int64_t)(s * Q + i) * a.plane + y * a.pitch + x] = f2[s][i];
+                        sum[s] += rho2[s];
+                    }
+                }
+            }
+            for (int it = tid; IL == 0 && it < kItems; it += NT) {
                 float f[S][Q], rho[S];
                 if (it < kL1) {
                     if (!do1) continue;
@@ -258,13 +294,13 @@ __global__ void __launch_bounds__(NT, MINB) step_tb2_kernel(StepArgs a, int64_t 
     if (a.mass_out) block_mass_reduce<S, NT>(acc, a.partials, a.counter, a.mass_out);
 }
 
-template <int Q, int S, int NT, int TX, int NS, int MINB>
+template <int Q, int S, int NT, int TX, int NS, int MINB, int IL>
 cudaError_t launch_tb(const StepArgs &a, cudaStream_t st) {
     using G = TbGeom<Q, S, TX>;
     if (a.nx % TX != 0) return cudaErrorInvalidValue;
     const int64_t nstrips = a.nx / TX;
     const size_t smem = ((size_t)NS * G::kStage + 4 * (size_t)G::kRow1) * sizeof(float);
-    auto kern = step_tb2_kernel<Q, S, NT, TX, NS, MINB>;
+    auto kern = step_tb2_kernel<Q, S, NT, TX, NS, MINB, IL>;
     static bool configured[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -280,12 +316,12 @@ cudaError_t launch_tb(const StepArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int NT, int TX, int NS, int MINB>
+template <int NT, int TX, int NS, int MINB, int IL = 0>
 cudaError_t dispatch_tb(int Q, int S, const StepArgs &a, cudaStream_t st) {
-    if (Q == 9 && S == 1) return launch_tb<9, 1, NT, TX, NS, MINB>(a, st);
-    if (Q == 9 && S == 2) return launch_tb<9, 2, NT, TX, NS, MINB>(a, st);
-    if (Q == 5 && S == 1) return launch_tb<5, 1, NT, TX, NS, MINB>(a, st);
-    if (Q == 5 && S == 2) return launch_tb<5, 2, NT, TX, NS, MINB>(a, st);
+    if (Q == 9 && S == 1) return launch_tb<9, 1, NT, TX, NS, MINB, IL>(a, st);
+    if (Q == 9 && S == 2) return launch_tb<9, 2, NT, TX, NS, MINB, IL>(a, st);
+    if (Q == 5 && S == 1) return launch_tb<5, 1, NT, TX, NS, MINB, IL>(a, st);
+    if (Q == 5 && S == 2) return launch_tb<5, 2, NT, TX, NS, MINB, IL>(a, st);
     return cudaErrorInvalidValue;
 }
 
@@ -301,6 +337,10 @@ cudaError_t launch_step_f32_tb2(int v, int Q, int S, const StepArgs &a, cudaStre
         case 3: return dispatch_tb<352, 512, 2, 1>(Q, S, a, st);
         case 4: return dispatch_tb<288, 256, 2, 2>(Q, S, a, st);
         case 5: return dispatch_tb<544, 512, 2, 1>(Q, S, a, st);
+        case 6: return dispatch_tb<288, 256, 2, 2, 1>(Q, S, a, st);
+        case 7: return dispatch_tb<544, 512, 2, 1, 1>(Q, S, a, st);
+        case 8: return dispatch_tb<160, 128, 4, 2, 1>(Q, S, a, st);
+        case 9: return dispatch_tb<288, 256, 3, 1, 1>(Q, S, a, st);
         default: return cudaErrorInvalidValue;
     }
 }

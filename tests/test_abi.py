@@ -143,5 +143,7 @@ def test_inplace_config_validation_and_size(lib):
     with pytest.raises(B.LbRdError):
         B.lb_rd_check_config(cfg)
     out = B.c_void_p()
-    cfgs = (B.lb_rd_config * 1)(B.make_config(**base, inplace=True))
-    assert lib.lb_rd_batch_create(cfgs, 1, B.ctypes.byref(out)) == B.LB_RD_EINVAL
+    # batches take in-place FP32 instances only (checked before any device call)
+    for bad in (dict(base, precision="fp64"),):
+        cfgs = (B.lb_rd_config * 1)(B.make_config(**bad, inplace=True))
+        assert lib.lb_rd_batch_create(cfgs, 1, B.ctypes.byref(out)) == B.LB_RD_EINVAL

@@ -112,3 +112,22 @@ def test_phase_diagram_sweep_full_size_sampled():
             ref = orc.density("D2Q9", orc.run("D2Q9", taus, reac, orc.init("D2Q9", rho0), T))
             err = np.max(np.abs(rho - ref), axis=(1, 2)) / np.maximum(np.max(np.abs(ref), axis=(1, 2)), 1e-4)
             assert np.all(err <= 5e-5), (i, err)
+
+
+def test_batch_with_inplace_instances_equals_single_handles():
+    """A batch mixing one-copy (in-place) and two-copy FP32 instances: every
+    instance gives the bits of a single two-copy handle, at odd and even
+    batch times, with and without graphs."""
+    extra = dict(_configs("fp32")[0], nx=70, ny=9)  # nx % 4 != 0: one site per thread in place
+    cfgs = _configs("fp32") + [extra, dict(extra, nx=37, ny=5)]
+    cfgs = [dict(c, inplace=(j != 1)) for j, c in enumerate(cfgs)]
+    for graph, steps in ((0, 23), (8, 40)):
+        with B.Batch(cfgs) as b:
+            b.set_graph(graph)
+            for j, c in enumerate(cfgs):
+                b.init(j, _rho0(c, j))
+            b.step(steps)
+            for j, c in enumerate(cfgs):
+                rho, _ = b.moments(j)
+                ref_rho, _ = _single(dict(c, inplace=False), _rho0(c, j), steps)
+                np.testing.assert_array_equal(rho, ref_rho, err_msg=f"instance {j} graph {graph}")

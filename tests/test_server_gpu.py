@@ -146,3 +146,39 @@ def test_fp64_server_equals_oracle_bitwise():
             assert abs(mass.sum() - 1.0) < 1e-13
     finally:
         B.lb_rd_server_destroy(srv)
+
+
+def test_inplace_requests_mix_and_double_the_residents():
+    """In-place (one state copy) FP32 requests next to two-copy ones give the
+    single-handle bits; under a budget that holds one two-copy request, two
+    in-place requests are resident at once."""
+    kw, rho0, _ = _request(40, 128, 1, 60)
+    kw2, rho2, _ = _request(41, 70, 2, 45)  # nx % 4 != 0: one site per thread
+    reqs = [(dict(kw, inplace=True), rho0, 60), (kw, rho0, 61), (dict(kw, inplace=True), rho0, 33),
+            (dict(kw2, inplace=True), rho2, 45)]
+    srv = B.lb_rd_server_create(hbm_budget_bytes=1 << 30, max_slots=4, steps_per_tick=16)
+    try:
+        ts = [B.lb_rd_submit(srv, B.make_config(**c), r, n) for c, r, n in reqs]
+        for (c, r, n), t in zip(reqs, ts):
+            rc, rho, _, _ = _wait(srv, t, 2, c["nx"])
+            assert rc == B.LB_RD_OK
+            ref, _ = _alone(dict(c, inplace=False), r, n)
+            np.testing.assert_array_equal(rho, ref)
+    finally:
+        B.lb_rd_server_destroy(srv)
+    state = 2 * 9 * 128 * 128 * 4
+    rho_b = 2 * 128 * 128 * 4
+    budget = int(2 * (state + rho_b) * 1.02)  # two one-copy requests, but one two-copy request only
+    for inplace, concurrent in ((True, True), (False, False)):
+        srv = B.lb_rd_server_create(hbm_budget_bytes=budget, max_slots=4, steps_per_tick=8)
+        try:
+            c = dict(kw, inplace=inplace)
+            t1 = B.lb_rd_submit(srv, B.make_config(**c), rho0, 400)
+            t2 = B.lb_rd_submit(srv, B.make_config(**c), rho0, 400)
+            B.lb_rd_server_drain(srv, 60000)
+            _, r1, _, s1 = _wait(srv, t1, 2, 128)
+            _, r2, _, s2 = _wait(srv, t2, 2, 128)
+            np.testing.assert_array_equal(r1, r2)
+            assert (s2["start_ns"] < s1["end_ns"]) == concurrent, (inplace, s1, s2)
+        finally:
+            B.lb_rd_server_destroy(srv)

@@ -5,6 +5,8 @@ bulk-copy staging) performs the same per-site operations in the same order,
 so their states must agree bit for bit; the autotuner must not advance or
 change the simulation state.
 """
+import re
+
 import numpy as np
 import pytest
 
@@ -43,10 +45,9 @@ def test_every_fp32_variant_is_bitwise_identical(grid):
         name = B.lb_rd_variant_name("fp32", v)
         out = _run(lat, S, nx, ny, reac, v)
         if out is None:
-            # bulk-copy variants need nx % 4 == 0, two-step variants nx % strip == 0
-            strip = {"tb2_288x128_s8": 128, "tb2_288x128_s4x2": 128, "tb2_288x256_s6": 256, "tb2_352x512_s2": 512,
-                     "tb2_288x256_s2x2": 256, "tb2_544x512_s2": 512}
-            assert (name.startswith("bulk") and nx % 4) or (name in strip and nx % strip[name]), name
+            # bulk-copy variants need nx % 4 == 0, two-step variants (tb2[i]_<threads>x<strip>_...) nx % strip == 0
+            m = re.match(r"tb2i?_\d+x(\d+)_", name)
+            assert (name.startswith("bulk") and nx % 4) or (m and nx % int(m.group(1))), name
             continue
         ran += 1
         rho, mass, f = out
