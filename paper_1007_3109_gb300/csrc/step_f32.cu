@@ -66,6 +66,10 @@ const F32Variant kF32Variants[] = {
     {"tb2i_544x512_s2", 544, 512, 2, 3, 2, 512},
     {"tb2i_160x128_s4x2", 160, 128, 4, 3, 2, 128},
     {"tb2i_288x256_s3", 288, 256, 3, 3, 2, 256},
+    {"tb2w_288x256_s2x2", 288, 256, 2, 3, 2, 256},
+    {"tb2w_288x256_s4", 288, 256, 4, 3, 2, 256},
+    {"tb2w_160x128_s3x3", 160, 128, 3, 3, 2, 128},
+    {"tb2w_544x512_s2", 544, 512, 2, 3, 2, 512},
 };
 const int kF32VariantCount = sizeof(kF32Variants) / sizeof(kF32Variants[0]);
 

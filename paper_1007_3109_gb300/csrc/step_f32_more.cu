@@ -13,6 +13,7 @@ cudaError_t launch_step_f32_variant_b(int v, int Q, int S, const StepArgs &a, cu
         case 8: case 9: case 10: case 11: case 12: case 13:
             return per_tile ? cudaErrorInvalidValue : launch_step_f32_bulk(v - 8, Q, S, a, st);
         case 14: case 15: case 16: case 17: case 18: case 19: case 20: case 21: case 22: case 23:
+        case 24: case 25: case 26: case 27:
             return per_tile ? cudaErrorInvalidValue : launch_step_f32_tb2(v - 14, Q, S, a, st);
         default: return cudaErrorInvalidValue;
     }

@@ -294,6 +294,194 @@ __global__ void __launch_bounds__(NT, MINB) step_tb2_kernel(StepArgs a, int64_t 
     if (a.mass_out) block_mass_reduce<S, NT>(acc, a.partials, a.counter, a.mass_out);
 }
 
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Warp-decoupled two-step kernel: W consumer warps and one producer warp.
+// The block's strip is TX = 32 W columns; consumer warp w owns the 32
+// columns c0 = x0 + 32 w ... and computes level 1 on its 34 columns
+// [c0 - 1, c0 + 33) (recomputing the two halo columns its neighbours also
+// compute) into a ring of three level-1 rows private to the warp, and level
+// 2 of its 32 columns from that ring, so the warp synchronises only with
+// itself: each iteration loads everything it needs (the level-0 stage and
+// ring rows j - 3 .. j - 1), passes __syncwarp, and only then overwrites the
+// ring slot of row j - 3 with level-1 row j.  Level-0 rows arrive by TMA bulk
+// copy into NS block-shared stages: the producer warp refills stage k once
+// every consumer warp has arrived on its "empty" barrier (count W) and the
+// copies complete on its "full" barrier.  Every wait is bounded (status
+// word, drain, return); the arithmetic of every site is the one-step
+// kernels'.
+template <int Q, int S, int W, int NS, int MINB>
+__global__ void __launch_bounds__((W + 1) * 32, MINB) step_tbw_kernel(StepArgs a, int64_t nstrips) {
+    using L = Lattice<Q>;
+    constexpr int TX = 32 * W;
+    using G = TbGeom<Q, S, TX>;
+    constexpr int RW = 34;                // ring row width: the warp's 34 level-1 columns
+    constexpr int kRing = S * Q * RW;     // one level-1 row of one warp
+    extern __shared__ __align__(128) float smem[];
+    float *stages = smem;                 // NS level-0 stages of the strip
+    float *rings = smem + NS * G::kStage; // [W][3] level-1 rows
+    __shared__ __align__(8) unsigned long long full[NS], empty[NS];
+    __shared__ volatile int abort_flag;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    float *__restrict__ dst = static_cast<float *>(a.dst);
+    if (tid == 0) {
+        for (int k = 0; k < NS; ++k) {
+            mbar_init(smem_u32(&full[k]), 1);
+            mbar_init(smem_u32(&empty[k]), W);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+    }
+    __syncthreads();
+    double acc[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) acc[s] = 0.0;
+    int64_t ticket = 0;  // level-0 rows (stages) used by this block so far
+    int64_t issued = 0;  // producer: rows issued
+    const int64_t total = nstrips * a.ny;
+    const int64_t u_end = total * (blockIdx.x + 1) / gridDim.x;
+    float *ring = rings + (w < W ? w : 0) * 3 * kRing;
+    for (int64_t u = total * blockIdx.x / gridDim.x; u < u_end;) {
+        const int64_t strip = u / a.ny;
+        const int64_t y0 = u - strip * a.ny;
+        const int64_t ly = (a.ny - y0 < u_end - u) ? a.ny - y0 : u_end - u;
+        u += ly;
+        const int64_t x0 = strip * TX;
+        const int64_t nrows = ly + 2;
+        // Every decision below is warp-uniform (__any_sync / __all_sync), so the
+        // lanes of a warp always take the same path to each __syncwarp.
+        if (w == W) {  // producer
+            for (int64_t j = 0; j < nrows; ++j) {
+                if (__any_sync(kFullMask, abort_flag != 0)) break;
+                const int64_t tk = ticket + j;
+                const int sk = (int)(tk % NS);
+                const bool ok = tk < NS || mbar_wait(smem_u32(&empty[sk]), (unsigned)(((tk / NS) - 1) & 1));
+                if (!__all_sync(kFullMask, ok)) {
+                    abort_flag = 1;
+                    break;
+                }
+                // the consumers' reads of this stage (generic proxy) before the copies into it (async proxy)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue_row<Q, S, TX>(a, y0 - 1 + j, x0, stages + sk * G::kStage, smem_u32(&full[sk]),
+                                    (a.inject_timeout && blockIdx.x == 0 && tk == 0) ? 16u : 0u);
+                issued = tk + 1;
+            }
+        } else {  // consumer warp w
+            const int64_t c0 = x0 + 32 * w;
+            const int k1 = 32 * w + 3 + lane;  // stage slot of ring column `lane` (column c0 - 1 + lane)
+            float sum[S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) sum[s] = 0.f;
+            int m3 = 0;  // j % 3
+            for (int64_t j = 0; j <= nrows; ++j, m3 = m3 == 2 ? 0 : m3 + 1) {
+                if (__any_sync(kFullMask, abort_flag != 0)) break;
+                const bool do1 = j < nrows, do2 = j >= 3;
+                const int64_t tk = ticket + j;
+                const int sk = (int)(tk % NS);
+                const bool ok = !do1 || mbar_wait(smem_u32(&full[sk]), (unsigned)((tk / NS) & 1));
+                if (!__all_sync(kFullMask, ok)) {
+                    abort_flag = 1;
+                    break;
+                }
+                const float *st = stages + sk * G::kStage;
+                // ring slots: row j (written) and rows j - 3, j - 2, j - 1 (read) are j % 3, j % 3, +1, +2
+                float *r1 = ring + m3 * kRing;
+                const float *rows1[3] = {ring + m3 * kRing, ring + (m3 == 2 ? 0 : m3 + 1) * kRing,
+                                         ring + (m3 == 0 ? 2 : m3 - 1) * kRing};
+                const int64_t y = y0 + j - 3;
+                float f1[S][Q], f2[S][Q], rho1[S], rho2[S];
+#pragma unroll
+                for (int s = 0; s < S; ++s)
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        f1[s][i] = st[(s * Q + i) * G::W0 + k1 - L::ex(i)];
+                        f2[s][i] = rows1[1 - L::ey(i)][(s * Q + i) * RW + lane + 1 - L::ex(i)];
+                    }
+                __syncwarp();  // every lane has read ring row j - 3 before it is overwritten
+                collide_site<Q, S>(a, f1, rho1);
+                collide_site<Q, S>(a, f2, rho2);
+                if (do1) {
+#pragma unroll
+                    for (int s = 0; s < S; ++s)
+#pragma unroll
+                        for (int i = 0; i < Q; ++i) r1[(s * Q + i) * RW + lane] = f1[s][i];
+                    if (lane < 2) {  // ring columns 32, 33: columns c0 + 31, c0 + 32
+#pragma unroll
+                        for (int s = 0; s < S; ++s)
+#pragma unroll
+                            for (int i = 0; i < Q; ++i) f1[s][i] = st[(s * Q + i) * G::W0 + k1 + 32 - L::ex(i)];
+                        collide_site<Q, S>(a, f1, rho1);
+#pragma unroll
+                        for (int s = 0; s < S; ++s)
+#pragma unroll
+                            for (int i = 0; i < Q; ++i) r1[(s * Q + i) * RW + lane + 32] = f1[s][i];
+                    }
+                }
+                if (do2) {
+                    const int64_t x = c0 + lane;
+#pragma unroll
+                    for (int s = 0; s < S; ++s) {
+#pragma unroll
+                        for (int i = 0; i < Q; ++i) dst[(int64_t)(s * Q + i) * a.plane + y * a.pitch + x] = f2[s][i];
+                        sum[s] += rho2[s];
+                    }
+                }
+                __syncwarp();  // stage reads and ring writes of this row are done
+                if (do1 && lane == 0) mbar_arrive(smem_u32(&empty[sk]));
+            }
+            if (a.mass_out) {
+#pragma unroll
+                for (int s = 0; s < S; ++s) acc[s] += (double)sum[s];
+            }
+        }
+        ticket += nrows;
+        if (__any_sync(kFullMask, abort_flag != 0)) break;
+    }
+    if (w == W && abort_flag) {  // wait (bounded) for the copies that may still be in flight
+        for (int64_t tk = issued - NS > 0 ? issued - NS : 0; tk < issued; ++tk)
+            mbar_wait(smem_u32(&full[tk % NS]), (unsigned)((tk / NS) & 1));
+    }
+    __syncthreads();
+    if (abort_flag) {
+        if (tid == 0 && a.status) atomicExch(a.status, LB_RD_ETIMEOUT);
+        return;
+    }
+    if (a.mass_out) block_mass_reduce<S, (W + 1) * 32>(acc, a.partials, a.counter, a.mass_out);
+}
+
+template <int Q, int S, int W, int NS, int MINB>
+cudaError_t launch_tbw(const StepArgs &a, cudaStream_t st) {
+    constexpr int TX = 32 * W;
+    using G = TbGeom<Q, S, TX>;
+    if (a.nx % TX != 0) return cudaErrorInvalidValue;
+    const int64_t nstrips = a.nx / TX;
+    const size_t smem = ((size_t)NS * G::kStage + (size_t)W * 3 * S * Q * 34) * sizeof(float);
+    auto kern = step_tbw_kernel<Q, S, W, NS, MINB>;
+    static bool configured[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !configured[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured[dev] = true;
+    }
+    const int64_t work = nstrips * a.ny / 16 > 0 ? nstrips * a.ny / 16 : 1;
+    const unsigned grid = persistent_blocks(kern, (W + 1) * 32, work, smem);
+    kern<<<grid, (W + 1) * 32, smem, st>>>(a, nstrips);
+    return cudaGetLastError();
+}
+
+template <int W, int NS, int MINB>
+cudaError_t dispatch_tbw(int Q, int S, const StepArgs &a, cudaStream_t st) {
+    if (Q == 9 && S == 1) return launch_tbw<9, 1, W, NS, MINB>(a, st);
+    if (Q == 9 && S == 2) return launch_tbw<9, 2, W, NS, MINB>(a, st);
+    if (Q == 5 && S == 1) return launch_tbw<5, 1, W, NS, MINB>(a, st);
+    if (Q == 5 && S == 2) return launch_tbw<5, 2, W, NS, MINB>(a, st);
+    return cudaErrorInvalidValue;
+}
+
 template <int Q, int S, int NT, int TX, int NS, int MINB, int IL>
 cudaError_t launch_tb(const StepArgs &a, cudaStream_t st) {
     using G = TbGeom<Q, S, TX>;
@@ -341,6 +529,10 @@ cudaError_t launch_step_f32_tb2(int v, int Q, int S, const StepArgs &a, cudaStre
         case 7: return dispatch_tb<544, 512, 2, 1, 1>(Q, S, a, st);
         case 8: return dispatch_tb<160, 128, 4, 2, 1>(Q, S, a, st);
         case 9: return dispatch_tb<288, 256, 3, 1, 1>(Q, S, a, st);
+        case 10: return dispatch_tbw<8, 2, 2>(Q, S, a, st);
+        case 11: return dispatch_tbw<8, 4, 1>(Q, S, a, st);
+        case 12: return dispatch_tbw<4, 3, 3>(Q, S, a, st);
+        case 13: return dispatch_tbw<16, 2, 1>(Q, S, a, st);
         default: return cudaErrorInvalidValue;
     }
 }

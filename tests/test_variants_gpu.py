@@ -45,8 +45,8 @@ def test_every_fp32_variant_is_bitwise_identical(grid):
         name = B.lb_rd_variant_name("fp32", v)
         out = _run(lat, S, nx, ny, reac, v)
         if out is None:
-            # bulk-copy variants need nx % 4 == 0, two-step variants (tb2[i]_<threads>x<strip>_...) nx % strip == 0
-            m = re.match(r"tb2i?_\d+x(\d+)_", name)
+            # bulk-copy variants need nx % 4 == 0, two-step variants (tb2[iw]_<threads>x<strip>_...) nx % strip == 0
+            m = re.match(r"tb2[iw]?_\d+x(\d+)_", name)
             assert (name.startswith("bulk") and nx % 4) or (m and nx % int(m.group(1))), name
             continue
         ran += 1

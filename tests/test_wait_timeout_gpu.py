@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.timeout(120)
-@pytest.mark.parametrize("variant", ["bulk256_s2", "tb2_352x512_s2"])
+@pytest.mark.parametrize("variant", ["bulk256_s2", "tb2_352x512_s2", "tb2w_288x256_s2x2"])
 def test_bounded_wait_reports_timeout_and_context_survives(variant):
     nx, ny = 512, 24
     rho0 = inputs.rho0_square(nx, ny, seed=77, side=8)
