@@ -41,6 +41,18 @@ __device__ __forceinline__ unsigned f2h(float v) {
     return (unsigned)__half_as_ushort(__float2half_rn(v));
 }
 
+// Two values rounded to nearest even and packed (lo in bits 0-15): the bits
+// of f2h(lo) | f2h(hi) << 16, in one paired conversion.
+template <int H>
+__device__ __forceinline__ unsigned f2h2(float lo, float hi) {
+    if (H == 0) {
+        const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<const unsigned *>(&v);
+    }
+    const __half2 v = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const unsigned *>(&v);
+}
+
 struct Cols {
     int64_t xc, xl, xr;
     bool need_l, need_r;
@@ -156,11 +168,11 @@ __device__ __forceinline__ void tile_half(const StepArgs &a, int64_t x0, int64_t
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
                 const float w = weight<Q, float>(i);
-                unsigned hv[kVec];
+                float hv[kVec];
 #pragma unroll
-                for (int j = 0; j < kVec; ++j) hv[j] = f2h<H>(c1 * fmaf(-w, rho[s][j], f[s][i][j]));
+                for (int j = 0; j < kVec; ++j) hv[j] = c1 * fmaf(-w, rho[s][j], f[s][i][j]);
                 *reinterpret_cast<uint2 *>(g + (int64_t)(i - 1) * plane + y * pitch + x0) =
-                    make_uint2(hv[0] | (hv[1] << 16), hv[2] | (hv[3] << 16));
+                    make_uint2(f2h2<H>(hv[0], hv[1]), f2h2<H>(hv[2], hv[3]));
             }
             if (a.rho_out)
                 *reinterpret_cast<float4 *>(static_cast<float *>(a.rho_out) + (int64_t)s * plane + y * pitch + x0) =
