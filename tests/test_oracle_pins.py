@@ -665,3 +665,32 @@ def test_network_schnakenberg_fixed_point():
     f = orc.run("D2Q9", [0.8, 1.1], net, f, 50)
     rho = orc.density("D2Q9", f)
     assert np.max(np.abs(rho[0] - u)) < 1e-13 and np.max(np.abs(rho[1] - v)) < 1e-13
+
+
+@pytest.mark.parametrize("lat", ["D2Q9", "D2Q5"])
+@pytest.mark.parametrize("tau", [0.6, 0.8, 1.2, 1.5])
+def test_dispersion_fourth_order_term_closed_form(lat, tau):
+    """Truncation trend in tau (Chapman-Enskog, appendix): for a mode along a
+    lattice axis both lattices reduce to three velocities with weights
+    (2/3, 1/6, 1/6), and expanding the leading eigenvalue of that 3 x 3 BGK
+    symbol in k gives the decay rate -log(lambda) = D k^2 + c4 k^4 + O(k^6)
+    with D = (tau - 1/2)/3 and c4 = -tau (tau - 1/2)(tau - 1)/9 (series of the
+    characteristic polynomial, done by hand and by computer algebra).  So the
+    gap to the continuum rate D k^2 falls by 16 when k halves, changes sign at
+    tau = 1, and vanishes to fourth order there."""
+    D = (tau - 0.5) / 3.0
+    c4 = -tau * (tau - 0.5) * (tau - 1.0) / 9.0
+    for k in (0.04, 0.02):
+        lam = np.max(np.abs(np.linalg.eigvals(orc.lb_symbol(lat, [tau], np.zeros((1, 1)), (k, 0.0)))))
+        gap = -math.log(lam) - D * k * k
+        assert gap / k ** 4 == pytest.approx(c4, rel=0.02), (k, gap / k ** 4, c4)
+
+
+@pytest.mark.parametrize("lat", ["D2Q9", "D2Q5"])
+def test_dispersion_sixth_order_at_tau_one(lat):
+    """At tau = 1 the k^4 term vanishes: the gap falls by 2^6 when k halves."""
+    gaps = []
+    for k in (0.08, 0.04):
+        lam = np.max(np.abs(np.linalg.eigvals(orc.lb_symbol(lat, [1.0], np.zeros((1, 1)), (k, 0.0)))))
+        gaps.append(-math.log(lam) - k * k / 6.0)
+    assert gaps[0] / gaps[1] == pytest.approx(64.0, rel=0.02), gaps
