@@ -667,6 +667,14 @@ def main():
         line["cpu_baseline"] = {"value": ssu / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                                 "sample": f"{args.cpu_window}x{args.cpu_window} periodic window of {args.workload}, "
                                           f"{args.cpu_steps} FP64 oracle steps ({dt:.1f} s)"}
+        import oracle as orc
+        all_cores = orc.threads()
+        orc.set_threads(1)
+        ssu1, dt1, _ = run_cpu_oracle_sample(args.workload, args.lattice, args.cpu_window // 4, args.cpu_steps // 2)
+        orc.set_threads(all_cores)
+        line["cpu_baseline"]["single_core"] = {
+            "value": ssu1 / dt1 / 1e6, "unit": "MLUPS", "cores": 1,
+            "sample": f"{args.cpu_window // 4}x{args.cpu_window // 4} window, {args.cpu_steps // 2} steps ({dt1:.1f} s)"}
     sim.close()
     if rank == 0:
         print(json.dumps(line))

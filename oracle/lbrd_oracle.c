@@ -354,6 +354,19 @@ int orc_run_network(int lattice, int S, int64_t nx, int64_t ny, const double *ta
     return run_impl(lattice, S, nx, ny, tau, &src, nsteps, f, tmp);
 }
 
+/* Set the number of threads of the parallel loops (n >= 1); returns it. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1)
+        omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 /* Number of threads the parallel loops use. */
 int orc_threads(void)
 {

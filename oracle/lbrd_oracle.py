@@ -38,7 +38,7 @@ CS2 = 1.0 / 3.0  # lattice sound speed squared, c_s^2 = dx^2 / (3 dt^2) (Sec. II
 
 __all__ = [
     "LATTICES", "REACTIONS", "CS2", "Reaction", "OracleLib", "build", "default",
-    "lattice", "init", "step", "run", "density", "threads",
+    "lattice", "init", "step", "run", "density", "threads", "set_threads",
     "tau_from_diffusion", "diffusion_from_tau", "gs_dimensionless",
     "gs_params_from_dimensionless", "gs_steady_states_dimensionless",
     "gs_steady_states", "gs_jacobian", "gs_matrix_M", "gs_trace_det_M",
@@ -135,6 +135,8 @@ class OracleLib:
         L.orc_run_network.restype = i32
         L.orc_threads.argtypes = []
         L.orc_threads.restype = i32
+        L.orc_set_threads.argtypes = [i32]
+        L.orc_set_threads.restype = i32
         self.L = L
 
     # -- lattice ----------------------------------------------------------
@@ -209,6 +211,11 @@ class OracleLib:
     def threads(self) -> int:
         return int(self.L.orc_threads())
 
+    def set_threads(self, n: int) -> int:
+        """Threads of the parallel loops from now on (timing only; results do
+        not depend on it)."""
+        return int(self.L.orc_set_threads(int(n)))
+
 
 def _code(lat) -> int:
     return LATTICES[lat] if isinstance(lat, str) else int(lat)
@@ -251,6 +258,10 @@ def density(lat, f):
 
 def threads() -> int:
     return default().threads()
+
+
+def set_threads(n: int) -> int:
+    return default().set_threads(n)
 
 
 # ---------------------------------------------------------------------------
