@@ -23,6 +23,8 @@
 // Every mbarrier wait is bounded (about 2^31 clock cycles, ~1 s): on timeout
 // the block records LB_RD_ETIMEOUT in the status word, waits (again bounded)
 // for its own copies still in flight and returns.
+#include <atomic>
+
 #include "step_f32_kernel.cuh"
 #include "lb_rd.h"
 
@@ -270,13 +272,13 @@ cudaError_t launch_bulk(const StepArgs &a, cudaStream_t st, bool per_unit) {
     const int64_t nunits = nstrips * a.ny;
     const size_t smem = (size_t)STAGES * G::kStageFloats * sizeof(float);
     auto kern = step_bulk_kernel<Q, S, NT, STAGES>;
-    static bool configured[64] = {};  // per device ordinal
+    static std::atomic<bool> configured[64] = {};  // per device ordinal (handles on several threads)
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 64 && !configured[dev]) {
+    if (dev < 64 && !configured[dev].load()) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured[dev] = true;
+        configured[dev].store(true);
     }
     const unsigned grid = per_unit ? (unsigned)nunits : persistent_blocks(kern, NT, nunits, smem);
     kern<<<grid, NT, smem, st>>>(a, nstrips, nunits);

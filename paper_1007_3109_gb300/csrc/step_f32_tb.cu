@@ -21,6 +21,8 @@
 // loads and stores of a warp touch consecutive words (no bank conflicts) and
 // global stores are coalesced 128-byte rows.  Every mbarrier wait is bounded
 // as in the bulk-copy kernel (status word, drain, return).
+#include <atomic>
+
 #include "step_f32_kernel.cuh"
 #include "lb_rd.h"
 
@@ -459,13 +461,13 @@ cudaError_t launch_tbw(const StepArgs &a, cudaStream_t st) {
     const int64_t nstrips = a.nx / TX;
     const size_t smem = ((size_t)NS * G::kStage + (size_t)W * 3 * S * Q * 34) * sizeof(float);
     auto kern = step_tbw_kernel<Q, S, W, NS, MINB>;
-    static bool configured[64] = {};
+    static std::atomic<bool> configured[64] = {};  // per device ordinal (handles on several threads)
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 64 && !configured[dev]) {
+    if (dev < 64 && !configured[dev].load()) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured[dev] = true;
+        configured[dev].store(true);
     }
     const int64_t work = nstrips * a.ny / 16 > 0 ? nstrips * a.ny / 16 : 1;
     const unsigned grid = persistent_blocks(kern, (W + 1) * 32, work, smem);
@@ -489,13 +491,13 @@ cudaError_t launch_tb(const StepArgs &a, cudaStream_t st) {
     const int64_t nstrips = a.nx / TX;
     const size_t smem = ((size_t)NS * G::kStage + 4 * (size_t)G::kRow1) * sizeof(float);
     auto kern = step_tb2_kernel<Q, S, NT, TX, NS, MINB, IL>;
-    static bool configured[64] = {};
+    static std::atomic<bool> configured[64] = {};  // per device ordinal (handles on several threads)
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 64 && !configured[dev]) {
+    if (dev < 64 && !configured[dev].load()) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured[dev] = true;
+        configured[dev].store(true);
     }
     // at least 16 rows per block so that the two halo rows stay a small overhead
     const int64_t work = nstrips * a.ny / 16 > 0 ? nstrips * a.ny / 16 : 1;
