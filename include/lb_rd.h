@@ -282,6 +282,13 @@ LB_RD_API int lb_rd_batch_step(lb_rd_batch *b, int64_t nsteps);
  * step directly.  Default 64. */
 LB_RD_API int lb_rd_batch_set_graph(lb_rd_batch *b, int32_t steps_per_graph);
 
+/* Time steps per launch: 2 runs the two-step (temporal blocking) kernel over
+ * all instances, bitwise the same as two single steps; it needs FP32
+ * instances with two state copies and nx a multiple of 256 (the default
+ * then), otherwise EINVAL.  1: one step per launch.  The last step of every
+ * lb_rd_batch_step call is a single step (it writes the densities). */
+LB_RD_API int lb_rd_batch_set_steps_per_launch(lb_rd_batch *b, int32_t k);
+
 /* Densities and FP64 mass of instance idx at the batch's current time (as
  * lb_rd_moments).  Synchronises. */
 LB_RD_API int lb_rd_batch_moments(lb_rd_batch *b, int32_t idx, double *rho_out, double *mass_out, int is_device);

@@ -88,6 +88,7 @@ _SIGNATURES = {
     "lb_rd_batch_step": ([c_void_p, c_int64], c_int),
     "lb_rd_batch_set_graph": ([c_void_p, c_int32], c_int),
     "lb_rd_batch_moments": ([c_void_p, c_int32, c_void_p, c_void_p, c_int], c_int),
+    "lb_rd_batch_set_steps_per_launch": ([c_void_p, c_int32], c_int),
     "lb_rd_batch_get_time": ([c_void_p, POINTER(c_int64), POINTER(c_int64)], c_int),
     "lb_rd_server_create": ([ctypes.c_void_p, POINTER(c_void_p)], c_int),
     "lb_rd_server_destroy": ([c_void_p], c_int),
@@ -339,6 +340,10 @@ def lb_rd_batch_moments(b: int, idx: int, rho_out=None, mass_out=None):
     _check(lib().lb_rd_batch_moments(b, int(idx), pr, pm, dev_r if rho_out is not None else dev_m))
 
 
+def lb_rd_batch_set_steps_per_launch(b: int, k: int):
+    _check(lib().lb_rd_batch_set_steps_per_launch(b, int(k)))
+
+
 def lb_rd_batch_get_time(b: int):
     t, n = c_int64(0), c_int64(0)
     _check(lib().lb_rd_batch_get_time(b, ctypes.byref(t), ctypes.byref(n)))
@@ -479,6 +484,10 @@ class Batch:
 
     def set_graph(self, steps):
         lb_rd_batch_set_graph(self.b, steps)
+        return self
+
+    def set_steps_per_launch(self, k):
+        lb_rd_batch_set_steps_per_launch(self.b, k)
         return self
 
     def moments(self, idx):

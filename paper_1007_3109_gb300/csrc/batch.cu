@@ -161,6 +161,12 @@ struct lb_rd_batch {
     int64_t t = 0, launches = 0;
     int graph_steps = 64;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // by starting parity
+    // two steps per launch (FP32, two state copies, every nx % strip == 0)
+    bool tb_ok = false;
+    int steps_per_launch = 1;
+    lbrd::TbwItem *d_tb[2] = {nullptr, nullptr};  // by buffer parity
+    int64_t tb_units = 0;
+    cudaGraphExec_t tb_graph[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -183,6 +189,15 @@ void drop_graphs(lb_rd_batch *b) {
             cudaGraphExecDestroy(g);
             g = nullptr;
         }
+    for (auto &g : b->tb_graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+cudaError_t launch_two(lb_rd_batch *b, int parity) {
+    return lbrd::launch_batch_tb2(b->d_tb[parity], (int)b->cfgs.size(), b->tb_units, b->Q, b->S, b->stream);
 }
 
 }  // namespace
@@ -197,6 +212,7 @@ int lb_rd_batch_destroy(lb_rd_batch *b) {
     cudaFree(b->buf[1]);
     cudaFree(b->rho);
     for (auto p : b->d_items) cudaFree(p);
+    for (auto p : b->d_tb) cudaFree(p);
     cudaFree(b->stage);
     cudaFree(b->partials);
     cudaFree(b->counter);
@@ -300,6 +316,29 @@ int lb_rd_batch_create(const lb_rd_config *cfgs, int32_t n, lb_rd_batch **out) {
         e = cudaMalloc(&b->d_items[k], n * sizeof(lbrd::BatchItem));
         if (!e) e = cudaMemcpy(b->d_items[k], v.data(), n * sizeof(lbrd::BatchItem), cudaMemcpyHostToDevice);
     }
+    // two-step descriptors: every instance FP32 with two copies and nx % strip == 0
+    b->tb_ok = prec == LB_RD_FP32;
+    for (int i = 0; i < n && b->tb_ok; ++i)
+        if (b->inplace[i] || cfgs[i].nx % lbrd::batch_tb2_strip()) b->tb_ok = false;
+    if (b->tb_ok && !e) {
+        std::vector<lbrd::TbwItem> tv(n);
+        for (int parity = 0; parity < 2 && !e; ++parity) {
+            int64_t units = 0;
+            for (int i = 0; i < n; ++i) {
+                tv[i].a = items[i].a;
+                char *c0 = b->buf[0] + b->state_off[i], *c1 = b->buf[1] + b->state_off1[i];
+                tv[i].a.src = parity ? c1 : c0;
+                tv[i].a.dst = parity ? c0 : c1;
+                tv[i].a.rho_out = nullptr;
+                tv[i].unit_begin = units;
+                units += (cfgs[i].nx / lbrd::batch_tb2_strip()) * cfgs[i].ny;
+            }
+            b->tb_units = units;
+            e = cudaMalloc(&b->d_tb[parity], n * sizeof(lbrd::TbwItem));
+            if (!e) e = cudaMemcpy(b->d_tb[parity], tv.data(), n * sizeof(lbrd::TbwItem), cudaMemcpyHostToDevice);
+        }
+        b->steps_per_launch = 2;
+    }
     if (e) {
         int rc = cuda_err(e, "lb_rd_batch_create allocation");
         lb_rd_batch_destroy(b);
@@ -371,7 +410,8 @@ int lb_rd_batch_set_graph(lb_rd_batch *b, int32_t steps_per_graph) {
     return LB_RD_OK;
 }
 
-static int capture_graph(lb_rd_batch *b, int parity) {
+// two == true: graph_steps / 2 two-step launches (parity alternates per launch).
+static int capture_graph(lb_rd_batch *b, int parity, bool two = false) {
     // A private stream: capturing on the legacy default stream is not allowed.
     cudaStream_t cs;
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
@@ -380,11 +420,12 @@ static int capture_graph(lb_rd_batch *b, int parity) {
     b->stream = cs;
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    for (int k = 0; k < b->graph_steps && !e; ++k) e = launch_one(b, (parity + k) & 1, false);
+    const int nl = two ? b->graph_steps / 2 : b->graph_steps;
+    for (int k = 0; k < nl && !e; ++k) e = two ? launch_two(b, (parity + k) & 1) : launch_one(b, (parity + k) & 1, false);
     cudaError_t e2 = cudaStreamEndCapture(cs, &g);
     b->stream = saved;
     if (!e) e = e2;
-    if (!e) e = cudaGraphInstantiate(&b->graph[parity], g, 0);
+    if (!e) e = cudaGraphInstantiate(two ? &b->tb_graph[parity] : &b->graph[parity], g, 0);
     if (g) cudaGraphDestroy(g);
     cudaStreamDestroy(cs);
     if (e) return cuda_err(e, "graph capture");
@@ -399,6 +440,33 @@ int lb_rd_batch_step(lb_rd_batch *b, int64_t nsteps) {
             return report_error(LB_RD_EINVAL, "lb_rd_batch_step: instance " + std::to_string(i) + " not initialised");
     if (nsteps == 0) return LB_RD_OK;
     int64_t body = nsteps - 1;  // the last step also writes the densities
+    if (b->steps_per_launch == 2 && body >= 2) {
+        int64_t n_two = body / 2;
+        body -= 2 * n_two;
+        const int per_graph = b->graph_steps / 2;  // two-step launches per graph
+        if (per_graph > 0 && n_two >= per_graph) {
+            const int64_t reps = n_two / per_graph;
+            for (int64_t r = 0; r < reps; ++r) {
+                if (!b->tb_graph[b->cur]) {  // captured once per starting parity
+                    int rc = capture_graph(b, b->cur, true);
+                    if (rc) return rc;
+                }
+                cudaError_t e = cudaGraphLaunch(b->tb_graph[b->cur], b->stream);
+                if (e) return cuda_err(e, "graph launch");
+                if (per_graph & 1) b->cur ^= 1;  // an odd number of launches flips the buffers
+            }
+            b->launches += reps * per_graph;
+            b->t += reps * per_graph * 2;
+            n_two -= reps * per_graph;
+        }
+        for (int64_t k = 0; k < n_two; ++k) {
+            cudaError_t e = launch_two(b, b->cur);
+            if (e) return cuda_err(e, "batch two-step kernel");
+            b->cur ^= 1;
+            b->t += 2;
+            b->launches++;
+        }
+    }
     if (b->graph_steps > 0 && body >= b->graph_steps) {
         if (!b->graph[b->cur]) {
             int rc = capture_graph(b, b->cur);
@@ -420,6 +488,16 @@ int lb_rd_batch_step(lb_rd_batch *b, int64_t nsteps) {
         b->t++;
         b->launches++;
     }
+    return LB_RD_OK;
+}
+
+int lb_rd_batch_set_steps_per_launch(lb_rd_batch *b, int32_t k) {
+    if (!b) return report_error(LB_RD_EINVAL, "batch is NULL");
+    if (k != 1 && k != 2) return report_error(LB_RD_EINVAL, "steps per launch must be 1 or 2");
+    if (k == 2 && !b->tb_ok)
+        return report_error(LB_RD_EINVAL, "two steps per launch need FP32 instances with two state copies and "
+                                          "nx a multiple of " + std::to_string(lbrd::batch_tb2_strip()));
+    b->steps_per_launch = k;
     return LB_RD_OK;
 }
 

@@ -139,6 +139,15 @@ struct BatchItem {
     int aa;              // FP32: 0 two state copies; in place (a.src == a.dst), phase A (t even) / B:
                          // 1 / 2 four sites per thread (nx % 4 == 0), 3 / 4 one site per thread
 };
+// Batched two-step launches over (strip, row) units: one item per instance
+// (FP32, two state copies, nx % batch_tb2_strip() == 0); the units of item k
+// are [unit_begin, unit_begin + (nx / strip) * ny).
+struct TbwItem {
+    StepArgs a;
+    int64_t unit_begin;
+};
+int batch_tb2_strip();
+cudaError_t launch_batch_tb2(const TbwItem *items, int n, int64_t total_units, int Q, int S, cudaStream_t st);
 int64_t batch_tiles_x(int64_t nx);
 int64_t batch_tiles(int64_t nx, int64_t ny);
 // mode: 0 FP32 storage, 1 bf16 deviations, 2 fp16 deviations, 3 FP64,

@@ -96,8 +96,8 @@ __device__ __forceinline__ unsigned copy_periodic(float *dst, const float *row, 
 // Issue the level-0 copies for level-1 row r.  Called by all 32 lanes of one
 // warp: lane 0 posts the expected bytes, lane p < S * Q issues plane p's
 // pieces (a negative transaction count before the arrival is allowed).
-template <int Q, int S, int TX>
-__device__ __forceinline__ void issue_row(const StepArgs &a, int64_t r, int64_t x0, float *st, unsigned bar,
+template <int Q, int S, int TX, typename Args>
+__device__ __forceinline__ void issue_row(const Args &a, int64_t r, int64_t x0, float *st, unsigned bar,
                                           unsigned extra_tx = 0) {
     using L = Lattice<Q>;
     using G = TbGeom<Q, S, TX>;
@@ -119,8 +119,8 @@ __device__ __forceinline__ void issue_row(const StepArgs &a, int64_t r, int64_t 
 }
 
 // The fused step of one site from S * Q pulled values.
-template <int Q, int S>
-__device__ __forceinline__ void collide_site(const StepArgs &a, float (&f)[S][Q], float (&rho)[S]) {
+template <int Q, int S, typename Args>
+__device__ __forceinline__ void collide_site(const Args &a, float (&f)[S][Q], float (&rho)[S]) {
     using L = Lattice<Q>;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
@@ -300,6 +300,33 @@ __device__ __forceinline__ void mbar_arrive(unsigned bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+// The fields of one grid a two-step segment needs, in registers (FP32 copies
+// of the relaxation rates and reaction constants: the values the one-step
+// kernels compute with).
+struct SegArgs {
+    const void *src;
+    void *dst;
+    int64_t nx, ny, pitch, plane;
+    float omega[2];
+    int rkind;
+    float kappa, F, k;
+};
+
+__device__ __forceinline__ void load_seg(const StepArgs &a, SegArgs &g) {
+    g.src = a.src;
+    g.dst = a.dst;
+    g.nx = a.nx;
+    g.ny = a.ny;
+    g.pitch = a.pitch;
+    g.plane = a.plane;
+    g.omega[0] = (float)a.omega[0];
+    g.omega[1] = (float)a.omega[1];
+    g.rkind = a.rkind;
+    g.kappa = (float)a.kappa;
+    g.F = (float)a.F;
+    g.k = (float)a.k;
+}
+
 // Warp-decoupled two-step kernel: W consumer warps and one producer warp.
 // The block's strip is TX = 32 W columns; consumer warp w owns the 32
 // columns c0 = x0 + 32 w ... and computes level 1 on its 34 columns
@@ -313,9 +340,12 @@ __device__ __forceinline__ void mbar_arrive(unsigned bar) {
 // every consumer warp has arrived on its "empty" barrier (count W) and the
 // copies complete on its "full" barrier.  Every wait is bounded (status
 // word, drain, return); the arithmetic of every site is the one-step
-// kernels'.
-template <int Q, int S, int W, int NS, int MINB>
-__global__ void __launch_bounds__((W + 1) * 32, MINB) step_tbw_kernel(StepArgs a, int64_t nstrips) {
+// kernels'.  BATCH: the (strip, row) units of a list of grids (TbwItem, one
+// per batched instance, all with nx % TX == 0) instead of one grid; a
+// segment never crosses from one grid to the next.
+template <int Q, int S, int W, int NS, int MINB, bool BATCH>
+__global__ void __launch_bounds__((W + 1) * 32, MINB)
+    step_tbw_kernel(StepArgs a, int64_t nstrips, const TbwItem *__restrict__ items, int nitems, int64_t total_units) {
     using L = Lattice<Q>;
     constexpr int TX = 32 * W;
     using G = TbGeom<Q, S, TX>;
@@ -327,7 +357,6 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) step_tbw_kernel(StepArgs a
     __shared__ __align__(8) unsigned long long full[NS], empty[NS];
     __shared__ volatile int abort_flag;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    float *__restrict__ dst = static_cast<float *>(a.dst);
     if (tid == 0) {
         for (int k = 0; k < NS; ++k) {
             mbar_init(smem_u32(&full[k]), 1);
@@ -342,16 +371,28 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) step_tbw_kernel(StepArgs a
     for (int s = 0; s < S; ++s) acc[s] = 0.0;
     int64_t ticket = 0;  // level-0 rows (stages) used by this block so far
     int64_t issued = 0;  // producer: rows issued
-    const int64_t total = nstrips * a.ny;
+    const int64_t total = BATCH ? total_units : nstrips * a.ny;
     const int64_t u_end = total * (blockIdx.x + 1) / gridDim.x;
     float *ring = rings + (w < W ? w : 0) * 3 * kRing;
+    int it = 0;  // BATCH: the grid of unit u (a block's units only increase)
     for (int64_t u = total * blockIdx.x / gridDim.x; u < u_end;) {
-        const int64_t strip = u / a.ny;
-        const int64_t y0 = u - strip * a.ny;
-        const int64_t ly = (a.ny - y0 < u_end - u) ? a.ny - y0 : u_end - u;
+        SegArgs g;
+        int64_t local;
+        if constexpr (BATCH) {
+            while (it + 1 < nitems && items[it + 1].unit_begin <= u) ++it;
+            load_seg(items[it].a, g);
+            local = u - items[it].unit_begin;
+        } else {
+            load_seg(a, g);
+            local = u;
+        }
+        const int64_t strip = local / g.ny;
+        const int64_t y0 = local - strip * g.ny;
+        const int64_t ly = (g.ny - y0 < u_end - u) ? g.ny - y0 : u_end - u;
         u += ly;
         const int64_t x0 = strip * TX;
         const int64_t nrows = ly + 2;
+        float *__restrict__ dst = static_cast<float *>(g.dst);
         // Every decision below is warp-uniform (__any_sync / __all_sync), so the
         // lanes of a warp always take the same path to each __syncwarp.
         if (w == W) {  // producer
@@ -366,7 +407,7 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) step_tbw_kernel(StepArgs a
                 }
                 // the consumers' reads of this stage (generic proxy) before the copies into it (async proxy)
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue_row<Q, S, TX>(a, y0 - 1 + j, x0, stages + sk * G::kStage, smem_u32(&full[sk]),
+                issue_row<Q, S, TX>(g, y0 - 1 + j, x0, stages + sk * G::kStage, smem_u32(&full[sk]),
                                     (a.inject_timeout && blockIdx.x == 0 && tk == 0) ? 16u : 0u);
                 issued = tk + 1;
             }
@@ -402,8 +443,8 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) step_tbw_kernel(StepArgs a
                         f2[s][i] = rows1[1 - L::ey(i)][(s * Q + i) * RW + lane + 1 - L::ex(i)];
                     }
                 __syncwarp();  // every lane has read ring row j - 3 before it is overwritten
-                collide_site<Q, S>(a, f1, rho1);
-                collide_site<Q, S>(a, f2, rho2);
+                collide_site<Q, S>(g, f1, rho1);
+                collide_site<Q, S>(g, f2, rho2);
                 if (do1) {
 #pragma unroll
                     for (int s = 0; s < S; ++s)
@@ -414,7 +455,7 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) step_tbw_kernel(StepArgs a
                         for (int s = 0; s < S; ++s)
 #pragma unroll
                             for (int i = 0; i < Q; ++i) f1[s][i] = st[(s * Q + i) * G::W0 + k1 + 32 - L::ex(i)];
-                        collide_site<Q, S>(a, f1, rho1);
+                        collide_site<Q, S>(g, f1, rho1);
 #pragma unroll
                         for (int s = 0; s < S; ++s)
 #pragma unroll
@@ -426,7 +467,7 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) step_tbw_kernel(StepArgs a
 #pragma unroll
                     for (int s = 0; s < S; ++s) {
 #pragma unroll
-                        for (int i = 0; i < Q; ++i) dst[(int64_t)(s * Q + i) * a.plane + y * a.pitch + x] = f2[s][i];
+                        for (int i = 0; i < Q; ++i) dst[(int64_t)(s * Q + i) * g.plane + y * g.pitch + x] = f2[s][i];
                         sum[s] += rho2[s];
                     }
                 }
@@ -460,7 +501,7 @@ cudaError_t launch_tbw(const StepArgs &a, cudaStream_t st) {
     if (a.nx % TX != 0) return cudaErrorInvalidValue;
     const int64_t nstrips = a.nx / TX;
     const size_t smem = ((size_t)NS * G::kStage + (size_t)W * 3 * S * Q * 34) * sizeof(float);
-    auto kern = step_tbw_kernel<Q, S, W, NS, MINB>;
+    auto kern = step_tbw_kernel<Q, S, W, NS, MINB, false>;
     static std::atomic<bool> configured[64] = {};  // per device ordinal (handles on several threads)
     int dev = 0;
     cudaGetDevice(&dev);
@@ -471,7 +512,28 @@ cudaError_t launch_tbw(const StepArgs &a, cudaStream_t st) {
     }
     const int64_t work = nstrips * a.ny / 16 > 0 ? nstrips * a.ny / 16 : 1;
     const unsigned grid = persistent_blocks(kern, (W + 1) * 32, work, smem);
-    kern<<<grid, (W + 1) * 32, smem, st>>>(a, nstrips);
+    kern<<<grid, (W + 1) * 32, smem, st>>>(a, nstrips, nullptr, 0, 0);
+    return cudaGetLastError();
+}
+
+// Batched form: the same kernel over the units of a list of grids.
+template <int Q, int S, int W, int NS, int MINB>
+cudaError_t launch_tbw_batch(const TbwItem *items, int n, int64_t total_units, cudaStream_t st) {
+    constexpr int TX = 32 * W;
+    using G = TbGeom<Q, S, TX>;
+    const size_t smem = ((size_t)NS * G::kStage + (size_t)W * 3 * S * Q * 34) * sizeof(float);
+    auto kern = step_tbw_kernel<Q, S, W, NS, MINB, true>;
+    static std::atomic<bool> configured[64] = {};  // per device ordinal (handles on several threads)
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !configured[dev].load()) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured[dev].store(true);
+    }
+    const int64_t work = total_units / 16 > 0 ? total_units / 16 : 1;
+    const unsigned grid = persistent_blocks(kern, (W + 1) * 32, work, smem);
+    kern<<<grid, (W + 1) * 32, smem, st>>>(StepArgs{}, 0, items, n, total_units);
     return cudaGetLastError();
 }
 
@@ -516,6 +578,17 @@ cudaError_t dispatch_tb(int Q, int S, const StepArgs &a, cudaStream_t st) {
 }
 
 }  // namespace
+
+// Batched two steps per launch (tb2w_288x256_s2x2 shape: strips of 256).
+int batch_tb2_strip() { return 256; }
+
+cudaError_t launch_batch_tb2(const TbwItem *items, int n, int64_t total_units, int Q, int S, cudaStream_t st) {
+    if (Q == 9 && S == 1) return launch_tbw_batch<9, 1, 8, 2, 2>(items, n, total_units, st);
+    if (Q == 9 && S == 2) return launch_tbw_batch<9, 2, 8, 2, 2>(items, n, total_units, st);
+    if (Q == 5 && S == 1) return launch_tbw_batch<5, 1, 8, 2, 2>(items, n, total_units, st);
+    if (Q == 5 && S == 2) return launch_tbw_batch<5, 2, 8, 2, 2>(items, n, total_units, st);
+    return cudaErrorInvalidValue;
+}
 
 // Two time steps per launch (state t -> t + 2).  v: launch shape.
 cudaError_t launch_step_f32_tb2(int v, int Q, int S, const StepArgs &a, cudaStream_t st) {

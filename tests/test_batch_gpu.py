@@ -131,3 +131,36 @@ def test_batch_with_inplace_instances_equals_single_handles():
                 rho, _ = b.moments(j)
                 ref_rho, _ = _single(dict(c, inplace=False), _rho0(c, j), steps)
                 np.testing.assert_array_equal(rho, ref_rho, err_msg=f"instance {j} graph {graph}")
+
+
+@pytest.mark.parametrize("graph", [0, 8, 6])
+@pytest.mark.parametrize("steps", [1, 2, 7, 40])
+def test_batch_two_steps_per_launch_equals_single_handles(graph, steps):
+    """Instances with nx a multiple of 256 run the two-step kernel over the
+    whole list (the default for such batches); each instance gives the bits
+    of a single handle, whatever the graph length (6: an odd number of
+    two-step launches per graph) and step count (odd counts end with single
+    steps)."""
+    shapes = [(256, 40), (512, 16), (256, 3), (768, 9)]
+    cfgs = [dict(lattice="D2Q9", nspecies=2, nx=nx, ny=ny, tau=[0.8 + 0.05 * j, 0.65], reaction="gray_scott",
+                 F=0.03 + 0.004 * j, k=0.06 - 0.002 * j, precision="fp32") for j, (nx, ny) in enumerate(shapes)]
+    with B.Batch(cfgs) as b:
+        b.set_graph(graph)
+        for j, c in enumerate(cfgs):
+            b.init(j, _rho0(c, j))
+        b.step(steps).step(steps)
+        _, launches = B.lb_rd_batch_get_time(b.b)
+        for j, c in enumerate(cfgs):
+            rho, _ = b.moments(j)
+            ref_rho, _ = _single(c, _rho0(c, j), 2 * steps)
+            np.testing.assert_array_equal(rho, ref_rho, err_msg=f"instance {j}")
+    if steps >= 7:
+        assert launches < 2 * steps  # two steps per launch were used
+
+
+def test_batch_steps_per_launch_switch():
+    cfgs = _configs("fp32")  # includes nx not a multiple of 256
+    with B.Batch(cfgs) as b:
+        with pytest.raises(B.LbRdError):
+            b.set_steps_per_launch(2)
+        b.set_steps_per_launch(1)
