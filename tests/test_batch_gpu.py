@@ -133,16 +133,17 @@ def test_batch_with_inplace_instances_equals_single_handles():
                 np.testing.assert_array_equal(rho, ref_rho, err_msg=f"instance {j} graph {graph}")
 
 
+@pytest.mark.parametrize("lat", ["D2Q9", "D2Q5"])
 @pytest.mark.parametrize("graph", [0, 8, 6])
 @pytest.mark.parametrize("steps", [1, 2, 7, 40])
-def test_batch_two_steps_per_launch_equals_single_handles(graph, steps):
+def test_batch_two_steps_per_launch_equals_single_handles(lat, graph, steps):
     """Instances with nx a multiple of 256 run the two-step kernel over the
     whole list (the default for such batches); each instance gives the bits
     of a single handle, whatever the graph length (6: an odd number of
     two-step launches per graph) and step count (odd counts end with single
     steps)."""
     shapes = [(256, 40), (512, 16), (256, 3), (768, 9)]
-    cfgs = [dict(lattice="D2Q9", nspecies=2, nx=nx, ny=ny, tau=[0.8 + 0.05 * j, 0.65], reaction="gray_scott",
+    cfgs = [dict(lattice=lat, nspecies=2, nx=nx, ny=ny, tau=[0.8 + 0.05 * j, 0.65], reaction="gray_scott",
                  F=0.03 + 0.004 * j, k=0.06 - 0.002 * j, precision="fp32") for j, (nx, ny) in enumerate(shapes)]
     with B.Batch(cfgs) as b:
         b.set_graph(graph)
