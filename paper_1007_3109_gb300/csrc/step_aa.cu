@@ -34,7 +34,7 @@ constexpr int kBX = 128;
 template <typename T, int Q, int S, int PHASE>
 __global__ void __launch_bounds__(kBX) step_aa_kernel(StepArgs a, int64_t tiles_x, int64_t ntiles) {
     __shared__ AANet net;
-    load_aanet(a.net, net);
+    load_net(a.net, net);
     double acc[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[s] = 0.0;
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kBX) step_aa_kernel(StepArgs a, int64_t tiles_
 template <int Q, int S, int V, int PHASE, int MINB>
 __global__ void __launch_bounds__(kBX, MINB) step_aa_vec_kernel(StepArgs a, int64_t tiles_x, int64_t ntiles) {
     __shared__ AANet net;
-    load_aanet(a.net, net);
+    load_net(a.net, net);
     const int lane = threadIdx.x & 31;
     double acc[S];
 #pragma unroll

@@ -4,6 +4,7 @@
 #pragma once
 
 #include "lbrd_kernels.h"
+#include "site_math.cuh"
 
 namespace lbrd {
 namespace aa {
@@ -15,134 +16,55 @@ __host__ __device__ constexpr int opp(int i) {
     return i;
 }
 
-struct AANet {
-    int nr;
-    double rate[kMaxReactions];
-    signed char order[kMaxReactions][kMaxSpecies];
-    signed char change[kMaxReactions][kMaxSpecies];
-};
-
-__device__ __forceinline__ void load_aanet(const Network &n, AANet &sn) {
-    if (threadIdx.x == 0) {
-        sn.nr = n.nr;
-        for (int r = 0; r < kMaxReactions; ++r) {
-            sn.rate[r] = n.rate[r];
-            for (int j = 0; j < kMaxSpecies; ++j) {
-                sn.order[r][j] = n.order[r][j];
-                sn.change[r][j] = n.change[r][j];
-            }
-        }
-    }
-    __syncthreads();
-}
+using AANet = sm::NetSmem;
+using sm::load_net;
+using sm::radd;
+using sm::relax;
 
 // Reaction source with the arithmetic of the ping-pong kernels: the
-// Gray-Scott and transformation sources of lbrd_common.cuh, or the network
-// evaluated as in the general kernel.
+// Gray-Scott and transformation sources of lbrd_common.cuh, or the network.
 template <int S>
 __device__ __forceinline__ void source(const StepArgs &a, const AANet &n, const double (&rho)[S], double (&R)[S]) {
-    if (a.rkind != kMassAction) {
-        if constexpr (S <= 2) reaction_f64<S>(a.rkind, a.kappa, a.F, a.k, rho, R);
-        else {
+    if (a.rkind == kMassAction) {
+        sm::network_source<S>(n, rho, R);
+    } else if constexpr (S <= 2) {
+        reaction_f64<S>(a.rkind, a.kappa, a.F, a.k, rho, R);
+    } else {
 #pragma unroll
-            for (int s = 0; s < S; ++s) R[s] = 0.0;
-        }
-        return;
-    }
-#pragma unroll
-    for (int s = 0; s < S; ++s) R[s] = 0.0;
-    for (int r = 0; r < n.nr; ++r) {
-        double p = n.rate[r];
-#pragma unroll
-        for (int j = 0; j < S; ++j)
-            for (int e = 0; e < n.order[r][j]; ++e) p = __dmul_rn(p, rho[j]);
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-            const int c = n.change[r][s];
-            if (c != 0) R[s] = __dadd_rn(R[s], __dmul_rn((double)c, p));
-        }
+        for (int s = 0; s < S; ++s) R[s] = 0.0;
     }
 }
 
 template <int S>
 __device__ __forceinline__ void source(const StepArgs &a, const AANet &n, const float (&rho)[S], float (&R)[S]) {
-    if (a.rkind != kMassAction) {
-        if constexpr (S <= 2) reaction_f32<S>(a.rkind, (float)a.kappa, (float)a.F, (float)a.k, rho, R);
-        else {
+    if (a.rkind == kMassAction) {
+        sm::network_source<S>(n, rho, R);
+    } else if constexpr (S <= 2) {
+        reaction_f32<S>(a.rkind, (float)a.kappa, (float)a.F, (float)a.k, rho, R);
+    } else {
 #pragma unroll
-            for (int s = 0; s < S; ++s) R[s] = 0.f;
-        }
-        return;
-    }
-#pragma unroll
-    for (int s = 0; s < S; ++s) R[s] = 0.f;
-    for (int r = 0; r < n.nr; ++r) {
-        float p = (float)n.rate[r];
-#pragma unroll
-        for (int j = 0; j < S; ++j)
-            for (int e = 0; e < n.order[r][j]; ++e) p *= rho[j];
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-            const int c = n.change[r][s];
-            if (c != 0) R[s] += (float)c * p;
-        }
+        for (int s = 0; s < S; ++s) R[s] = 0.f;
     }
 }
 
-// V sites at once: kinds other than mass action per site as above; the
-// network with each step's constants read once for all V sites (per site
-// the same operations in the same order).
+// V sites at once (the network's constants read once for all of them).
 template <int S, int V>
 __device__ __forceinline__ void source_vec(const StepArgs &a, const AANet &n, const float (&rho)[S][V],
                                            float (&R)[S][V]) {
-    if (a.rkind != kMassAction) {
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            float rv[S], Rv[S];
-#pragma unroll
-            for (int s = 0; s < S; ++s) rv[s] = rho[s][v];
-            source<S>(a, n, rv, Rv);
-#pragma unroll
-            for (int s = 0; s < S; ++s) R[s][v] = Rv[s];
-        }
+    if (a.rkind == kMassAction) {
+        sm::network_source_vec<S, V>(n, rho, R);
         return;
     }
 #pragma unroll
-    for (int s = 0; s < S; ++s)
+    for (int v = 0; v < V; ++v) {
+        float rv[S], Rv[S];
 #pragma unroll
-        for (int v = 0; v < V; ++v) R[s][v] = 0.f;
-    for (int r = 0; r < n.nr; ++r) {
-        float p[V];
-        const float k = (float)n.rate[r];
+        for (int s = 0; s < S; ++s) rv[s] = rho[s][v];
+        source<S>(a, n, rv, Rv);
 #pragma unroll
-        for (int v = 0; v < V; ++v) p[v] = k;
-#pragma unroll
-        for (int j = 0; j < S; ++j) {
-            const int o = n.order[r][j];
-            for (int e = 0; e < o; ++e)
-#pragma unroll
-                for (int v = 0; v < V; ++v) p[v] *= rho[j][v];
-        }
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-            const int c = n.change[r][s];
-            if (c != 0) {
-                const float cf = (float)c;
-#pragma unroll
-                for (int v = 0; v < V; ++v) R[s][v] += cf * p[v];
-            }
-        }
+        for (int s = 0; s < S; ++s) R[s][v] = Rv[s];
     }
 }
-
-__device__ __forceinline__ double relax(double f, double w, double rho, double om, double R) {
-    return __dadd_rn(__dadd_rn(f, __dmul_rn(__dsub_rn(__dmul_rn(w, rho), f), om)), __dmul_rn(w, R));
-}
-__device__ __forceinline__ float relax(float f, float w, float rho, float om, float R) {
-    return fmaf(1.f - om, f, w * (om * rho + R));
-}
-__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ float radd(float a, float b) { return a + b; }
 
 // The step of one site (x, y), one thread per site.
 template <typename T, int Q, int S, int PHASE>

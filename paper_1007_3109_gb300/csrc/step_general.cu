@@ -15,6 +15,7 @@
 // per-site arithmetic.  The network is copied to shared
 // memory once per block (its entries are indexed by the loop counters).
 #include "lbrd_kernels.h"
+#include "site_math.cuh"
 
 namespace lbrd {
 
@@ -22,115 +23,36 @@ namespace {
 
 constexpr int kBX = 128;
 
-struct SharedNet {
-    int nr;
-    double rate[kMaxReactions];
-    float ratef[kMaxReactions];
-    signed char order[kMaxReactions][kMaxSpecies];
-    signed char change[kMaxReactions][kMaxSpecies];
-};
+using namespace sm;
 
-__device__ __forceinline__ void load_net(const Network &n, SharedNet &sn) {
-    if (threadIdx.x == 0) {
-        sn.nr = n.nr;
-        for (int r = 0; r < kMaxReactions; ++r) {
-            sn.rate[r] = n.rate[r];
-            sn.ratef[r] = (float)n.rate[r];
-            for (int j = 0; j < kMaxSpecies; ++j) {
-                sn.order[r][j] = n.order[r][j];
-                sn.change[r][j] = n.change[r][j];
-            }
-        }
-    }
-    __syncthreads();
-}
-
-template <int S>
-__device__ __forceinline__ void network_source(const SharedNet &n, int kind, const double (&rho)[S], double (&R)[S]) {
+// The general kernel evaluates the network only for mass action (kind 0: R = 0).
+template <int S, typename T>
+__device__ __forceinline__ void general_source(const NetSmem &n, int kind, const T (&rho)[S], T (&R)[S]) {
+    if (kind == kMassAction) {
+        network_source<S>(n, rho, R);
+    } else {
 #pragma unroll
-    for (int s = 0; s < S; ++s) R[s] = 0.0;
-    if (kind != kMassAction) return;
-    for (int r = 0; r < n.nr; ++r) {
-        double p = n.rate[r];
-#pragma unroll
-        for (int j = 0; j < S; ++j)
-            for (int e = 0; e < n.order[r][j]; ++e) p = __dmul_rn(p, rho[j]);
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-            const int c = n.change[r][s];
-            if (c != 0) R[s] = __dadd_rn(R[s], __dmul_rn((double)c, p));
-        }
+        for (int s = 0; s < S; ++s) R[s] = T(0);
     }
 }
 
-template <int S>
-__device__ __forceinline__ void network_source(const SharedNet &n, int kind, const float (&rho)[S], float (&R)[S]) {
-#pragma unroll
-    for (int s = 0; s < S; ++s) R[s] = 0.f;
-    if (kind != kMassAction) return;
-    for (int r = 0; r < n.nr; ++r) {
-        float p = n.ratef[r];
-#pragma unroll
-        for (int j = 0; j < S; ++j)
-            for (int e = 0; e < n.order[r][j]; ++e) p *= rho[j];
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-            const int c = n.change[r][s];
-            if (c != 0) R[s] += (float)c * p;
-        }
-    }
-}
-
-// The network for V sites at once: each step's rate, orders and changes are
-// read once and applied to every site; per site the operations and their
-// order are exactly those of network_source.
 template <int S, int V>
-__device__ __forceinline__ void network_source_vec(const SharedNet &n, int kind, const float (&rho)[S][V],
+__device__ __forceinline__ void general_source_vec(const NetSmem &n, int kind, const float (&rho)[S][V],
                                                    float (&R)[S][V]) {
+    if (kind == kMassAction) {
+        network_source_vec<S, V>(n, rho, R);
+    } else {
 #pragma unroll
-    for (int s = 0; s < S; ++s)
+        for (int s = 0; s < S; ++s)
 #pragma unroll
-        for (int v = 0; v < V; ++v) R[s][v] = 0.f;
-    if (kind != kMassAction) return;
-    for (int r = 0; r < n.nr; ++r) {
-        float p[V];
-        const float k = n.ratef[r];
-#pragma unroll
-        for (int v = 0; v < V; ++v) p[v] = k;
-#pragma unroll
-        for (int j = 0; j < S; ++j) {
-            const int o = n.order[r][j];
-            for (int e = 0; e < o; ++e)
-#pragma unroll
-                for (int v = 0; v < V; ++v) p[v] *= rho[j][v];
-        }
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-            const int c = n.change[r][s];
-            if (c != 0) {
-                const float cf = (float)c;
-#pragma unroll
-                for (int v = 0; v < V; ++v) R[s][v] += cf * p[v];
-            }
-        }
+            for (int v = 0; v < V; ++v) R[s][v] = 0.f;
     }
 }
-
-// Post-collision value of one population.// Post-collision value of one population.
-__device__ __forceinline__ double relax(double f, double w, double rho, double om, double R) {
-    return __dadd_rn(__dadd_rn(f, __dmul_rn(__dsub_rn(__dmul_rn(w, rho), f), om)), __dmul_rn(w, R));
-}
-__device__ __forceinline__ float relax(float f, float w, float rho, float om, float R) {
-    return fmaf(1.f - om, f, w * (om * rho + R));
-}
-
-__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ float radd(float a, float b) { return a + b; }
 
 template <typename T, int Q, int S>
 __global__ void __launch_bounds__(kBX, 6) step_general_kernel(StepArgs a, int64_t tiles_x, int64_t ntiles) {
     using L = Lattice<Q>;
-    __shared__ SharedNet net;
+    __shared__ NetSmem net;
     load_net(a.net, net);
     const T *__restrict__ src = static_cast<const T *>(a.src);
     T *__restrict__ dst = static_cast<T *>(a.dst);
@@ -152,7 +74,7 @@ __global__ void __launch_bounds__(kBX, 6) step_general_kernel(StepArgs a, int64_
             for (int i = 1; i < Q; ++i) r = radd(r, f[s][i]);
             rho[s] = r;
         }
-        network_source<S>(net, a.rkind, rho, R);
+        general_source<S>(net, a.rkind, rho, R);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             const T om = (T)a.omega[s];
@@ -193,7 +115,7 @@ __device__ __forceinline__ void stvec(float *p, const float (&v)[V]) {
 template <int Q, int S, int V, int MINB>
 __global__ void __launch_bounds__(kBX, MINB) step_general_vec_kernel(StepArgs a, int64_t tiles_x, int64_t ntiles) {
     using L = Lattice<Q>;
-    __shared__ SharedNet net;
+    __shared__ NetSmem net;
     load_net(a.net, net);
     const float *__restrict__ src = static_cast<const float *>(a.src);
     float *__restrict__ dst = static_cast<float *>(a.dst);
@@ -245,7 +167,7 @@ __global__ void __launch_bounds__(kBX, MINB) step_general_vec_kernel(StepArgs a,
         }
         if (!live) continue;
         float R[S][V];
-        network_source_vec<S, V>(net, a.rkind, rho, R);
+        general_source_vec<S, V>(net, a.rkind, rho, R);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             const float om = (float)a.omega[s];
@@ -274,7 +196,7 @@ __global__ void __launch_bounds__(kBX, MINB) step_general_vec_kernel(StepArgs a,
 template <int Q, int S, int MINB>
 __global__ void __launch_bounds__(kBX, MINB) step_general_2pass_kernel(StepArgs a, int64_t tiles_x, int64_t ntiles) {
     using L = Lattice<Q>;
-    __shared__ SharedNet net;
+    __shared__ NetSmem net;
     load_net(a.net, net);
     const float *__restrict__ src = static_cast<const float *>(a.src);
     float *__restrict__ dst = static_cast<float *>(a.dst);
@@ -298,7 +220,7 @@ __global__ void __launch_bounds__(kBX, MINB) step_general_2pass_kernel(StepArgs 
             for (int i = 1; i < Q; ++i) r = radd(r, __ldg(sp + off(i)));
             rho[s] = r;
         }
-        network_source<S>(net, a.rkind, rho, R);
+        general_source<S>(net, a.rkind, rho, R);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             const float *sp = src + (int64_t)s * Q * plane;
@@ -316,7 +238,7 @@ __global__ void __launch_bounds__(kBX, MINB) step_general_2pass_kernel(StepArgs 
 
 template <typename T, int Q, int S>
 __global__ void __launch_bounds__(kBX) init_general_kernel(InitArgs a) {
-    __shared__ SharedNet net;
+    __shared__ NetSmem net;
     load_net(a.net, net);
     const int64_t x = (int64_t)blockIdx.x * kBX + threadIdx.x, y = blockIdx.y;
     if (x >= a.nx) return;
@@ -333,7 +255,7 @@ __global__ void __launch_bounds__(kBX) init_general_kernel(InitArgs a) {
         for (int i = 1; i < Q; ++i) r = radd(r, f[s][i]);
         rho[s] = r;
     }
-    network_source<S>(net, a.rkind, rho, R);
+    general_source<S>(net, a.rkind, rho, R);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
         const T om = (T)a.omega[s];
