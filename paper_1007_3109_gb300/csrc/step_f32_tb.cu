@@ -300,6 +300,53 @@ __device__ __forceinline__ void mbar_arrive(unsigned bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+// Level-0 row r for the warp-decoupled kernel, by the producer warp.  An
+// interior strip (halos inside the row) takes one bulk copy of
+// [x0 - 4, x0 + TX + 4) per plane.  A strip at the periodic edge takes one
+// bulk copy of [x0, x0 + TX) (16-byte aligned: x0 and nx are multiples of TX)
+// and its wrapped halos [x0 - 4, x0), [x0 + TX, x0 + TX + 4) by plain 16-byte
+// loads stored into the stage (HALO_LOADS; otherwise by three bulk copies,
+// which keep the producer asynchronous: single grids, where the edge strips
+// are a few blocks' whole share and would otherwise lag).  Then lane 0
+// arrives on the stage's full barrier (count 2 with the expect_tx arrival)
+// after a __syncwarp that orders the lanes' halo stores before it.  Grids one
+// strip wide (batched 256^2 instances) thus take one copy per plane instead
+// of three.
+template <int Q, int S, int TX, bool HALO_LOADS, typename Args>
+__device__ __forceinline__ void issue_row_tbw(const Args &a, int64_t r, int64_t x0, float *st, unsigned bar,
+                                              unsigned extra_tx) {
+    using G = TbGeom<Q, S, TX>;
+    const int lane = threadIdx.x & 31;
+    const float *src = static_cast<const float *>(a.src);
+    const bool interior = x0 >= 4 && x0 + TX + 4 <= a.nx;  // the halos do not wrap: one copy per plane
+    const bool loads = HALO_LOADS && !interior;
+    const unsigned per_plane = (unsigned)(loads ? TX : TX + 8) * 4u;
+    if (lane == 0) mbar_expect_tx(bar, per_plane * S * Q + extra_tx);
+    __syncwarp();
+    if (lane < S * Q) {
+        const int i = lane % Q;
+        const int ey = (Q == 9) ? Lattice<9>::ey(i) : Lattice<5>::ey(i);
+        const int64_t yr = wrap(wrap(r, a.ny) - ey, a.ny);
+        const float *row = src + (int64_t)lane * a.plane + yr * a.pitch;
+        float *d = st + lane * G::W0;
+        if (interior) {
+            bulk_copy(smem_u32(d), row + x0 - 4, per_plane, bar);
+        } else if (!loads) {
+            copy_periodic(d, row, x0 - 4, x0 + TX + 4, a.nx, bar, true);
+        } else {
+            bulk_copy(smem_u32(d + 4), row + x0, per_plane, bar);
+            const int64_t xl = x0 == 0 ? a.nx - 4 : x0 - 4;
+            const int64_t xr = x0 + TX == a.nx ? 0 : x0 + TX;
+            const float4 hl = *reinterpret_cast<const float4 *>(row + xl);
+            const float4 hr = *reinterpret_cast<const float4 *>(row + xr);
+            *reinterpret_cast<float4 *>(d) = hl;
+            *reinterpret_cast<float4 *>(d + TX + 4) = hr;
+        }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(bar);
+}
+
 // The fields of one grid a two-step segment needs, in registers (FP32 copies
 // of the relaxation rates and reaction constants: the values the one-step
 // kernels compute with).
@@ -359,7 +406,7 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB)
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     if (tid == 0) {
         for (int k = 0; k < NS; ++k) {
-            mbar_init(smem_u32(&full[k]), 1);
+            mbar_init(smem_u32(&full[k]), 2);  // expect_tx arrival + halo arrival
             mbar_init(smem_u32(&empty[k]), W);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -407,7 +454,7 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB)
                 }
                 // the consumers' reads of this stage (generic proxy) before the copies into it (async proxy)
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue_row<Q, S, TX>(g, y0 - 1 + j, x0, stages + sk * G::kStage, smem_u32(&full[sk]),
+                issue_row_tbw<Q, S, TX, BATCH>(g, y0 - 1 + j, x0, stages + sk * G::kStage, smem_u32(&full[sk]),
                                     (a.inject_timeout && blockIdx.x == 0 && tk == 0) ? 16u : 0u);
                 issued = tk + 1;
             }
