@@ -441,7 +441,7 @@ def network_mode(args):
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": "gs2x_8192", "nx": n, "ny": n, "species": S, "reaction_steps": len(net[0]),
-                       "precision": prec, "variant": names[best], "autotune_ms_per_launch": tuning,
+                       "precision": prec, "variant": names[best], "autotune_ms_per_step": tuning,
                        "streaming": "in-place (AA), one state copy" if args.inplace else "ping-pong, two state copies",
                        "l2": f"no flush: state of {(0.5 if args.inplace else 1) * bps * n * n / 1e9:.1f} GB >> 129 MB L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -627,7 +627,7 @@ def main():
             traffic = ent["bytes_per_launch"]
     single = None
     if tuning:
-        ones = {k: v for k, v in tuning.items() if v and not k.startswith("tb2")}
+        ones = {k: v for k, v in tuning.items() if v and B.variant_steps(k) == 1}
         if ones:
             k1 = min(ones, key=ones.get)
             gbs = bps * sites / (ones[k1] / 1e3) / 1e9
@@ -663,7 +663,7 @@ def main():
                    "mass_diagnostic": "fused into every launch (every step, or every second step with temporal blocking)",
                    "l2": f"no flush: state of {(1 if args.inplace else 2) * sim_state_bytes(args.lattice, args.precision, n) / 1e9:.2f} GB >> 129 MB L2",
                    "parallelism": f"replicas x{world}",
-                   "variant": variant_name, "autotune_ms_per_launch": tuning,
+                   "variant": variant_name, "autotune_ms_per_step": tuning,
                    "streaming": "in-place (AA), one state copy" if args.inplace else "ping-pong, two state copies"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "kernel": f"step_{args.precision}:{variant_name}",

@@ -214,21 +214,23 @@ LB_RD_API int lb_rd_launch_count(const lb_rd_handle *h, int64_t *launches);
 
 /* Launch variants and the autotuner.  The step kernel of a precision comes in
  * several launch variants (tile shape, register budget, cache policy, TMA
- * bulk-copy staging, temporal blocking of two steps per launch; see
- * lb_rd_variant_name).  lb_rd_autotune times every variant that fits the grid
- * on the handle's own state -- reading the current state and writing the
- * spare copy, so the simulation is unchanged -- with one warm-up launch and
- * `iters` timed launches each, and selects the fastest single-step variant
- * and, if faster per step, a two-step variant; the choice is cached per
- * (device, precision, lattice, species, nx, ny) and handles created later with
- * the same shape start from it.  With a two-step variant lb_rd_step advances
- * two steps per launch except for the last one or two steps.  times_ms (may
- * be NULL) receives the mean time per time step of each variant (-1 for a
- * variant that does not fit), at most max_times entries; *best the variant
- * used for the bulk of the steps.  Synchronises.  lb_rd_set_variant forces a
- * variant (a two-step one is used together with the current single-step
- * variant; -1 restores the cached or default choice); lb_rd_get_variant
- * returns the variant used for the bulk of the steps. */
+ * bulk-copy staging, temporal blocking of K = 2, 4 or 8 steps per launch:
+ * FP32 variants named tb2*_ (two steps) and deep<K>_ (K steps, the deep1_
+ * form one step); see lb_rd_variant_name).  lb_rd_autotune times every
+ * variant that fits the grid on the handle's own state -- reading the current
+ * state and writing the spare copy, so the simulation is unchanged -- with
+ * one warm-up launch and `iters` timed launches each, and selects the fastest
+ * single-step variant and, if faster per step, a multi-step variant; the
+ * choice is cached per (device, precision, lattice, species, nx, ny) and
+ * handles created later with the same shape start from it.  With a K-step
+ * variant lb_rd_step advances K steps per launch except for the last 1 .. K
+ * steps (single steps).  times_ms (may be NULL) receives the mean time per
+ * time step of each variant (-1 for a variant that does not fit), at most
+ * max_times entries; *best the variant used for the bulk of the steps.
+ * Synchronises.  lb_rd_set_variant forces a variant (a multi-step one is used
+ * together with the current single-step variant; -1 restores the cached or
+ * default choice); lb_rd_get_variant returns the variant used for the bulk of
+ * the steps. */
 LB_RD_API int lb_rd_variant_count(int32_t precision, int32_t *count);
 LB_RD_API const char *lb_rd_variant_name(int32_t precision, int32_t variant);
 /* The variants of one handle's configuration: configurations with more than

@@ -13,6 +13,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import re
 import time
 from ctypes import POINTER, c_double, c_int, c_int32, c_int64, c_size_t, c_void_p, c_char_p
 
@@ -278,8 +279,18 @@ def lb_rd_variant_name(precision, variant: int) -> str:
     return lib().lb_rd_variant_name(PRECISIONS.get(precision, precision), int(variant)).decode()
 
 
+def variant_steps(name: str) -> int:
+    """Time steps per launch of an FP32 launch variant, from its name: tb2*_
+    variants two, deep<K>_ variants K, the others one."""
+    m = re.match(r"deep(\d+)_", name)
+    if m:
+        return int(m.group(1))
+    return 2 if name.startswith("tb2") else 1
+
+
 def lb_rd_autotune(h: int, iters: int = 20, max_times: int = 64):
-    """Returns (best variant, mean ms per launch of every variant)."""
+    """Returns (best variant, mean ms per time step of every variant; -1 where
+    a variant does not fit the grid)."""
     best = c_int32(0)
     times = (c_double * max_times)()
     _check(lib().lb_rd_autotune(h, int(iters), ctypes.byref(best), times, max_times))

@@ -82,14 +82,14 @@ struct lb_rd_handle {
     int64_t launches = 0;
     int inject_timeout = 0;  // one-shot test switch for the bounded-wait error path
     int variant = 0;      // single-step launch variant of the step kernel
-    int tb_variant = -1;  // two-step (temporal blocking) variant, or -1
+    int tb_variant = -1;  // multi-step (temporal blocking, K steps per launch) variant, or -1
     bool general = false; // runs the general kernel
     bool inplace = false; // one state copy, AA pattern (buf[1] unused)
 };
 
 namespace {
 // Autotuner choices per (device, precision, Q, S, nx, ny): single-step
-// variant and two-step variant (-1 if none is faster).
+// variant and multi-step variant (-1 if none is faster).
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int64_t, int64_t>, std::pair<int, int>> g_tune_cache;
 
@@ -372,11 +372,12 @@ int lb_rd_step(lb_rd_handle *h, int64_t nsteps) {
         }
         return LB_RD_OK;
     }
-    // With a two-step variant, all but the last one or two steps go two at a
-    // time; the last launch is always a single step, so that the other state
-    // copy holds f*(t - 1) and rho(t) can be recomputed from it on demand.
-    const int64_t n_two = h->tb_variant >= 0 ? (nsteps - 1) / 2 : 0;
-    for (int64_t n = 0; n < n_two + (nsteps - 2 * n_two); ++n) {
+    // With a K-step variant, all but the last 1 .. K steps go K at a time; the
+    // last launch is always a single step, so that the other state copy holds
+    // f*(t - 1) and rho(t) can be recomputed from it on demand.
+    const int64_t K = h->tb_variant >= 0 ? variant_steps(h, h->tb_variant) : 1;
+    const int64_t n_two = K > 1 ? (nsteps - 1) / K : 0;
+    for (int64_t n = 0; n < n_two + (nsteps - K * n_two); ++n) {
         const bool two = n < n_two;
         a.src = h->buf[h->cur];
         a.dst = h->buf[h->cur ^ 1];
@@ -399,7 +400,7 @@ int lb_rd_step(lb_rd_handle *h, int64_t nsteps) {
             h->events.push_back(e1);
         }
         h->cur ^= 1;
-        h->t += two ? 2 : 1;
+        h->t += two ? K : 1;
     }
     if (nsteps > 0) h->mass_fresh = h->cfg.track_mass != 0;
     return LB_RD_OK;
@@ -623,7 +624,7 @@ int lb_rd_set_variant(lb_rd_handle *h, int32_t variant) {
                                       std::to_string(h->inplace   ? lbrd::kAAVariants[variant].sites
                                                      : h->general ? lbrd::kGeneralVariants[variant].sites
                                                                   : lbrd::kF32Variants[variant].nx_multiple));
-    if (variant_steps(h, variant) == 2) {
+    if (variant_steps(h, variant) >= 2) {
         h->tb_variant = variant;
     } else {
         h->variant = variant;
@@ -745,7 +746,7 @@ int lb_rd_autotune(lb_rd_handle *h, int32_t iters, int32_t *best, double *times_
             best1 = v;
             ms1 = per;
         }
-        if (steps == 2 && (best2 < 0 || per < ms2)) {
+        if (steps >= 2 && (best2 < 0 || per < ms2)) {
             best2 = v;
             ms2 = per;
         }

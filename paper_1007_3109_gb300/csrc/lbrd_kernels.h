@@ -83,7 +83,8 @@ cudaError_t launch_init_f64(int Q, int S, const InitArgs &a, cudaStream_t st);
 // Launch variants differ in tile shape, register budget and cache policy.
 struct F32Variant {
     const char *name;
-    int bx, by, minb, cache;  // cache: 0/1 register path policies, 2 bulk-copy ring, 3 temporal blocking
+    int bx, by, minb, cache;  // cache: 0/1 register path policies, 2 bulk-copy ring, 3 temporal blocking,
+                              // 4 temporal blocking to depth by with the levels in registers
     int steps;                // time steps per launch
     int nx_multiple;          // the variant needs nx % nx_multiple == 0
 };
@@ -93,6 +94,7 @@ cudaError_t launch_step_f32_variant(int v, int Q, int S, const StepArgs &a, cuda
 cudaError_t launch_step_f32_variant_b(int v, int Q, int S, const StepArgs &a, cudaStream_t st, bool per_tile);
 cudaError_t launch_step_f32_bulk(int v, int Q, int S, const StepArgs &a, cudaStream_t st);
 cudaError_t launch_step_f32_tb2(int v, int Q, int S, const StepArgs &a, cudaStream_t st);
+cudaError_t launch_step_f32_deep(int v, int Q, int S, const StepArgs &a, cudaStream_t st);
 StepShape step_shape_f32(int64_t nx, int64_t ny);
 cudaError_t launch_step_f32(int Q, int S, const StepArgs &a, cudaStream_t st);
 cudaError_t launch_init_f32(int Q, int S, const InitArgs &a, cudaStream_t st);

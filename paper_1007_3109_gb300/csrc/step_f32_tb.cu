@@ -23,12 +23,14 @@
 // as in the bulk-copy kernel (status word, drain, return).
 #include <atomic>
 
-#include "step_f32_kernel.cuh"
+#include "step_f32_tb_common.cuh"
 #include "lb_rd.h"
 
 namespace lbrd {
 
 namespace {
+
+using namespace tb;
 
 constexpr long long kWaitCycles = 1ll << 31;
 
@@ -116,32 +118,6 @@ __device__ __forceinline__ void issue_row(const Args &a, int64_t r, int64_t x0, 
         copy_periodic(st + lane * G::W0, row, x0 - 4, x0 + TX + 4, a.nx, bar, true);
     }
     (void)sizeof(L);
-}
-
-// The fused step of one site from S * Q pulled values.
-template <int Q, int S, typename Args>
-__device__ __forceinline__ void collide_site(const Args &a, float (&f)[S][Q], float (&rho)[S]) {
-    using L = Lattice<Q>;
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-        float r = f[s][0];
-#pragma unroll
-        for (int i = 1; i < Q; ++i) r += f[s][i];
-        rho[s] = r;
-    }
-    float R[S];
-    reaction_f32<S>(a.rkind, (float)a.kappa, (float)a.F, (float)a.k, rho, R);
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-        const float om = (float)a.omega[s];
-        const float c1 = 1.f - om;
-        const float t = om * rho[s] + R[s];
-        float wt[L::kClasses];
-#pragma unroll
-        for (int c = 0; c < L::kClasses; ++c) wt[c] = L::template wc<float>(c) * t;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) f[s][i] = fmaf(c1, f[s][i], wt[L::wclass(i)]);
-    }
 }
 
 // IL = 1 (needs NT >= TX + 2): thread t computes level-1 site t and level-2
@@ -345,33 +321,6 @@ __device__ __forceinline__ void issue_row_tbw(const Args &a, int64_t r, int64_t 
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(bar);
-}
-
-// The fields of one grid a two-step segment needs, in registers (FP32 copies
-// of the relaxation rates and reaction constants: the values the one-step
-// kernels compute with).
-struct SegArgs {
-    const void *src;
-    void *dst;
-    int64_t nx, ny, pitch, plane;
-    float omega[2];
-    int rkind;
-    float kappa, F, k;
-};
-
-__device__ __forceinline__ void load_seg(const StepArgs &a, SegArgs &g) {
-    g.src = a.src;
-    g.dst = a.dst;
-    g.nx = a.nx;
-    g.ny = a.ny;
-    g.pitch = a.pitch;
-    g.plane = a.plane;
-    g.omega[0] = (float)a.omega[0];
-    g.omega[1] = (float)a.omega[1];
-    g.rkind = a.rkind;
-    g.kappa = (float)a.kappa;
-    g.F = (float)a.F;
-    g.k = (float)a.k;
 }
 
 // Warp-decoupled two-step kernel: W consumer warps and one producer warp.

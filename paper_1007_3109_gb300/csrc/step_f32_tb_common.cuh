@@ -1,0 +1,68 @@
+// Per-site step and per-grid arguments shared by the multi-step FP32
+// kernels (two steps per launch in step_f32_tb.cu, K steps per launch in
+// step_f32_deep.cu).  collide_site is the one-step kernels' arithmetic
+// (density in index order, reaction, relaxation with source of Eq. relax in
+// the FP32 form fma(1 - omega, f, w (omega rho + R))), so a multi-step launch
+// gives the bits of as many single steps.
+#pragma once
+
+#include "step_f32_kernel.cuh"
+
+namespace lbrd {
+namespace tb {
+
+// The fused step of one site from S * Q pulled values.
+template <int Q, int S, typename Args>
+__device__ __forceinline__ void collide_site(const Args &a, float (&f)[S][Q], float (&rho)[S]) {
+    using L = Lattice<Q>;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        float r = f[s][0];
+#pragma unroll
+        for (int i = 1; i < Q; ++i) r += f[s][i];
+        rho[s] = r;
+    }
+    float R[S];
+    reaction_f32<S>(a.rkind, (float)a.kappa, (float)a.F, (float)a.k, rho, R);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const float om = (float)a.omega[s];
+        const float c1 = 1.f - om;
+        const float t = om * rho[s] + R[s];
+        float wt[L::kClasses];
+#pragma unroll
+        for (int c = 0; c < L::kClasses; ++c) wt[c] = L::template wc<float>(c) * t;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f[s][i] = fmaf(c1, f[s][i], wt[L::wclass(i)]);
+    }
+}
+
+// The fields of one grid a multi-step segment needs, in registers (FP32 copies
+// of the relaxation rates and reaction constants: the values the one-step
+// kernels compute with).
+struct SegArgs {
+    const void *src;
+    void *dst;
+    int64_t nx, ny, pitch, plane;
+    float omega[2];
+    int rkind;
+    float kappa, F, k;
+};
+
+__device__ __forceinline__ void load_seg(const StepArgs &a, SegArgs &g) {
+    g.src = a.src;
+    g.dst = a.dst;
+    g.nx = a.nx;
+    g.ny = a.ny;
+    g.pitch = a.pitch;
+    g.plane = a.plane;
+    g.omega[0] = (float)a.omega[0];
+    g.omega[1] = (float)a.omega[1];
+    g.rkind = a.rkind;
+    g.kappa = (float)a.kappa;
+    g.F = (float)a.F;
+    g.k = (float)a.k;
+}
+
+}  // namespace tb
+}  // namespace lbrd
