@@ -77,6 +77,11 @@ const F32Variant kF32Variants[] = {
     {"deep4_128_minb3", 128, 4, 3, 4, 4, 1},
     {"deep8_128_minb2", 128, 8, 2, 4, 8, 1},
     {"deep8_128_minb3", 128, 8, 3, 4, 8, 1},
+    // the same with the level-0 rows staged in 16-byte chunks (nx % 4 == 0)
+    {"deep2v_128_minb4", 128, 2, 4, 4, 2, 4},
+    {"deep4v_128_minb4", 128, 4, 4, 4, 4, 4},
+    {"deep4v_128_minb3", 128, 4, 3, 4, 4, 4},
+    {"deep8v_128_minb2", 128, 8, 2, 4, 8, 4},
 };
 const int kF32VariantCount = sizeof(kF32Variants) / sizeof(kF32Variants[0]);
 

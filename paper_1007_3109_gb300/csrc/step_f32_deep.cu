@@ -46,6 +46,10 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src) {
                  : "memory");
 }
 
+__device__ __forceinline__ void cp_async16(unsigned dst, const float *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 
 template <int N>
@@ -58,20 +62,28 @@ __host__ __device__ __forceinline__ int64_t wrap_mod(int64_t a, int64_t n) {
     return r < 0 ? r + n : r;
 }
 
-template <int Q, int S, int K, int NW, int NS, int MINB>
+// V16: level-0 rows staged in 16-byte chunks (needs nx and the row pitch to
+// be multiples of 4): the warp's columns xb - 1 .. xb + 32 lie in the ten
+// aligned chunks [a0, a0 + 40), a0 = xb - 1 rounded down to a multiple of 4
+// (a chunk never straddles the periodic seam); lane 10 q + c (q < 3, c < 10)
+// copies chunk c of planes q, q + 3, q + 6, ... (lanes 30, 31 idle).
+// Otherwise 4-byte copies: lane l copies column xb - 1 + l of every plane,
+// lanes 0 and 1 also columns xb + 31, xb + 32.
+template <int Q, int S, int K, int NW, int NS, int MINB, bool V16>
 __global__ void __launch_bounds__(NW * 32, MINB)
     step_deep_kernel(StepArgs a, int64_t nstrips, int64_t nbands, int64_t band) {
     using L = Lattice<Q>;
     constexpr int SQ = S * Q;
-    constexpr int CW = 34;         // staged columns of a warp row: xb - 1 .. xb + 32
-    constexpr int kRow = SQ * CW;  // one staged row, all planes
-    constexpr int P = NS - 3;      // rows staged ahead of use
-    constexpr int WO = 34 - 2 * K; // output columns per warp
+    constexpr int CW = V16 ? 40 : 34;  // staged columns of a warp row
+    constexpr int kRow = SQ * CW;      // one staged row, all planes
+    constexpr int P = NS - 3;          // rows staged ahead of use
+    constexpr int WO = 34 - 2 * K;     // output columns per warp
     constexpr int KC = K > 1 ? K - 1 : 1;
     static_assert(K >= 1 && K <= 8 && NS >= 4, "depth 1 .. 8, at least four staged rows");
     extern __shared__ __align__(16) float smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float *ring = smem + (size_t)w * NS * kRow;
+    const unsigned ring_s = static_cast<unsigned>(__cvta_generic_to_shared(ring));
     SegArgs g;
     load_seg(a, g);
     const float *__restrict__ src = static_cast<const float *>(g.src);
@@ -81,24 +93,38 @@ __global__ void __launch_bounds__(NW * 32, MINB)
     for (int s = 0; s < S; ++s) acc[s] = 0.0;
     const int64_t nwarps = (int64_t)gridDim.x * NW;
     const int64_t units = nstrips * nbands;
+    const int cq = lane / 10, cc = lane - 10 * cq;  // V16 copy role: plane residue, chunk
     for (int64_t u = (int64_t)blockIdx.x * NW + w; u < units; u += nwarps) {
         const int64_t b = u / nstrips, strip = u - b * nstrips;
         const int64_t y0 = b * band;
         const int64_t ly = g.ny - y0 < band ? g.ny - y0 : band;
-        const int64_t xb = strip * WO - (K - 1);            // column of lane 0
-        const int64_t cA = wrap_mod(xb - 1 + lane, g.nx);   // staged column `lane`
-        const int64_t cB = wrap_mod(xb + 31 + lane, g.nx);  // staged column 32 + lane (lanes 0, 1)
-        const int64_t nrows = ly + 2 * K;                   // iterations: level-0 rows y0 - K .. y0 + ly + K - 1
-        int64_t yl = wrap_mod(y0 - K, g.ny);                // next level-0 row to stage
+        const int64_t xb = strip * WO - (K - 1);  // column of lane 0
+        const int64_t a0 = V16 ? (xb - 1) - wrap_mod(xb - 1, 4) : xb - 1;
+        const int o = (int)(xb - 1 - a0);         // staged column of xb - 1
+        // source offsets of this lane's copies (elements, row excluded)
+        const int64_t offA = V16 ? (int64_t)cq * g.plane + wrap_mod(a0 + 4 * cc, g.nx) : wrap_mod(xb - 1 + lane, g.nx);
+        const int64_t offB = V16 ? 0 : wrap_mod(xb + 31 + lane, g.nx);
+        const int64_t nrows = ly + 2 * K;  // iterations: level-0 rows y0 - K .. y0 + ly + K - 1
+        int64_t yl = wrap_mod(y0 - K, g.ny);  // next level-0 row to stage
         // stage level-0 row j into ring slot `slot`; one commit group per row (empty past the band)
         auto stage = [&](int64_t j, int slot) {
             if (j < nrows) {
-                float *d = ring + slot * kRow;
                 const float *row = src + yl * g.pitch;
+                if constexpr (V16) {
+                    if (lane < 30) {
+                        const unsigned d = ring_s + (unsigned)(slot * kRow + cq * CW + 4 * cc) * 4u;
+                        const float *sp = row + offA;
 #pragma unroll
-                for (int p = 0; p < SQ; ++p) {
-                    cp_async4(d + p * CW + lane, row + p * g.plane + cA);
-                    if (lane < 2) cp_async4(d + p * CW + 32 + lane, row + p * g.plane + cB);
+                        for (int r = 0; r < (SQ + 2) / 3; ++r)
+                            if (cq + 3 * r < SQ) cp_async16(d + (unsigned)(3 * r * CW * 4), sp + 3 * r * g.plane);
+                    }
+                } else {
+                    float *d = ring + slot * kRow;
+#pragma unroll
+                    for (int p = 0; p < SQ; ++p) {
+                        cp_async4(d + p * CW + lane, row + p * g.plane + offA);
+                        if (lane < 2) cp_async4(d + p * CW + 32 + lane, row + p * g.plane + offB);
+                    }
                 }
             }
             yl = yl + 1 == g.ny ? 0 : yl + 1;
@@ -126,12 +152,13 @@ __global__ void __launch_bounds__(NW * 32, MINB)
             __syncwarp();        // ... and every other lane's
             const int s1 = sl == 0 ? NS - 1 : sl - 1, s2 = s1 == 0 ? NS - 1 : s1 - 1;
             // staged rows of iterations j - 2, j - 1, j: pulled with e_iy = +1, 0, -1
-            const float *rows0[3] = {ring + s2 * kRow, ring + s1 * kRow, ring + sl * kRow};
+            const float *rows0[3] = {ring + s2 * kRow + o + lane + 1, ring + s1 * kRow + o + lane + 1,
+                                     ring + sl * kRow + o + lane + 1};
             float f[S][Q], rho[S];
 #pragma unroll
             for (int s = 0; s < S; ++s)
 #pragma unroll
-                for (int i = 0; i < Q; ++i) f[s][i] = rows0[1 - L::ey(i)][(s * Q + i) * CW + lane + 1 - L::ex(i)];
+                for (int i = 0; i < Q; ++i) f[s][i] = rows0[1 - L::ey(i)][(s * Q + i) * CW - L::ex(i)];
             collide_site<Q, S>(g, f, rho);
 #pragma unroll
             for (int m = 1; m < K; ++m) {  // level m + 1 from level m (carried index m - 1)
@@ -140,7 +167,8 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                 for (int s = 0; s < S; ++s)
 #pragma unroll
                     for (int i = 0; i < Q; ++i) {
-                        const float v = L::ey(i) < 0 ? f[s][i] : (L::ey(i) == 0 ? E0[m - 1][s][i] : P2[m - 1][s][i]);
+                        const float v =
+                            L::ey(i) < 0 ? f[s][i] : (L::ey(i) == 0 ? E0[m - 1][s][i] : P2[m - 1][s][i]);
                         h[s][i] = L::ex(i) > 0   ? __shfl_up_sync(kFullMask, v, 1)
                                   : L::ex(i) < 0 ? __shfl_down_sync(kFullMask, v, 1)
                                                  : v;
@@ -181,11 +209,12 @@ __global__ void __launch_bounds__(NW * 32, MINB)
     if (a.mass_out) block_mass_reduce<S, NW * 32>(acc, a.partials, a.counter, a.mass_out);
 }
 
-template <int Q, int S, int K, int NW, int NS, int MINB>
+template <int Q, int S, int K, int NW, int NS, int MINB, bool V16>
 cudaError_t launch_deep(const StepArgs &a, cudaStream_t st) {
     constexpr int WO = 34 - 2 * K;
-    const size_t smem = (size_t)NW * NS * S * Q * 34 * sizeof(float);
-    auto kern = step_deep_kernel<Q, S, K, NW, NS, MINB>;
+    if (V16 && (a.nx % 4 != 0 || a.pitch % 4 != 0)) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)NW * NS * S * Q * (V16 ? 40 : 34) * sizeof(float);
+    auto kern = step_deep_kernel<Q, S, K, NW, NS, MINB, V16>;
     static std::atomic<bool> configured[64] = {};  // per device ordinal (handles on several threads)
     int dev = 0;
     cudaGetDevice(&dev);
@@ -219,12 +248,12 @@ cudaError_t launch_deep(const StepArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int K, int NW, int NS, int MINB>
+template <int K, int NW, int NS, int MINB, bool V16 = false>
 cudaError_t dispatch_deep(int Q, int S, const StepArgs &a, cudaStream_t st) {
-    if (Q == 9 && S == 1) return launch_deep<9, 1, K, NW, NS, MINB>(a, st);
-    if (Q == 9 && S == 2) return launch_deep<9, 2, K, NW, NS, MINB>(a, st);
-    if (Q == 5 && S == 1) return launch_deep<5, 1, K, NW, NS, MINB>(a, st);
-    if (Q == 5 && S == 2) return launch_deep<5, 2, K, NW, NS, MINB>(a, st);
+    if (Q == 9 && S == 1) return launch_deep<9, 1, K, NW, NS, MINB, V16>(a, st);
+    if (Q == 9 && S == 2) return launch_deep<9, 2, K, NW, NS, MINB, V16>(a, st);
+    if (Q == 5 && S == 1) return launch_deep<5, 1, K, NW, NS, MINB, V16>(a, st);
+    if (Q == 5 && S == 2) return launch_deep<5, 2, K, NW, NS, MINB, V16>(a, st);
     return cudaErrorInvalidValue;
 }
 
@@ -239,6 +268,10 @@ cudaError_t launch_step_f32_deep(int v, int Q, int S, const StepArgs &a, cudaStr
         case 3: return dispatch_deep<4, 4, 4, 3>(Q, S, a, st);
         case 4: return dispatch_deep<8, 4, 4, 2>(Q, S, a, st);
         case 5: return dispatch_deep<8, 4, 4, 3>(Q, S, a, st);
+        case 6: return dispatch_deep<2, 4, 4, 4, true>(Q, S, a, st);
+        case 7: return dispatch_deep<4, 4, 4, 4, true>(Q, S, a, st);
+        case 8: return dispatch_deep<4, 4, 4, 3, true>(Q, S, a, st);
+        case 9: return dispatch_deep<8, 4, 4, 2, true>(Q, S, a, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -15,7 +15,7 @@ cudaError_t launch_step_f32_variant_b(int v, int Q, int S, const StepArgs &a, cu
         case 14: case 15: case 16: case 17: case 18: case 19: case 20: case 21: case 22: case 23:
         case 24: case 25: case 26: case 27:
             return per_tile ? cudaErrorInvalidValue : launch_step_f32_tb2(v - 14, Q, S, a, st);
-        case 28: case 29: case 30: case 31: case 32: case 33:
+        case 28: case 29: case 30: case 31: case 32: case 33: case 34: case 35: case 36: case 37:
             return per_tile ? cudaErrorInvalidValue : launch_step_f32_deep(v - 28, Q, S, a, st);
         default: return cudaErrorInvalidValue;
     }
