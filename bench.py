@@ -633,6 +633,22 @@ def main():
             gbs = bps * sites / (ones[k1] / 1e3) / 1e9
             single = {"variant": k1, "ms_per_step": ones[k1], "GBs": gbs, "frac": gbs / peak,
                       "source": "autotuner, CUDA events"}
+    # Temporal-blocking depth sweep: per steps-per-launch K, the fastest variant
+    # of the autotuner's sweep (K = 1: every single-step kernel).  A K-step
+    # launch moves the state once (bps per site), so its HBM use per launch is
+    # bps * sites / (K * ms per step).
+    depth = {}
+    for name, ms in tuning.items():
+        if not ms:
+            continue
+        kk = B.variant_steps(name)
+        if kk not in depth or ms < depth[kk]["ms_per_step"]:
+            depth[kk] = {"variant": name, "ms_per_step": ms}
+    for kk, d in depth.items():
+        gbs = bps * sites / (d["ms_per_step"] * kk / 1e3) / 1e9
+        d.update({"MLUPS": ssu_per_step / (d["ms_per_step"] / 1e3) / 1e6, "hbm_GBs_per_launch": gbs,
+                  "hbm_frac_per_launch": gbs / peak})
+    depth = {str(kk): depth[kk] for kk in sorted(depth)}
 
     # -- end to end through the C ABI with host buffers --------------------------
     del rho0_dev
@@ -660,7 +676,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.workload, "lattice": args.lattice, "nx": n, "ny": n, "species": 2,
                    "precision": args.precision, "lb_steps_per_step": 1,
-                   "mass_diagnostic": "fused into every launch (every step, or every second step with temporal blocking)",
+                   "mass_diagnostic": "fused into every launch (every step, or every K-th step with K steps per launch)",
                    "l2": f"no flush: state of {(1 if args.inplace else 2) * sim_state_bytes(args.lattice, args.precision, n) / 1e9:.2f} GB >> 129 MB L2",
                    "parallelism": f"replicas x{world}",
                    "variant": variant_name, "autotune_ms_per_step": tuning,
@@ -670,6 +686,7 @@ def main():
                      "steps_per_launch": steps_per_launch, "bytes_per_site_per_launch": bps,
                      "effective_per_step_GBs": effective, "effective_frac": effective / peak,
                      "peak_kind": peak_kind, "avg_launch_ms": avg_launch_s * 1e3, "single_step": single},
+        "depth_sweep": depth or None,
         "e2e": {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "lb_steps": e2e_steps, "path": "lb_rd_init(host) + lb_rd_step + lb_rd_moments(host)"},
         "gpu_launches": int(launches),

@@ -82,6 +82,12 @@ const F32Variant kF32Variants[] = {
     {"deep4v_128_minb4", 128, 4, 4, 4, 4, 4},
     {"deep4v_128_minb3", 128, 4, 3, 4, 4, 4},
     {"deep8v_128_minb2", 128, 8, 2, 4, 8, 4},
+    {"deep4v_128_minb3_s5", 128, 4, 3, 4, 4, 4},
+    {"deep4v_192_minb2", 192, 4, 2, 4, 4, 4},
+    {"deep4v_192_minb2_s5", 192, 4, 2, 4, 4, 4},
+    {"deep4v_96_minb4", 96, 4, 4, 4, 4, 4},
+    {"deep6v_128_minb2", 128, 6, 2, 4, 6, 4},
+    {"deep8v_192_minb1", 192, 8, 1, 4, 8, 4},
 };
 const int kF32VariantCount = sizeof(kF32Variants) / sizeof(kF32Variants[0]);
 

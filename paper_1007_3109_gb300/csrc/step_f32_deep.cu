@@ -272,6 +272,12 @@ cudaError_t launch_step_f32_deep(int v, int Q, int S, const StepArgs &a, cudaStr
         case 7: return dispatch_deep<4, 4, 4, 4, true>(Q, S, a, st);
         case 8: return dispatch_deep<4, 4, 4, 3, true>(Q, S, a, st);
         case 9: return dispatch_deep<8, 4, 4, 2, true>(Q, S, a, st);
+        case 10: return dispatch_deep<4, 4, 5, 3, true>(Q, S, a, st);
+        case 11: return dispatch_deep<4, 6, 4, 2, true>(Q, S, a, st);
+        case 12: return dispatch_deep<4, 6, 5, 2, true>(Q, S, a, st);
+        case 13: return dispatch_deep<4, 3, 4, 4, true>(Q, S, a, st);
+        case 14: return dispatch_deep<6, 4, 4, 2, true>(Q, S, a, st);
+        case 15: return dispatch_deep<8, 6, 4, 1, true>(Q, S, a, st);
         default: return cudaErrorInvalidValue;
     }
 }
