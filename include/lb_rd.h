@@ -286,9 +286,14 @@ LB_RD_API int lb_rd_batch_set_graph(lb_rd_batch *b, int32_t steps_per_graph);
 
 /* Time steps per launch: 2 runs the two-step (temporal blocking) kernel over
  * all instances, bitwise the same as two single steps; it needs FP32
- * instances with two state copies and nx a multiple of 256 (the default
- * then), otherwise EINVAL.  1: one step per launch.  The last step of every
- * lb_rd_batch_step call is a single step (it writes the densities). */
+ * instances with two state copies and nx a multiple of 256.  4, 6 or 8 run
+ * the depth-K kernel over the (band, strip) units of all instances (FP32, two
+ * state copies, any nx; bitwise the same as K single steps; the default for
+ * such batches: 6 for D2Q9, 4 for D2Q5).  Otherwise EINVAL.  1: one step per
+ * launch (the default for other batches).  The last step of every
+ * lb_rd_batch_step call is a single step (it writes the densities); the
+ * graphs of lb_rd_batch_set_graph then hold steps_per_graph / K launches.
+ * Synchronises the batch's stream. */
 LB_RD_API int lb_rd_batch_set_steps_per_launch(lb_rd_batch *b, int32_t k);
 
 /* Densities and FP64 mass of instance idx at the batch's current time (as

@@ -161,12 +161,19 @@ struct lb_rd_batch {
     int64_t t = 0, launches = 0;
     int graph_steps = 64;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // by starting parity
-    // two steps per launch (FP32, two state copies, every nx % strip == 0)
+    // K steps per launch: K = 2 the two-step kernel (FP32, two state copies,
+    // every nx % strip == 0), K = 4, 6, 8 the depth-K kernel (FP32, two state
+    // copies); tb_graph holds graphs of K-step launches for the current K
     bool tb_ok = false;
     int steps_per_launch = 1;
     lbrd::TbwItem *d_tb[2] = {nullptr, nullptr};  // by buffer parity
     int64_t tb_units = 0;
     cudaGraphExec_t tb_graph[2] = {nullptr, nullptr};
+    bool deep_ok = false, deep_v16 = false;
+    std::vector<lbrd::DeepItem> deep_base;            // per instance, without buffers
+    lbrd::DeepItem *d_deep[2] = {nullptr, nullptr};  // by buffer parity, planned for deep_K
+    int64_t deep_units = 0;
+    int deep_K = 0;
 };
 
 namespace {
@@ -196,8 +203,35 @@ void drop_graphs(lb_rd_batch *b) {
         }
 }
 
-cudaError_t launch_two(lb_rd_batch *b, int parity) {
-    return lbrd::launch_batch_tb2(b->d_tb[parity], (int)b->cfgs.size(), b->tb_units, b->Q, b->S, b->stream);
+// One launch of steps_per_launch (>= 2) steps from buffer parity `parity`.
+cudaError_t launch_multi(lb_rd_batch *b, int parity) {
+    if (b->steps_per_launch == 2)
+        return lbrd::launch_batch_tb2(b->d_tb[parity], (int)b->cfgs.size(), b->tb_units, b->Q, b->S, b->stream);
+    return lbrd::launch_batch_deep(b->steps_per_launch, b->Q, b->S, b->deep_v16, b->d_deep[parity],
+                                   (int)b->cfgs.size(), b->deep_units, b->stream);
+}
+
+// Plans and uploads the depth-K descriptors of both parities.
+cudaError_t plan_deep(lb_rd_batch *b, int K) {
+    const int n = (int)b->cfgs.size();
+    std::vector<lbrd::DeepItem> v = b->deep_base;
+    const int64_t units = lbrd::batch_deep_plan(K, b->Q, b->S, b->deep_v16, v.data(), n);
+    if (units < 0) return cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
+    for (int parity = 0; parity < 2 && !e; ++parity) {
+        for (int i = 0; i < n; ++i) {
+            char *c0 = b->buf[0] + b->state_off[i], *c1 = b->buf[1] + b->state_off1[i];
+            v[i].a.src = parity ? c1 : c0;
+            v[i].a.dst = parity ? c0 : c1;
+        }
+        if (!b->d_deep[parity]) e = cudaMalloc(&b->d_deep[parity], n * sizeof(lbrd::DeepItem));
+        if (!e) e = cudaMemcpy(b->d_deep[parity], v.data(), n * sizeof(lbrd::DeepItem), cudaMemcpyHostToDevice);
+    }
+    if (!e) {
+        b->deep_units = units;
+        b->deep_K = K;
+    }
+    return e;
 }
 
 }  // namespace
@@ -213,6 +247,7 @@ int lb_rd_batch_destroy(lb_rd_batch *b) {
     cudaFree(b->rho);
     for (auto p : b->d_items) cudaFree(p);
     for (auto p : b->d_tb) cudaFree(p);
+    for (auto p : b->d_deep) cudaFree(p);
     cudaFree(b->stage);
     cudaFree(b->partials);
     cudaFree(b->counter);
@@ -339,6 +374,25 @@ int lb_rd_batch_create(const lb_rd_config *cfgs, int32_t n, lb_rd_batch **out) {
         }
         b->steps_per_launch = 2;
     }
+    // depth-K descriptors (planned when K >= 4 is selected): FP32 with two state copies
+    b->deep_ok = prec == LB_RD_FP32;
+    b->deep_v16 = true;
+    for (int i = 0; i < n; ++i) {
+        if (b->inplace[i]) b->deep_ok = false;
+        if (cfgs[i].nx % 4 || b->pitch[i] % 4) b->deep_v16 = false;
+    }
+    if (b->deep_ok) {
+        b->deep_base.resize(n);
+        for (int i = 0; i < n; ++i) {
+            b->deep_base[i] = lbrd::DeepItem{};
+            b->deep_base[i].a = items[i].a;
+            b->deep_base[i].a.rho_out = nullptr;
+        }
+        // default: the depth-K kernel, K = 6 (D2Q9) or 4 (D2Q5)
+        const int K = b->Q == 9 ? 6 : 4;
+        if (!e) e = plan_deep(b, K);
+        if (!e) b->steps_per_launch = K;
+    }
     if (e) {
         int rc = cuda_err(e, "lb_rd_batch_create allocation");
         lb_rd_batch_destroy(b);
@@ -410,7 +464,8 @@ int lb_rd_batch_set_graph(lb_rd_batch *b, int32_t steps_per_graph) {
     return LB_RD_OK;
 }
 
-// two == true: graph_steps / 2 two-step launches (parity alternates per launch).
+// two == true: graph_steps / K launches of K = steps_per_launch steps (parity
+// alternates per launch).
 static int capture_graph(lb_rd_batch *b, int parity, bool two = false) {
     // A private stream: capturing on the legacy default stream is not allowed.
     cudaStream_t cs;
@@ -420,8 +475,9 @@ static int capture_graph(lb_rd_batch *b, int parity, bool two = false) {
     b->stream = cs;
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    const int nl = two ? b->graph_steps / 2 : b->graph_steps;
-    for (int k = 0; k < nl && !e; ++k) e = two ? launch_two(b, (parity + k) & 1) : launch_one(b, (parity + k) & 1, false);
+    const int nl = two ? b->graph_steps / b->steps_per_launch : b->graph_steps;
+    for (int k = 0; k < nl && !e; ++k)
+        e = two ? launch_multi(b, (parity + k) & 1) : launch_one(b, (parity + k) & 1, false);
     cudaError_t e2 = cudaStreamEndCapture(cs, &g);
     b->stream = saved;
     if (!e) e = e2;
@@ -440,10 +496,11 @@ int lb_rd_batch_step(lb_rd_batch *b, int64_t nsteps) {
             return report_error(LB_RD_EINVAL, "lb_rd_batch_step: instance " + std::to_string(i) + " not initialised");
     if (nsteps == 0) return LB_RD_OK;
     int64_t body = nsteps - 1;  // the last step also writes the densities
-    if (b->steps_per_launch == 2 && body >= 2) {
-        int64_t n_two = body / 2;
-        body -= 2 * n_two;
-        const int per_graph = b->graph_steps / 2;  // two-step launches per graph
+    const int K = b->steps_per_launch;
+    if (K >= 2 && body >= K) {
+        int64_t n_two = body / K;
+        body -= K * n_two;
+        const int per_graph = b->graph_steps / K;  // K-step launches per graph
         if (per_graph > 0 && n_two >= per_graph) {
             const int64_t reps = n_two / per_graph;
             for (int64_t r = 0; r < reps; ++r) {
@@ -456,14 +513,14 @@ int lb_rd_batch_step(lb_rd_batch *b, int64_t nsteps) {
                 if (per_graph & 1) b->cur ^= 1;  // an odd number of launches flips the buffers
             }
             b->launches += reps * per_graph;
-            b->t += reps * per_graph * 2;
+            b->t += reps * per_graph * K;
             n_two -= reps * per_graph;
         }
         for (int64_t k = 0; k < n_two; ++k) {
-            cudaError_t e = launch_two(b, b->cur);
-            if (e) return cuda_err(e, "batch two-step kernel");
+            cudaError_t e = launch_multi(b, b->cur);
+            if (e) return cuda_err(e, "batch multi-step kernel");
             b->cur ^= 1;
-            b->t += 2;
+            b->t += K;
             b->launches++;
         }
     }
@@ -493,10 +550,19 @@ int lb_rd_batch_step(lb_rd_batch *b, int64_t nsteps) {
 
 int lb_rd_batch_set_steps_per_launch(lb_rd_batch *b, int32_t k) {
     if (!b) return report_error(LB_RD_EINVAL, "batch is NULL");
-    if (k != 1 && k != 2) return report_error(LB_RD_EINVAL, "steps per launch must be 1 or 2");
+    if (k != 1 && k != 2 && k != 4 && k != 6 && k != 8)
+        return report_error(LB_RD_EINVAL, "steps per launch must be 1, 2, 4, 6 or 8");
     if (k == 2 && !b->tb_ok)
         return report_error(LB_RD_EINVAL, "two steps per launch need FP32 instances with two state copies and "
                                           "nx a multiple of " + std::to_string(lbrd::batch_tb2_strip()));
+    if (k >= 4 && !b->deep_ok)
+        return report_error(LB_RD_EINVAL, "4, 6 or 8 steps per launch need FP32 instances with two state copies");
+    cudaStreamSynchronize(b->stream);
+    if (k >= 4 && b->deep_K != k) {
+        cudaError_t e = plan_deep(b, k);
+        if (e) return cuda_err(e, "lb_rd_batch_set_steps_per_launch");
+    }
+    if (k != b->steps_per_launch) drop_graphs(b);  // the multi-step graphs hold launches of the old K
     b->steps_per_launch = k;
     return LB_RD_OK;
 }

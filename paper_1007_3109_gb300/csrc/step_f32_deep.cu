@@ -69,9 +69,12 @@ __host__ __device__ __forceinline__ int64_t wrap_mod(int64_t a, int64_t n) {
 // copies chunk c of planes q, q + 3, q + 6, ... (lanes 30, 31 idle).
 // Otherwise 4-byte copies: lane l copies column xb - 1 + l of every plane,
 // lanes 0 and 1 also columns xb + 31, xb + 32.
-template <int Q, int S, int K, int NW, int NS, int MINB, bool V16>
+// BATCH: the units of a list of grids (DeepItem, sorted by unit_begin; each
+// with its own strips and band height) instead of one grid.
+template <int Q, int S, int K, int NW, int NS, int MINB, bool V16, bool BATCH>
 __global__ void __launch_bounds__(NW * 32, MINB)
-    step_deep_kernel(StepArgs a, int64_t nstrips, int64_t nbands, int64_t band) {
+    step_deep_kernel(StepArgs a, int64_t nstrips, int64_t nbands, int64_t band, const DeepItem *__restrict__ items,
+                     int nitems, int64_t total_units) {
     using L = Lattice<Q>;
     constexpr int SQ = S * Q;
     constexpr int CW = V16 ? 40 : 34;  // staged columns of a warp row
@@ -85,19 +88,28 @@ __global__ void __launch_bounds__(NW * 32, MINB)
     float *ring = smem + (size_t)w * NS * kRow;
     const unsigned ring_s = static_cast<unsigned>(__cvta_generic_to_shared(ring));
     SegArgs g;
-    load_seg(a, g);
-    const float *__restrict__ src = static_cast<const float *>(g.src);
-    float *__restrict__ dst = static_cast<float *>(g.dst);
+    if (!BATCH) load_seg(a, g);
     double acc[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[s] = 0.0;
     const int64_t nwarps = (int64_t)gridDim.x * NW;
-    const int64_t units = nstrips * nbands;
+    const int64_t units = BATCH ? total_units : nstrips * nbands;
     const int cq = lane / 10, cc = lane - 10 * cq;  // V16 copy role: plane residue, chunk
+    int it = 0;  // BATCH: the item of unit u (a warp's units only increase)
     for (int64_t u = (int64_t)blockIdx.x * NW + w; u < units; u += nwarps) {
-        const int64_t b = u / nstrips, strip = u - b * nstrips;
-        const int64_t y0 = b * band;
-        const int64_t ly = g.ny - y0 < band ? g.ny - y0 : band;
+        int64_t local = u, ns = nstrips, bh = band;
+        if constexpr (BATCH) {
+            while (it + 1 < nitems && items[it + 1].unit_begin <= u) ++it;
+            load_seg(items[it].a, g);
+            local = u - items[it].unit_begin;
+            ns = items[it].nstrips;
+            bh = items[it].band;
+        }
+        const float *__restrict__ src = static_cast<const float *>(g.src);
+        float *__restrict__ dst = static_cast<float *>(g.dst);
+        const int64_t b = local / ns, strip = local - b * ns;
+        const int64_t y0 = b * bh;
+        const int64_t ly = g.ny - y0 < bh ? g.ny - y0 : bh;
         const int64_t xb = strip * WO - (K - 1);  // column of lane 0
         const int64_t a0 = V16 ? (xb - 1) - wrap_mod(xb - 1, 4) : xb - 1;
         const int o = (int)(xb - 1 - a0);         // staged column of xb - 1
@@ -209,30 +221,15 @@ __global__ void __launch_bounds__(NW * 32, MINB)
     if (a.mass_out) block_mass_reduce<S, NW * 32>(acc, a.partials, a.counter, a.mass_out);
 }
 
-template <int Q, int S, int K, int NW, int NS, int MINB, bool V16>
-cudaError_t launch_deep(const StepArgs &a, cudaStream_t st) {
-    constexpr int WO = 34 - 2 * K;
-    if (V16 && (a.nx % 4 != 0 || a.pitch % 4 != 0)) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)NW * NS * S * Q * (V16 ? 40 : 34) * sizeof(float);
-    auto kern = step_deep_kernel<Q, S, K, NW, NS, MINB, V16>;
-    static std::atomic<bool> configured[64] = {};  // per device ordinal (handles on several threads)
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 64 && !configured[dev].load()) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured[dev].store(true);
-    }
-    const int64_t nstrips = (a.nx + WO - 1) / WO;
-    const unsigned full = persistent_blocks(kern, NW * 32, INT64_MAX, smem);
-    const int64_t nwarps = (int64_t)full * NW;
-    // Bands: the count nb whose round-robin deal takes the least time,
-    // rounds x (rows per band + 2K pipeline-fill iterations).
+// Bands: the count nb of bands per grid whose round-robin deal of
+// nb x nstrips units (ny rows each grid) to nwarps warps takes the least
+// time, rounds x (rows per band + 2K pipeline-fill iterations).
+int64_t choose_bands(int K, int64_t nstrips, int64_t ny, int64_t nwarps) {
     int64_t nb = 1, best = INT64_MAX;
     for (int64_t r = 1; r <= 64; ++r) {
         for (int64_t c = r * nwarps / nstrips; c <= r * nwarps / nstrips + 1; ++c) {
-            const int64_t n = c < 1 ? 1 : (c > a.ny ? a.ny : c);
-            const int64_t rows = (a.ny + n - 1) / n;
+            const int64_t n = c < 1 ? 1 : (c > ny ? ny : c);
+            const int64_t rows = (ny + n - 1) / n;
             const int64_t rounds = (n * nstrips + nwarps - 1) / nwarps;
             const int64_t cost = rounds * (rows + 2 * K);
             if (cost < best) {
@@ -241,11 +238,116 @@ cudaError_t launch_deep(const StepArgs &a, cudaStream_t st) {
             }
         }
     }
+    return nb;
+}
+
+template <int Q, int S, int K, int NW, int NS, int MINB, bool V16, bool BATCH>
+struct DeepKernel {
+    static constexpr size_t smem = (size_t)NW * NS * S * Q * (V16 ? 40 : 34) * sizeof(float);
+    // the kernel, its shared-memory attribute set once per device, and its full persistent grid
+    static cudaError_t get(unsigned *full) {
+        auto kern = step_deep_kernel<Q, S, K, NW, NS, MINB, V16, BATCH>;
+        static std::atomic<bool> configured[64] = {};  // per device ordinal (handles on several threads)
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev < 64 && !configured[dev].load()) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            configured[dev].store(true);
+        }
+        *full = persistent_blocks(kern, NW * 32, INT64_MAX, smem);
+        return cudaSuccess;
+    }
+};
+
+template <int Q, int S, int K, int NW, int NS, int MINB, bool V16>
+cudaError_t launch_deep(const StepArgs &a, cudaStream_t st) {
+    constexpr int WO = 34 - 2 * K;
+    if (V16 && (a.nx % 4 != 0 || a.pitch % 4 != 0)) return cudaErrorInvalidValue;
+    using DK = DeepKernel<Q, S, K, NW, NS, MINB, V16, false>;
+    unsigned full = 0;
+    cudaError_t e = DK::get(&full);
+    if (e != cudaSuccess) return e;
+    const int64_t nstrips = (a.nx + WO - 1) / WO;
+    const int64_t nwarps = (int64_t)full * NW;
+    const int64_t nb = choose_bands(K, nstrips, a.ny, nwarps);
     const int64_t band = (a.ny + nb - 1) / nb, nbands = (a.ny + band - 1) / band;
     const int64_t units = nstrips * nbands;
     const unsigned grid = units < nwarps ? (unsigned)((units + NW - 1) / NW) : full;
-    kern<<<grid, NW * 32, smem, st>>>(a, nstrips, nbands, band);
+    step_deep_kernel<Q, S, K, NW, NS, MINB, V16, false>
+        <<<grid, NW * 32, DK::smem, st>>>(a, nstrips, nbands, band, nullptr, 0, 0);
     return cudaGetLastError();
+}
+
+// Batched launch shapes per K: the single-grid choices (K = 4: six warps,
+// two blocks per SM; K = 6, 8: four warps, two blocks per SM).
+template <int Q, int S, int K, bool V16>
+struct BatchShape;
+template <int Q, int S, bool V16>
+struct BatchShape<Q, S, 4, V16> : DeepKernel<Q, S, 4, 6, 4, 2, V16, true> {
+    static constexpr int NW = 6;
+};
+template <int Q, int S, bool V16>
+struct BatchShape<Q, S, 6, V16> : DeepKernel<Q, S, 6, 4, 4, 2, V16, true> {
+    static constexpr int NW = 4;
+};
+template <int Q, int S, bool V16>
+struct BatchShape<Q, S, 8, V16> : DeepKernel<Q, S, 8, 4, 4, 2, V16, true> {
+    static constexpr int NW = 4;
+};
+
+template <int Q, int S, int K, bool V16>
+int64_t plan_batch(DeepItem *items, int n) {
+    using BS = BatchShape<Q, S, K, V16>;
+    constexpr int WO = 34 - 2 * K;
+    unsigned full = 0;
+    if (BS::get(&full) != cudaSuccess) return -1;
+    int64_t strips = 0, ny = 1;
+    for (int i = 0; i < n; ++i) {
+        items[i].nstrips = (items[i].a.nx + WO - 1) / WO;
+        strips += items[i].nstrips;
+        ny = items[i].a.ny > ny ? items[i].a.ny : ny;
+    }
+    const int64_t nb = choose_bands(K, strips, ny, (int64_t)full * BS::NW);
+    int64_t units = 0;
+    for (int i = 0; i < n; ++i) {
+        const int64_t g = items[i].a.ny;
+        items[i].band = (g + nb - 1) / nb;
+        items[i].unit_begin = units;
+        units += items[i].nstrips * ((g + items[i].band - 1) / items[i].band);
+    }
+    return units;
+}
+
+template <int Q, int S, int K, bool V16>
+cudaError_t launch_batch(const DeepItem *items, int n, int64_t total_units, cudaStream_t st) {
+    using BS = BatchShape<Q, S, K, V16>;
+    unsigned full = 0;
+    cudaError_t e = BS::get(&full);
+    if (e != cudaSuccess) return e;
+    const int64_t nwarps = (int64_t)full * BS::NW;
+    const unsigned grid = total_units < nwarps ? (unsigned)((total_units + BS::NW - 1) / BS::NW) : full;
+    step_deep_kernel<Q, S, K, BS::NW, 4, 2, V16, true>
+        <<<grid, BS::NW * 32, BS::smem, st>>>(StepArgs{}, 0, 0, 0, items, n, total_units);
+    return cudaGetLastError();
+}
+
+template <int K, bool V16>
+int64_t plan_qs(int Q, int S, DeepItem *items, int n) {
+    if (Q == 9 && S == 1) return plan_batch<9, 1, K, V16>(items, n);
+    if (Q == 9 && S == 2) return plan_batch<9, 2, K, V16>(items, n);
+    if (Q == 5 && S == 1) return plan_batch<5, 1, K, V16>(items, n);
+    if (Q == 5 && S == 2) return plan_batch<5, 2, K, V16>(items, n);
+    return -1;
+}
+
+template <int K, bool V16>
+cudaError_t launch_qs(int Q, int S, const DeepItem *items, int n, int64_t total_units, cudaStream_t st) {
+    if (Q == 9 && S == 1) return launch_batch<9, 1, K, V16>(items, n, total_units, st);
+    if (Q == 9 && S == 2) return launch_batch<9, 2, K, V16>(items, n, total_units, st);
+    if (Q == 5 && S == 1) return launch_batch<5, 1, K, V16>(items, n, total_units, st);
+    if (Q == 5 && S == 2) return launch_batch<5, 2, K, V16>(items, n, total_units, st);
+    return cudaErrorInvalidValue;
 }
 
 template <int K, int NW, int NS, int MINB, bool V16 = false>
@@ -258,6 +360,28 @@ cudaError_t dispatch_deep(int Q, int S, const StepArgs &a, cudaStream_t st) {
 }
 
 }  // namespace
+
+int64_t batch_deep_plan(int K, int Q, int S, bool v16, DeepItem *items, int n) {
+    switch (K) {
+        case 4: return v16 ? plan_qs<4, true>(Q, S, items, n) : plan_qs<4, false>(Q, S, items, n);
+        case 6: return v16 ? plan_qs<6, true>(Q, S, items, n) : plan_qs<6, false>(Q, S, items, n);
+        case 8: return v16 ? plan_qs<8, true>(Q, S, items, n) : plan_qs<8, false>(Q, S, items, n);
+        default: return -1;
+    }
+}
+
+cudaError_t launch_batch_deep(int K, int Q, int S, bool v16, const DeepItem *items, int n, int64_t total_units,
+                              cudaStream_t st) {
+    switch (K) {
+        case 4: return v16 ? launch_qs<4, true>(Q, S, items, n, total_units, st)
+                           : launch_qs<4, false>(Q, S, items, n, total_units, st);
+        case 6: return v16 ? launch_qs<6, true>(Q, S, items, n, total_units, st)
+                           : launch_qs<6, false>(Q, S, items, n, total_units, st);
+        case 8: return v16 ? launch_qs<8, true>(Q, S, items, n, total_units, st)
+                           : launch_qs<8, false>(Q, S, items, n, total_units, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 // K time steps per launch (state t -> t + K).  v: depth and launch shape.
 cudaError_t launch_step_f32_deep(int v, int Q, int S, const StepArgs &a, cudaStream_t st) {

@@ -40,10 +40,13 @@ def _single(c, rho0, steps):
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_bf16dev", "fp32_fp16dev"])
 @pytest.mark.parametrize("graph", [0, 8])
 def test_batch_instances_equal_single_handles(precision, graph):
+    """One step per launch (the FP32 default, K steps per launch, is tested
+    below)."""
     cfgs = _configs(precision)
     steps = 57
     with B.Batch(cfgs) as b:
         b.set_graph(graph)
+        b.set_steps_per_launch(1)
         for j, c in enumerate(cfgs):
             b.init(j, _rho0(c, j))
         b.step(20).step(steps - 20)
@@ -137,8 +140,8 @@ def test_batch_with_inplace_instances_equals_single_handles():
 @pytest.mark.parametrize("graph", [0, 8, 6])
 @pytest.mark.parametrize("steps", [1, 2, 7, 40])
 def test_batch_two_steps_per_launch_equals_single_handles(lat, graph, steps):
-    """Instances with nx a multiple of 256 run the two-step kernel over the
-    whole list (the default for such batches); each instance gives the bits
+    """Instances with nx a multiple of 256 can run the two-step kernel over
+    the whole list; each instance gives the bits
     of a single handle, whatever the graph length (6: an odd number of
     two-step launches per graph) and step count (odd counts end with single
     steps)."""
@@ -147,6 +150,7 @@ def test_batch_two_steps_per_launch_equals_single_handles(lat, graph, steps):
                  F=0.03 + 0.004 * j, k=0.06 - 0.002 * j, precision="fp32") for j, (nx, ny) in enumerate(shapes)]
     with B.Batch(cfgs) as b:
         b.set_graph(graph)
+        b.set_steps_per_launch(2)
         for j, c in enumerate(cfgs):
             b.init(j, _rho0(c, j))
         b.step(steps).step(steps)
@@ -159,9 +163,48 @@ def test_batch_two_steps_per_launch_equals_single_handles(lat, graph, steps):
         assert launches < 2 * steps  # two steps per launch were used
 
 
+@pytest.mark.parametrize("lat", ["D2Q9", "D2Q5"])
+@pytest.mark.parametrize("K", [4, 6, 8])
+@pytest.mark.parametrize("staging", ["16-byte", "4-byte"])
+@pytest.mark.parametrize("graph", [0, 8, 12])
+def test_batch_k_steps_per_launch_equals_single_handles(lat, K, staging, graph):
+    """K = 4, 6, 8 steps per launch run the depth-K kernel over the (band,
+    strip) units of all instances (ragged strips, bands of a few rows); each
+    instance gives the bits of a single handle.  All nx multiples of 4: the
+    16-byte staging; otherwise 4-byte copies.  Graph 12: an odd number of
+    K-step launches per graph for K = 4 and 8."""
+    shapes = [(64, 48), (100, 37), (36, 70), (8, 3), (256, 16)]
+    if staging == "4-byte":
+        shapes += [(70, 9), (33, 20)]
+    cfgs = [dict(lattice=lat, nspecies=2, nx=nx, ny=ny, tau=[0.8 + 0.05 * j, 0.65], reaction="gray_scott",
+                 F=0.03 + 0.004 * j, k=0.06 - 0.002 * j, precision="fp32") for j, (nx, ny) in enumerate(shapes)]
+    steps = 21
+    with B.Batch(cfgs) as b:
+        b.set_graph(graph)
+        b.set_steps_per_launch(K)
+        for j, c in enumerate(cfgs):
+            b.init(j, _rho0(c, j))
+        b.step(steps).step(steps)
+        _, launches = B.lb_rd_batch_get_time(b.b)
+        for j, c in enumerate(cfgs):
+            rho, _ = b.moments(j)
+            ref_rho, _ = _single(c, _rho0(c, j), 2 * steps)
+            np.testing.assert_array_equal(rho, ref_rho, err_msg=f"instance {j}")
+    # one init launch per instance; per call 20 // K launches of K steps, then 20 % K + 1 single steps
+    assert launches == len(cfgs) + 2 * (20 // K + 20 % K + 1)
+
+
 def test_batch_steps_per_launch_switch():
     cfgs = _configs("fp32")  # includes nx not a multiple of 256
     with B.Batch(cfgs) as b:
         with pytest.raises(B.LbRdError):
             b.set_steps_per_launch(2)
         b.set_steps_per_launch(1)
+        b.set_steps_per_launch(6)  # the depth-K kernel takes any nx
+        for k in (0, 3, 5, 16):
+            with pytest.raises(B.LbRdError):
+                b.set_steps_per_launch(k)
+    ip = [dict(c, inplace=True) for c in _configs("fp32")[:2]]
+    with B.Batch(ip) as b:
+        with pytest.raises(B.LbRdError):
+            b.set_steps_per_launch(4)  # in-place instances: one state copy
