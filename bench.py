@@ -206,7 +206,7 @@ def batch_mode(args):
         for i in range(ninst):
             b.init(i, rho0s[i])
         # 1, 2 (every nx a multiple of 256), 4, 6, 8 time steps per launch; the fastest is the result
-        for k in (1, 2, 4, 6, 8):
+        for k in [int(x) for x in args.batch_k.split(",")]:
             try:
                 b.set_steps_per_launch(k)
             except B.LbRdError:
@@ -522,6 +522,8 @@ def main():
     ap.add_argument("--inplace", action="store_true", help="one state copy (AA streaming)")
     ap.add_argument("--variant", default="", help="force a launch variant by name (after the autotune sweep)")
     ap.add_argument("--instances", type=int, default=0)
+    ap.add_argument("--batch-k", default="1,2,4,6,8",
+                    help="batch mode: time steps per launch to time (comma-separated); the fastest is the result")
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--steps-scale", type=float, default=0.05)
     ap.add_argument("--load", type=float, default=0.8)
