@@ -6,8 +6,10 @@
 //      their device memory fits the budget (stream-ordered allocation from
 //      the device's memory pool, H2D copy of rho0, the init kernel),
 //   2. advances every resident request by one tick of up to steps_per_tick
-//      steps (never past the earliest finishing request), each step one
-//      launch of the batched kernel over all resident requests, the last
+//      steps (never past the earliest finishing request): FP32 requests with
+//      two state copies by K-step launches of the depth-K kernel over all
+//      resident requests (K = 6 for D2Q9, 4 for D2Q5) while more than K steps
+//      of the tick remain, the rest one batched launch per step, the last
 //      step of the tick also writing their densities,
 //   3. copies the results of finished requests to host memory, releases
 //      their device memory and wakes pollers.
@@ -88,6 +90,9 @@ struct lb_rd_server {
     lbrd::BatchItem *d_items = nullptr;
     lbrd::BatchItem *h_items = nullptr;  // pinned
     size_t items_cap = 0;
+    lbrd::DeepItem *d_deep = nullptr;  // K-step descriptors, two parities
+    lbrd::DeepItem *h_deep = nullptr;  // pinned
+    size_t deep_cap = 0;
     double *partials = nullptr;
     unsigned int *counter = nullptr;
     double *d_mass = nullptr;
@@ -198,6 +203,20 @@ int ensure_items(lb_rd_server *s, size_t n) {
     return LB_RD_OK;
 }
 
+int ensure_deep(lb_rd_server *s, size_t n) {
+    if (s->deep_cap >= 2 * n) return LB_RD_OK;
+    cudaStreamSynchronize(s->stream);
+    cudaFree(s->d_deep);
+    cudaFreeHost(s->h_deep);
+    s->d_deep = nullptr;
+    s->h_deep = nullptr;
+    const size_t cap = 2 * std::max<size_t>(n, 64);
+    if (cudaMalloc(&s->d_deep, cap * sizeof(lbrd::DeepItem)) != cudaSuccess) return LB_RD_ENOMEM;
+    if (cudaMallocHost(&s->h_deep, cap * sizeof(lbrd::DeepItem)) != cudaSuccess) return LB_RD_ENOMEM;
+    s->deep_cap = cap;
+    return LB_RD_OK;
+}
+
 void run_tick(lb_rd_server *s) {
     std::vector<Request *> &act = s->active;
     const size_t n = act.size();
@@ -211,9 +230,48 @@ void run_tick(lb_rd_server *s) {
         act.clear();
         return;
     }
-    // descriptor sets: [0] even steps, [1] odd steps, [2] the tick's last step (writes rho)
-    int64_t total = 0;
+    // K-step launches: FP32 requests with two state copies, while more than K
+    // steps of the tick remain (the last step is a single step writing rho)
     bool any_inplace = false;
+    for (Request *r : act) any_inplace = any_inplace || r->cfg.streaming == LB_RD_STREAM_INPLACE;
+    const int K = s->Q == 9 ? 6 : 4;
+    int64_t n_multi = (s->mode == 0 && !any_inplace) ? (tick - 1) / K : 0;
+    bool v16 = true;
+    for (Request *r : act) v16 = v16 && r->cfg.nx % 4 == 0 && r->pitch % 4 == 0;
+    int64_t deep_units = 0;
+    if (n_multi > 0 && ensure_deep(s, n) == LB_RD_OK) {
+        for (size_t i = 0; i < n; ++i) {  // parity 0 relative to each request's current copy
+            Request *r = act[i];
+            const lb_rd_config &c = r->cfg;
+            lbrd::DeepItem d{};
+            d.a.nx = c.nx;
+            d.a.ny = c.ny;
+            d.a.pitch = r->pitch;
+            d.a.plane = c.ny * r->pitch;
+            for (int k = 0; k < 2; ++k) d.a.omega[k] = k < c.nspecies ? 1.0 / c.tau[k] : 0.0;
+            d.a.rkind = c.reaction.kind;
+            d.a.kappa = c.reaction.kappa;
+            d.a.F = c.reaction.F;
+            d.a.k = c.reaction.k;
+            d.a.src = r->buf[r->cur];
+            d.a.dst = r->buf[r->cur ^ 1];
+            s->h_deep[i] = d;
+        }
+        deep_units = lbrd::batch_deep_plan(K, s->Q, s->cfg.nspecies, v16, s->h_deep, (int)n);
+        for (size_t i = 0; i < n; ++i) {  // parity 1: the copies swapped
+            s->h_deep[n + i] = s->h_deep[i];
+            s->h_deep[n + i].a.src = act[i]->buf[act[i]->cur ^ 1];
+            s->h_deep[n + i].a.dst = act[i]->buf[act[i]->cur];
+        }
+        if (deep_units > 0)
+            cudaMemcpyAsync(s->d_deep, s->h_deep, 2 * n * sizeof(lbrd::DeepItem), cudaMemcpyHostToDevice, s->stream);
+    }
+    if (deep_units <= 0) n_multi = 0;
+    // launches of the tick: n_multi K-step launches, then single steps; each
+    // launch swaps the two copies once
+    const int64_t L = n_multi + (tick - K * n_multi);
+    // descriptor sets: [0] even launches, [1] odd launches, [2] the tick's last launch (writes rho)
+    int64_t total = 0;
     for (size_t i = 0; i < n; ++i) {
         Request *r = act[i];
         const lb_rd_config &c = r->cfg;
@@ -231,12 +289,11 @@ void run_tick(lb_rd_server *s) {
         it.tile_begin = total;
         total += lbrd::batch_tiles(c.nx, c.ny);
         for (int set = 0; set < 3; ++set) {
-            const int par = set < 2 ? (r->cur + set) & 1 : (int)((r->cur + tick - 1) & 1);
+            const int par = set < 2 ? (r->cur + set) & 1 : (int)((r->cur + L - 1) & 1);
             lbrd::BatchItem v = it;
             if (c.streaming == LB_RD_STREAM_INPLACE) {
                 v.a.src = v.a.dst = r->buf[0];
                 v.aa = (c.nx % 4 == 0 ? 1 : 3) + par;
-                any_inplace = true;
             } else {
                 v.a.src = r->buf[par];
                 v.a.dst = r->buf[par ^ 1];
@@ -248,9 +305,13 @@ void run_tick(lb_rd_server *s) {
     cudaMemcpyAsync(s->d_items, s->h_items, 3 * n * sizeof(lbrd::BatchItem), cudaMemcpyHostToDevice, s->stream);
     cudaError_t e = cudaSuccess;
     const int S = s->cfg.nspecies;
-    for (int64_t k = 0; k < tick && !e; ++k) {
-        const lbrd::BatchItem *items = s->d_items + (k == tick - 1 ? 2 : (k & 1)) * n;
-        e = lbrd::launch_batch_step(any_inplace ? 4 : s->mode, s->Q, S, items, (int)n, total, s->stream);
+    for (int64_t l = 0; l < L && !e; ++l) {
+        if (l < n_multi) {
+            e = lbrd::launch_batch_deep(K, s->Q, S, v16, s->d_deep + (l & 1) * n, (int)n, deep_units, s->stream);
+        } else {
+            const lbrd::BatchItem *items = s->d_items + (l == L - 1 ? 2 : (l & 1)) * n;
+            e = lbrd::launch_batch_step(any_inplace ? 4 : s->mode, s->Q, S, items, (int)n, total, s->stream);
+        }
         s->launches++;
     }
     if (!e) e = cudaStreamSynchronize(s->stream);  // the pinned descriptors are reused next tick
@@ -262,7 +323,7 @@ void run_tick(lb_rd_server *s) {
             finish(s, r, LB_RD_ECUDA);
             continue;
         }
-        r->cur = (int)((r->cur + tick) & 1);
+        r->cur = (int)((r->cur + L) & 1);
         r->remaining -= tick;
         if (r->remaining > 0) {
             keep.push_back(r);
@@ -382,6 +443,8 @@ int lb_rd_server_destroy(lb_rd_server *s) {
     for (auto &kv : s->all) delete kv.second;
     cudaFree(s->d_items);
     cudaFreeHost(s->h_items);
+    cudaFree(s->d_deep);
+    cudaFreeHost(s->h_deep);
     cudaFree(s->partials);
     cudaFree(s->counter);
     cudaFree(s->d_mass);
