@@ -88,6 +88,10 @@ const F32Variant kF32Variants[] = {
     {"deep4v_96_minb4", 96, 4, 4, 4, 4, 4},
     {"deep6v_128_minb2", 128, 6, 2, 4, 6, 4},
     {"deep8v_192_minb1", 192, 8, 1, 4, 8, 4},
+    {"deep5v_128_minb2", 128, 5, 2, 4, 5, 4},
+    {"deep5v_192_minb2", 192, 5, 2, 4, 5, 4},
+    {"deep6v_192_minb2", 192, 6, 2, 4, 6, 4},
+    {"deep6v_128_minb3_s5", 128, 6, 3, 4, 6, 4},
 };
 const int kF32VariantCount = sizeof(kF32Variants) / sizeof(kF32Variants[0]);
 

@@ -402,6 +402,10 @@ cudaError_t launch_step_f32_deep(int v, int Q, int S, const StepArgs &a, cudaStr
         case 13: return dispatch_deep<4, 3, 4, 4, true>(Q, S, a, st);
         case 14: return dispatch_deep<6, 4, 4, 2, true>(Q, S, a, st);
         case 15: return dispatch_deep<8, 6, 4, 1, true>(Q, S, a, st);
+        case 16: return dispatch_deep<5, 4, 4, 2, true>(Q, S, a, st);
+        case 17: return dispatch_deep<5, 6, 4, 2, true>(Q, S, a, st);
+        case 18: return dispatch_deep<6, 6, 4, 2, true>(Q, S, a, st);
+        case 19: return dispatch_deep<6, 4, 5, 3, true>(Q, S, a, st);
         default: return cudaErrorInvalidValue;
     }
 }
