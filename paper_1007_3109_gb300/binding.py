@@ -281,8 +281,9 @@ def lb_rd_variant_name(precision, variant: int) -> str:
 
 def variant_steps(name: str) -> int:
     """Time steps per launch of an FP32 launch variant, from its name: tb2*_
-    variants two, deep<K>_ and deep<K>v_ variants K, the others one."""
-    m = re.match(r"deep(\d+)v?_", name)
+    variants two, deep<K>_, deep<K>v_ and deep<K>vp_ variants K, the others
+    one."""
+    m = re.match(r"deep(\d+)v?p?_", name)
     if m:
         return int(m.group(1))
     return 2 if name.startswith("tb2") else 1

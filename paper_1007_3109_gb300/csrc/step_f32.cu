@@ -92,6 +92,11 @@ const F32Variant kF32Variants[] = {
     {"deep5v_192_minb2", 192, 5, 2, 4, 5, 4},
     {"deep6v_192_minb2", 192, 6, 2, 4, 6, 4},
     {"deep6v_128_minb3_s5", 128, 6, 3, 4, 6, 4},
+    // the same, the pulls from earlier rows at the start of an iteration
+    {"deep8vp_128_minb2", 128, 8, 2, 4, 8, 4},
+    {"deep6vp_128_minb3_s5", 128, 6, 3, 4, 6, 4},
+    {"deep6vp_128_minb2", 128, 6, 2, 4, 6, 4},
+    {"deep5vp_192_minb2", 192, 5, 2, 4, 5, 4},
 };
 const int kF32VariantCount = sizeof(kF32Variants) / sizeof(kF32Variants[0]);
 

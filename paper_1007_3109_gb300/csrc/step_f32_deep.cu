@@ -19,7 +19,10 @@
 // side per level), so a warp writes 34 - 2K columns, and from iteration 2K of
 // its band on (the first 2K iterations fill the pipeline).  Each level is the
 // fused step of the one-step kernels (tb::collide_site): K levels give the
-// bits of K single steps.
+// bits of K single steps.  PP variants take the pulls of levels 2 .. K from
+// the rows of earlier iterations (e_iy >= 0) at the start of an iteration,
+// so the carried values die before the new rows are produced (fewer register
+// moves; which form is faster depends on the depth and the lattice).
 //
 // Work units are (band, strip) pairs, strips fastest, dealt to the warps
 // round-robin: consecutive warps walk adjacent strips of one band at about
@@ -71,7 +74,7 @@ __host__ __device__ __forceinline__ int64_t wrap_mod(int64_t a, int64_t n) {
 // lanes 0 and 1 also columns xb + 31, xb + 32.
 // BATCH: the units of a list of grids (DeepItem, sorted by unit_begin; each
 // with its own strips and band height) instead of one grid.
-template <int Q, int S, int K, int NW, int NS, int MINB, bool V16, bool BATCH>
+template <int Q, int S, int K, int NW, int NS, int MINB, bool V16, bool BATCH, bool PP>
 __global__ void __launch_bounds__(NW * 32, MINB)
     step_deep_kernel(StepArgs a, int64_t nstrips, int64_t nbands, int64_t band, const DeepItem *__restrict__ items,
                      int nitems, int64_t total_units) {
@@ -167,37 +170,75 @@ __global__ void __launch_bounds__(NW * 32, MINB)
             const float *rows0[3] = {ring + s2 * kRow + o + lane + 1, ring + s1 * kRow + o + lane + 1,
                                      ring + sl * kRow + o + lane + 1};
             float f[S][Q], rho[S];
+            float hp[KC][S][Q];
+            if constexpr (PP) {
+                // Pulls of levels 2 .. K from the rows of earlier iterations
+                // (e_iy >= 0) first: the carried values then die before the new
+                // rows are computed, so each level's new e_iy >= 0 components
+                // can be produced in the carried registers themselves.
+#pragma unroll
+                for (int m = 1; m < K; ++m)
+#pragma unroll
+                    for (int s = 0; s < S; ++s)
+#pragma unroll
+                        for (int i = 0; i < Q; ++i)
+                            if (L::ey(i) >= 0) {
+                                const float v = L::ey(i) == 0 ? E0[m - 1][s][i] : P2[m - 1][s][i];
+                                hp[m - 1][s][i] = L::ex(i) > 0   ? __shfl_up_sync(kFullMask, v, 1)
+                                                  : L::ex(i) < 0 ? __shfl_down_sync(kFullMask, v, 1)
+                                                                 : v;
+                                if (L::ey(i) > 0) P2[m - 1][s][i] = P1[m - 1][s][i];
+                            }
+            }
 #pragma unroll
             for (int s = 0; s < S; ++s)
 #pragma unroll
                 for (int i = 0; i < Q; ++i) f[s][i] = rows0[1 - L::ey(i)][(s * Q + i) * CW - L::ex(i)];
             collide_site<Q, S>(g, f, rho);
+            if constexpr (PP) {
 #pragma unroll
-            for (int m = 1; m < K; ++m) {  // level m + 1 from level m (carried index m - 1)
-                float h[S][Q];
+                for (int m = 1; m < K; ++m) {  // level m + 1 from level m (carried index m - 1)
 #pragma unroll
-                for (int s = 0; s < S; ++s)
+                    for (int s = 0; s < S; ++s)
 #pragma unroll
-                    for (int i = 0; i < Q; ++i) {
-                        const float v =
-                            L::ey(i) < 0 ? f[s][i] : (L::ey(i) == 0 ? E0[m - 1][s][i] : P2[m - 1][s][i]);
-                        h[s][i] = L::ex(i) > 0   ? __shfl_up_sync(kFullMask, v, 1)
-                                  : L::ex(i) < 0 ? __shfl_down_sync(kFullMask, v, 1)
-                                                 : v;
-                    }
-#pragma unroll
-                for (int s = 0; s < S; ++s)
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) {
-                        if (L::ey(i) > 0) {
-                            P2[m - 1][s][i] = P1[m - 1][s][i];
-                            P1[m - 1][s][i] = f[s][i];
-                        } else if (L::ey(i) == 0) {
-                            E0[m - 1][s][i] = f[s][i];
+                        for (int i = 0; i < Q; ++i) {
+                            if (L::ey(i) > 0) P1[m - 1][s][i] = f[s][i];
+                            else if (L::ey(i) == 0) E0[m - 1][s][i] = f[s][i];
+                            f[s][i] = L::ey(i) >= 0 ? hp[m - 1][s][i]
+                                      : L::ex(i) > 0 ? __shfl_up_sync(kFullMask, f[s][i], 1)
+                                      : L::ex(i) < 0 ? __shfl_down_sync(kFullMask, f[s][i], 1)
+                                                     : f[s][i];
                         }
-                        f[s][i] = h[s][i];
-                    }
-                collide_site<Q, S>(g, f, rho);
+                    collide_site<Q, S>(g, f, rho);
+                }
+            } else {
+#pragma unroll
+                for (int m = 1; m < K; ++m) {  // level m + 1 from level m (carried index m - 1)
+                    float h[S][Q];
+#pragma unroll
+                    for (int s = 0; s < S; ++s)
+#pragma unroll
+                        for (int i = 0; i < Q; ++i) {
+                            const float v =
+                                L::ey(i) < 0 ? f[s][i] : (L::ey(i) == 0 ? E0[m - 1][s][i] : P2[m - 1][s][i]);
+                            h[s][i] = L::ex(i) > 0   ? __shfl_up_sync(kFullMask, v, 1)
+                                      : L::ex(i) < 0 ? __shfl_down_sync(kFullMask, v, 1)
+                                                     : v;
+                        }
+#pragma unroll
+                    for (int s = 0; s < S; ++s)
+#pragma unroll
+                        for (int i = 0; i < Q; ++i) {
+                            if (L::ey(i) > 0) {
+                                P2[m - 1][s][i] = P1[m - 1][s][i];
+                                P1[m - 1][s][i] = f[s][i];
+                            } else if (L::ey(i) == 0) {
+                                E0[m - 1][s][i] = f[s][i];
+                            }
+                            f[s][i] = h[s][i];
+                        }
+                    collide_site<Q, S>(g, f, rho);
+                }
             }
             if (j >= 2 * K) {  // level K of row y0 + j - 2K
                 const int64_t x = xb + lane;
@@ -241,12 +282,12 @@ int64_t choose_bands(int K, int64_t nstrips, int64_t ny, int64_t nwarps) {
     return nb;
 }
 
-template <int Q, int S, int K, int NW, int NS, int MINB, bool V16, bool BATCH>
+template <int Q, int S, int K, int NW, int NS, int MINB, bool V16, bool BATCH, bool PP = false>
 struct DeepKernel {
     static constexpr size_t smem = (size_t)NW * NS * S * Q * (V16 ? 40 : 34) * sizeof(float);
     // the kernel, its shared-memory attribute set once per device, and its full persistent grid
     static cudaError_t get(unsigned *full) {
-        auto kern = step_deep_kernel<Q, S, K, NW, NS, MINB, V16, BATCH>;
+        auto kern = step_deep_kernel<Q, S, K, NW, NS, MINB, V16, BATCH, PP>;
         static std::atomic<bool> configured[64] = {};  // per device ordinal (handles on several threads)
         int dev = 0;
         cudaGetDevice(&dev);
@@ -260,11 +301,11 @@ struct DeepKernel {
     }
 };
 
-template <int Q, int S, int K, int NW, int NS, int MINB, bool V16>
+template <int Q, int S, int K, int NW, int NS, int MINB, bool V16, bool PP>
 cudaError_t launch_deep(const StepArgs &a, cudaStream_t st) {
     constexpr int WO = 34 - 2 * K;
     if (V16 && (a.nx % 4 != 0 || a.pitch % 4 != 0)) return cudaErrorInvalidValue;
-    using DK = DeepKernel<Q, S, K, NW, NS, MINB, V16, false>;
+    using DK = DeepKernel<Q, S, K, NW, NS, MINB, V16, false, PP>;
     unsigned full = 0;
     cudaError_t e = DK::get(&full);
     if (e != cudaSuccess) return e;
@@ -274,26 +315,30 @@ cudaError_t launch_deep(const StepArgs &a, cudaStream_t st) {
     const int64_t band = (a.ny + nb - 1) / nb, nbands = (a.ny + band - 1) / band;
     const int64_t units = nstrips * nbands;
     const unsigned grid = units < nwarps ? (unsigned)((units + NW - 1) / NW) : full;
-    step_deep_kernel<Q, S, K, NW, NS, MINB, V16, false>
+    step_deep_kernel<Q, S, K, NW, NS, MINB, V16, false, PP>
         <<<grid, NW * 32, DK::smem, st>>>(a, nstrips, nbands, band, nullptr, 0, 0);
     return cudaGetLastError();
 }
 
 // Batched launch shapes per K: the single-grid choices (K = 4: six warps,
-// two blocks per SM; K = 6, 8: four warps, two blocks per SM).
+// two blocks per SM; K = 6, 8: four warps, two blocks per SM; K = 8 with the
+// pulls from earlier rows first).
 template <int Q, int S, int K, bool V16>
 struct BatchShape;
 template <int Q, int S, bool V16>
 struct BatchShape<Q, S, 4, V16> : DeepKernel<Q, S, 4, 6, 4, 2, V16, true> {
     static constexpr int NW = 6;
+    static constexpr bool PP = false;
 };
 template <int Q, int S, bool V16>
 struct BatchShape<Q, S, 6, V16> : DeepKernel<Q, S, 6, 4, 4, 2, V16, true> {
     static constexpr int NW = 4;
+    static constexpr bool PP = false;
 };
 template <int Q, int S, bool V16>
-struct BatchShape<Q, S, 8, V16> : DeepKernel<Q, S, 8, 4, 4, 2, V16, true> {
+struct BatchShape<Q, S, 8, V16> : DeepKernel<Q, S, 8, 4, 4, 2, V16, true, true> {
     static constexpr int NW = 4;
+    static constexpr bool PP = true;
 };
 
 template <int Q, int S, int K, bool V16>
@@ -327,7 +372,7 @@ cudaError_t launch_batch(const DeepItem *items, int n, int64_t total_units, cuda
     if (e != cudaSuccess) return e;
     const int64_t nwarps = (int64_t)full * BS::NW;
     const unsigned grid = total_units < nwarps ? (unsigned)((total_units + BS::NW - 1) / BS::NW) : full;
-    step_deep_kernel<Q, S, K, BS::NW, 4, 2, V16, true>
+    step_deep_kernel<Q, S, K, BS::NW, 4, 2, V16, true, BS::PP>
         <<<grid, BS::NW * 32, BS::smem, st>>>(StepArgs{}, 0, 0, 0, items, n, total_units);
     return cudaGetLastError();
 }
@@ -350,12 +395,12 @@ cudaError_t launch_qs(int Q, int S, const DeepItem *items, int n, int64_t total_
     return cudaErrorInvalidValue;
 }
 
-template <int K, int NW, int NS, int MINB, bool V16 = false>
+template <int K, int NW, int NS, int MINB, bool V16 = false, bool PP = false>
 cudaError_t dispatch_deep(int Q, int S, const StepArgs &a, cudaStream_t st) {
-    if (Q == 9 && S == 1) return launch_deep<9, 1, K, NW, NS, MINB, V16>(a, st);
-    if (Q == 9 && S == 2) return launch_deep<9, 2, K, NW, NS, MINB, V16>(a, st);
-    if (Q == 5 && S == 1) return launch_deep<5, 1, K, NW, NS, MINB, V16>(a, st);
-    if (Q == 5 && S == 2) return launch_deep<5, 2, K, NW, NS, MINB, V16>(a, st);
+    if (Q == 9 && S == 1) return launch_deep<9, 1, K, NW, NS, MINB, V16, PP>(a, st);
+    if (Q == 9 && S == 2) return launch_deep<9, 2, K, NW, NS, MINB, V16, PP>(a, st);
+    if (Q == 5 && S == 1) return launch_deep<5, 1, K, NW, NS, MINB, V16, PP>(a, st);
+    if (Q == 5 && S == 2) return launch_deep<5, 2, K, NW, NS, MINB, V16, PP>(a, st);
     return cudaErrorInvalidValue;
 }
 
@@ -406,6 +451,11 @@ cudaError_t launch_step_f32_deep(int v, int Q, int S, const StepArgs &a, cudaStr
         case 17: return dispatch_deep<5, 6, 4, 2, true>(Q, S, a, st);
         case 18: return dispatch_deep<6, 6, 4, 2, true>(Q, S, a, st);
         case 19: return dispatch_deep<6, 4, 5, 3, true>(Q, S, a, st);
+        // the pulls from earlier rows first (PP)
+        case 20: return dispatch_deep<8, 4, 4, 2, true, true>(Q, S, a, st);
+        case 21: return dispatch_deep<6, 4, 5, 3, true, true>(Q, S, a, st);
+        case 22: return dispatch_deep<6, 4, 4, 2, true, true>(Q, S, a, st);
+        case 23: return dispatch_deep<5, 6, 4, 2, true, true>(Q, S, a, st);
         default: return cudaErrorInvalidValue;
     }
 }
