@@ -688,7 +688,12 @@ def main():
                      "traffic": traffic, "kernel": f"step_{args.precision}:{variant_name}",
                      "steps_per_launch": steps_per_launch, "bytes_per_site_per_launch": bps,
                      "effective_per_step_GBs": effective, "effective_frac": effective / peak,
-                     "peak_kind": peak_kind, "avg_launch_ms": avg_launch_s * 1e3, "single_step": single},
+                     "peak_kind": peak_kind, "avg_launch_ms": avg_launch_s * 1e3, "single_step": single,
+                     # a K-step launch moves the state once for K steps: it is bound by instruction
+                     # issue (ncu: issue active well above DRAM throughput), not by HBM
+                     "limiter": ("instruction issue (state moved once per launch of %.0f steps; ncu summary in "
+                                 "profiles/step_f32_deep_gs4096_ncu_full.md)" % steps_per_launch
+                                 if steps_per_launch > 1.5 else "hbm bandwidth")},
         "depth_sweep": depth or None,
         "e2e": {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "lb_steps": e2e_steps, "path": "lb_rd_init(host) + lb_rd_step + lb_rd_moments(host)"},
