@@ -513,7 +513,8 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="grid side override (same recipe, smaller grid)")
     ap.add_argument("--ref-window", type=int, default=512)
     ap.add_argument("--cpu-window", type=int, default=1024)
-    ap.add_argument("--cpu-steps", type=int, default=100)
+    ap.add_argument("--cpu-steps", type=int, default=2000,
+                    help="FP64 oracle steps of the CPU baseline sample (about 10-30 s on the host cores)")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--tune-iters", type=int, default=10)
