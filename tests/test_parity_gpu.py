@@ -32,7 +32,7 @@ def tol(precision, reac, steps):
 
 def rel_err(a, b):
     """max |a - b| / max |b| per species (denominator floored at 1e-4 so that
-    a field that has decayed to ~0 is judged on absolute error)."""
+    a field that has decayed to ~0 is compared on absolute error)."""
     a, b = np.asarray(a), np.asarray(b)
     ax = tuple(range(1, a.ndim))
     return np.max(np.abs(a - b), axis=ax) / np.maximum(np.max(np.abs(b), axis=ax), 1e-4)

@@ -27,7 +27,7 @@ BOUND_1000 = {"fp32_bf16dev": 5e-3, "fp32_fp16dev": 1e-3}
 def rel_err(a, b):
     """max |a - b| / max |b| per species, the denominator floored at 1e-4: fp16
     deviations resolve ~6e-8 absolute (subnormals), so a field that has decayed
-    to ~1e-8 is judged on absolute error."""
+    to ~1e-8 is compared on absolute error."""
     return np.max(np.abs(a - b), axis=(1, 2)) / np.maximum(np.max(np.abs(b), axis=(1, 2)), 1e-4)
 
 
