@@ -214,19 +214,30 @@ def _window(field, y0, x0, h, w):
 
 
 @pytest.mark.parametrize("lat", ["D2Q9", "D2Q5"])
-def test_gs_8192_sampled_windows(lat):
+@pytest.mark.parametrize("variant", ["autotuned", "deep6v_128_minb2", "deep5v_192_minb2", "deep6vp_128_minb3_s5"])
+def test_gs_8192_sampled_windows(lat, variant):
     """gs_8192 workload at full size, in the launch configuration the
-    benchmark times (FP32, 8192^2, two species): after T steps a site depends
-    only on sites within T of it, so the oracle run on a window with a margin
-    of T + 1 (its own periodic wrap never reaches the inner window) gives the
-    exact reference there.  Windows include the periodic corner."""
+    benchmark times (FP32, 8192^2, two species; the autotuner's choice, as in
+    the benchmark, and the depth-K variants it picks between): after T steps
+    a site depends only on sites within T of it, so the oracle run on a window
+    with a margin of T + 1 (its own periodic wrap never reaches the inner
+    window) gives the exact reference there.  T = 13: two K-step launches for
+    K = 5 and 6, then single steps.  Windows include the periodic corner."""
     w = inputs.WORKLOADS["gs_8192"]
-    n, T = w["nx"], 6
+    n, T = w["nx"], 13
     rho0 = inputs.initial_density("gs_8192")
     taus = [float(t) for t in orc.tau_from_diffusion(np.array(w["D"]))]
     reac = Reaction("gray_scott", F=w["reaction"]["F"], k=w["reaction"]["k"])
     with B.Simulation(lat, 2, n, n, taus, "gray_scott", F=reac.F, k=reac.k, precision="fp32") as sim:
-        sim.init(rho0).step(T)
+        sim.init(rho0)
+        names = [B.lb_rd_handle_variant_name(sim.h, v) for v in range(B.lb_rd_handle_variant_count(sim.h))]
+        if variant == "autotuned":
+            B.lb_rd_autotune(sim.h, iters=2)
+        else:
+            B.lb_rd_set_variant(sim.h, names.index(variant))
+        launches0 = B.lb_rd_launch_count(sim.h)
+        sim.step(T)
+        assert B.lb_rd_launch_count(sim.h) - launches0 < T  # multi-step launches were used
         rho, mass = sim.moments()
     px, py = inputs.spot_positions(w["seed"], n, n, 4)
     m = T + 1
