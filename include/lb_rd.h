@@ -214,7 +214,7 @@ LB_RD_API int lb_rd_launch_count(const lb_rd_handle *h, int64_t *launches);
 
 /* Launch variants and the autotuner.  The step kernel of a precision comes in
  * several launch variants (tile shape, register budget, cache policy, TMA
- * bulk-copy staging, temporal blocking of K = 2, 4, 5, 6 or 8 steps per launch:
+ * bulk-copy staging, temporal blocking of K = 2, 4 .. 8 steps per launch:
  * FP32 variants named tb2*_ (two steps) and deep<K>_ (K steps, the deep1_
  * form one step); see lb_rd_variant_name).  lb_rd_autotune times every
  * variant that fits the grid on the handle's own state -- reading the current

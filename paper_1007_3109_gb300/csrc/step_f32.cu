@@ -97,6 +97,7 @@ const F32Variant kF32Variants[] = {
     {"deep6vp_128_minb3_s5", 128, 6, 3, 4, 6, 4},
     {"deep6vp_128_minb2", 128, 6, 2, 4, 6, 4},
     {"deep5vp_192_minb2", 192, 5, 2, 4, 5, 4},
+    {"deep7vp_128_minb2", 128, 7, 2, 4, 7, 4},
 };
 const int kF32VariantCount = sizeof(kF32Variants) / sizeof(kF32Variants[0]);
 

@@ -456,6 +456,7 @@ cudaError_t launch_step_f32_deep(int v, int Q, int S, const StepArgs &a, cudaStr
         case 21: return dispatch_deep<6, 4, 5, 3, true, true>(Q, S, a, st);
         case 22: return dispatch_deep<6, 4, 4, 2, true, true>(Q, S, a, st);
         case 23: return dispatch_deep<5, 6, 4, 2, true, true>(Q, S, a, st);
+        case 24: return dispatch_deep<7, 4, 4, 2, true, true>(Q, S, a, st);
         default: return cudaErrorInvalidValue;
     }
 }
