@@ -388,10 +388,12 @@ int lb_rd_batch_create(const lb_rd_config *cfgs, int32_t n, lb_rd_batch **out) {
             b->deep_base[i].a = items[i].a;
             b->deep_base[i].a.rho_out = nullptr;
         }
-        // default: the depth-K kernel, K = 6 (D2Q9) or 4 (D2Q5)
+        // default: the depth-K kernel, K = 6 (D2Q9) or 4 (D2Q5); should its
+        // descriptors not be planned (no launch shape for this device), the
+        // batch keeps the previous default
         const int K = b->Q == 9 ? 6 : 4;
-        if (!e) e = plan_deep(b, K);
-        if (!e) b->steps_per_launch = K;
+        if (!e && plan_deep(b, K) == cudaSuccess) b->steps_per_launch = K;
+        cudaGetLastError();  // clear a non-sticky error of the attempt
     }
     if (e) {
         int rc = cuda_err(e, "lb_rd_batch_create allocation");
