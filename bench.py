@@ -258,6 +258,24 @@ def batch_mode(args):
                            "wall_ms_per_step": loop_wall / K, "launches_per_step": ninst},
             "speedup_vs_plain_loop": loop_ms / batched_ms, "gpu_launches": int(launches)}
     line["roofline"]["frac"] = line["roofline"]["achieved"] / peak
+    if not args.no_cpu:
+        # the FP64 oracle, as it stands, on the first 16 instances of the sweep
+        import oracle as orc
+        from oracle import Reaction
+        nsample = min(16, ninst)
+        otaus = [float(t) for t in orc.tau_from_diffusion(np.array(w["D"]))]
+        t_cpu, ssu_cpu = 0.0, 0
+        for i in range(nsample):
+            f = orc.init("D2Q9", rho0s[i])
+            reac = Reaction("gray_scott", F=float(F[i]), k=float(k[i]))
+            t0 = time.perf_counter()
+            orc.run("D2Q9", otaus, reac, f, args.cpu_steps)
+            t_cpu += time.perf_counter() - t0
+            ssu_cpu += 2 * n * n * args.cpu_steps
+        line["cpu_baseline"] = {"value": ssu_cpu / t_cpu / 1e6, "unit": "MLUPS", "cores": orc.threads(),
+                                "kind": "oracle",
+                                "sample": f"{nsample} instances of gs_sweep_256 (256^2, their own F and k), "
+                                          f"{args.cpu_steps} FP64 oracle steps each ({t_cpu:.1f} s)"}
     print(json.dumps(line))
     return 0
 
