@@ -206,9 +206,9 @@ def batch_mode(args):
         for i in range(ninst):
             b.init(i, rho0s[i])
         # 1, 2 (every nx a multiple of 256), 4, 6, 8 time steps per launch; the fastest is the result
-        for k in [int(x) for x in args.batch_k.split(",")]:
+        for spl in [int(x) for x in args.batch_k.split(",")]:
             try:
-                b.set_steps_per_launch(k)
+                b.set_steps_per_launch(spl)
             except B.LbRdError:
                 continue
             b.step(W)
@@ -219,7 +219,7 @@ def batch_mode(args):
             ev1.record()
             torch.cuda.synchronize()
             _, l1 = B.lb_rd_batch_get_time(b.b)
-            per_launch[k] = (ev0.elapsed_time(ev1), l1 - l0)
+            per_launch[spl] = (ev0.elapsed_time(ev1), l1 - l0)
         steps_per_launch = min(per_launch, key=lambda kk: per_launch[kk][0])
         batched_ms, launches = per_launch[steps_per_launch]
         mass0 = b.moments(0)[1]
