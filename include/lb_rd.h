@@ -309,8 +309,12 @@ LB_RD_API int lb_rd_batch_get_time(const lb_rd_batch *b, int64_t *t, int64_t *la
  * while the number of resident requests is below max_slots and their device
  * memory (two state copies plus the density cache) fits hbm_budget_bytes.
  * Resident requests advance together, steps_per_tick steps at a time (fewer
- * when a request finishes sooner), each step ONE launch of the batched kernel
- * over all of them; requests that arrive meanwhile are admitted between ticks
+ * when a request finishes sooner), by launches of the batched kernels over
+ * all of them: for FP32 requests with two state copies, K-step launches of the
+ * depth-K kernel (K = 6 for D2Q9, 4 for D2Q5) while more than K steps of the
+ * tick remain, otherwise one launch per step; the last step of a tick is a
+ * single step (it writes the densities).  Requests that arrive meanwhile are
+ * admitted between ticks
  * as slots and memory free up.  A finished request's densities and mass are
  * copied to host memory and its device memory is released.  Each result is
  * bitwise what a single handle with the same config computes.  Any
