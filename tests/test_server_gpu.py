@@ -69,6 +69,31 @@ def test_results_identical_alone_and_in_the_mix():
         B.lb_rd_server_destroy(srv)
 
 
+@pytest.mark.parametrize("tick", [5, 16, 64])
+def test_d2q5_k_step_ticks_equal_single_handles(tick):
+    """A D2Q5 server: ticks longer than K = 4 steps advance the resident
+    requests by four-step launches of the depth-K kernel (nx % 4 != 0 among
+    them: 4-byte staging for the whole tick), then single steps; every result
+    is bitwise a single handle's."""
+    sides = [(64, 41), (36, 17), (70, 9), (128, 30)]
+    reqs = []
+    for j, (side, steps) in enumerate(sides):
+        kw, rho0, _ = _request(j, side, 1 + j % 2, steps)
+        reqs.append((dict(kw, lattice="D2Q5"), rho0, steps))
+    srv = B.lb_rd_server_create(hbm_budget_bytes=1 << 30, max_slots=4, steps_per_tick=tick, lattice="D2Q5")
+    try:
+        tickets = [B.lb_rd_submit(srv, B.make_config(**kw), rho0, steps) for kw, rho0, steps in reqs]
+        for (kw, rho0, steps), t in zip(reqs, tickets):
+            rc, rho, mass, _ = _wait(srv, t, 2, kw["nx"])
+            assert rc == B.LB_RD_OK
+            ref_rho, _ = _alone(kw, rho0, steps)
+            np.testing.assert_array_equal(rho, ref_rho)
+        if tick > 5:
+            assert B.lb_rd_server_stats(srv)["launches"] < sum(r[2] for r in reqs) // 2
+    finally:
+        B.lb_rd_server_destroy(srv)
+
+
 def test_memory_budget_queues_and_rejects():
     kw, rho0, _ = _request(10, 128, 1, 40)
     need = 2 * 2 * 9 * 128 * 128 * 4 + 2 * 128 * 128 * 4
