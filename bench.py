@@ -639,7 +639,7 @@ def main():
     achieved = bps * sites / avg_launch_s / 1e9
     effective = bps * sites * args.steps / (ms_total / 1e3) / 1e9
     variant_name = names[best]
-    traffic = None
+    traffic = inst_per_launch = None
     if os.path.exists(TRAFFIC_FILE):
         with open(TRAFFIC_FILE) as fh:
             tr = json.load(fh)
@@ -647,6 +647,19 @@ def main():
         if ent and ent.get("n") == n and ent.get("src_sha") == _src_hash(
                 os.path.join(ROOT, "paper_1007_3109_gb300", "csrc", ent["src"])):
             traffic = ent["bytes_per_launch"]
+            inst_per_launch = ent.get("warp_inst_per_launch")
+    # Instruction-issue roofline of the same kernel (the limiter of a K-step
+    # launch): warp instructions per launch from the ncu capture over the
+    # live launch time, against SMs x 4 schedulers x 1 instruction per clock
+    # at the median SM clock sampled during the timed region.
+    clk = clocks.summary()
+    issue = None
+    if inst_per_launch and clk.get("sm_mhz"):
+        issue_peak = torch.cuda.get_device_properties(0).multi_processor_count * 4 * clk["sm_mhz"] * 1e6
+        issue_ach = inst_per_launch / avg_launch_s
+        issue = {"achieved": issue_ach, "peak": issue_peak, "unit": "warp instructions/s", "frac": issue_ach / issue_peak,
+                 "inst_per_launch": inst_per_launch,
+                 "source": "ncu smsp__inst_executed.sum of this kernel (profiles/traffic.json); peak = SMs x 4 x SM clock"}
     single = None
     if tuning:
         ones = {k: v for k, v in tuning.items() if v and B.variant_steps(k) == 1}
@@ -712,12 +725,13 @@ def main():
                      # issue (ncu: issue active well above DRAM throughput), not by HBM
                      "limiter": ("instruction issue (state moved once per launch of %.0f steps; ncu summary in "
                                  "profiles/step_f32_deep_gs4096_ncu_full.md)" % steps_per_launch
-                                 if steps_per_launch > 1.5 else "hbm bandwidth")},
+                                 if steps_per_launch > 1.5 else "hbm bandwidth"),
+                     "issue": issue},
         "depth_sweep": depth or None,
         "e2e": {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "lb_steps": e2e_steps, "path": "lb_rd_init(host) + lb_rd_step + lb_rd_moments(host)"},
         "gpu_launches": int(launches),
-        "clocks": clocks.summary(),
+        "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
         ssu, dt, cores = run_cpu_oracle_sample(args.workload, args.lattice, args.cpu_window, args.cpu_steps)
