@@ -514,7 +514,8 @@ def phase_mode(args):
             "config": {"workload": "gs_sweep_256", "instances": len(ref["F"]), "steps": steps},
             "by_precision_mlups": {p: 2 * r["site_steps"] / r["step_s"] / 1e6 for p, r in res.items()},
             "theory_vs_outcome": table, "precision_agreement": agree,
-            "map": studies.outcome_map(ref), "gpu_launches": int(steps)}
+            "map": studies.outcome_map(ref), "gpu_launches": int(ref["launches"]),
+            "gpu_launches_by_precision": {p: r["launches"] for p, r in res.items()}}
     print(json.dumps(line))
     return 0
 

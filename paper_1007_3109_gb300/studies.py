@@ -131,11 +131,13 @@ def loglog_slope(x, y) -> float:
 def phase_diagram(precision: str = "fp32", steps: int | None = None, keep=(), n_grid: int = 32) -> dict:
     """The Gray-Scott (F, k) sweep gs_sweep_256 in one batch: n_grid^2
     instances of 256^2 sites (F in [0.01, 0.08], k in [0.03, 0.07],
-    D = (0.1, 0.05)), noisy-square init, ``steps`` steps (10000), then each instance's outcome (``analysis.pattern_outcome``
-    of its v field, plus the mean of u) and linear-theory label
+    D = (0.1, 0.05)), noisy-square init, ``steps`` steps (10000), then each
+    instance's outcome (``analysis.pattern_outcome`` of its v field, plus the
+    mean of u) and linear-theory label
     (``analysis.gs_classify``).  Returns {"F", "k", "outcome" (list of
     dicts), "label", "fields" {index: rho} for the indices in ``keep``,
-    "step_s" (device time of the stepping, CUDA events), "site_steps"}."""
+    "step_s" (device time of the stepping, CUDA events), "site_steps",
+    "launches" (batched kernel launches of the stepping)}."""
     import torch
 
     from . import inputs
@@ -152,11 +154,13 @@ def phase_diagram(precision: str = "fp32", steps: int | None = None, keep=(), n_
         for i in range(len(F)):
             b.init(i, inputs.rho0_square(side, side, seed=seed + i))
         torch.cuda.synchronize()
+        _, l0 = B.lb_rd_batch_get_time(b.b)
         e0.record()
         b.step(steps)
         e1.record()
         torch.cuda.synchronize()
         step_s = e0.elapsed_time(e1) / 1e3
+        launches = B.lb_rd_batch_get_time(b.b)[1] - l0
         for i in range(len(F)):
             rho, _ = b.moments(i)
             o = analysis.pattern_outcome(rho[1])
@@ -166,7 +170,7 @@ def phase_diagram(precision: str = "fp32", steps: int | None = None, keep=(), n_
                 fields[i] = rho
     labels = [analysis.gs_classify(float(F[i]), float(k[i]), *D)["label"] for i in range(len(F))]
     return {"F": F, "k": k, "outcome": outcome, "label": labels, "fields": fields, "step_s": step_s,
-            "site_steps": int(len(F) * side * side * steps)}
+            "site_steps": int(len(F) * side * side * steps), "launches": int(launches)}
 
 
 def outcome_map(res: dict, n_grid: int = 32) -> list[str]:
