@@ -205,7 +205,7 @@ def batch_mode(args):
     with B.Batch(cfgs) as b:
         for i in range(ninst):
             b.init(i, rho0s[i])
-        # 1, 2 (every nx a multiple of 256), 4, 6, 8 time steps per launch; the fastest is the result
+        # 1, 2 (every nx a multiple of 256), 4, 5, 6, 8 time steps per launch; the fastest is the result
         for spl in [int(x) for x in args.batch_k.split(",")]:
             try:
                 b.set_steps_per_launch(spl)
@@ -542,7 +542,7 @@ def main():
     ap.add_argument("--inplace", action="store_true", help="one state copy (AA streaming)")
     ap.add_argument("--variant", default="", help="force a launch variant by name (after the autotune sweep)")
     ap.add_argument("--instances", type=int, default=0)
-    ap.add_argument("--batch-k", default="1,2,4,6,8",
+    ap.add_argument("--batch-k", default="1,2,4,5,6,8",
                     help="batch mode: time steps per launch to time (comma-separated); the fastest is the result")
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--steps-scale", type=float, default=0.05)

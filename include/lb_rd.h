@@ -286,7 +286,7 @@ LB_RD_API int lb_rd_batch_set_graph(lb_rd_batch *b, int32_t steps_per_graph);
 
 /* Time steps per launch: 2 runs the two-step (temporal blocking) kernel over
  * all instances, bitwise the same as two single steps; it needs FP32
- * instances with two state copies and nx a multiple of 256.  4, 6 or 8 run
+ * instances with two state copies and nx a multiple of 256.  4, 5, 6 or 8 run
  * the depth-K kernel over the (band, strip) units of all instances (FP32, two
  * state copies, any nx; bitwise the same as K single steps; the default for
  * such batches: 6 for D2Q9, 4 for D2Q5).  Otherwise EINVAL.  1: one step per

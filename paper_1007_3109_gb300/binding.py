@@ -500,7 +500,7 @@ class Batch:
 
     def set_steps_per_launch(self, k):
         """Time steps per batched launch: 1, 2 (two-step kernel, every nx a
-        multiple of 256) or 4, 6, 8 (depth-K kernel; FP32 batches with two
+        multiple of 256) or 4, 5, 6, 8 (depth-K kernel; FP32 batches with two
         state copies default to 6 for D2Q9, 4 for D2Q5).  Bitwise the same
         results for every choice."""
         lb_rd_batch_set_steps_per_launch(self.b, k)

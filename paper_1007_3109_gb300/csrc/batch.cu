@@ -552,13 +552,13 @@ int lb_rd_batch_step(lb_rd_batch *b, int64_t nsteps) {
 
 int lb_rd_batch_set_steps_per_launch(lb_rd_batch *b, int32_t k) {
     if (!b) return report_error(LB_RD_EINVAL, "batch is NULL");
-    if (k != 1 && k != 2 && k != 4 && k != 6 && k != 8)
-        return report_error(LB_RD_EINVAL, "steps per launch must be 1, 2, 4, 6 or 8");
+    if (k != 1 && k != 2 && k != 4 && k != 5 && k != 6 && k != 8)
+        return report_error(LB_RD_EINVAL, "steps per launch must be 1, 2, 4, 5, 6 or 8");
     if (k == 2 && !b->tb_ok)
         return report_error(LB_RD_EINVAL, "two steps per launch need FP32 instances with two state copies and "
                                           "nx a multiple of " + std::to_string(lbrd::batch_tb2_strip()));
     if (k >= 4 && !b->deep_ok)
-        return report_error(LB_RD_EINVAL, "4, 6 or 8 steps per launch need FP32 instances with two state copies");
+        return report_error(LB_RD_EINVAL, "4, 5, 6 or 8 steps per launch need FP32 instances with two state copies");
     cudaStreamSynchronize(b->stream);
     if (k >= 4 && b->deep_K != k) {
         cudaError_t e = plan_deep(b, k);

@@ -150,7 +150,7 @@ struct TbwItem {
 };
 int batch_tb2_strip();
 cudaError_t launch_batch_tb2(const TbwItem *items, int n, int64_t total_units, int Q, int S, cudaStream_t st);
-// Batched K-step launches (K = 4, 6 or 8; FP32, two state copies): the
+// Batched K-step launches (K = 4, 5, 6 or 8; FP32, two state copies): the
 // depth-K kernel over the (band, strip) units of a list of grids.  Item k's
 // units are [unit_begin, unit_begin + nstrips * ceil(ny / band)), strips of
 // 34 - 2K columns fastest.  batch_deep_plan fills nstrips and band of every

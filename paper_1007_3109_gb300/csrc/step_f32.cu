@@ -70,7 +70,7 @@ const F32Variant kF32Variants[] = {
     {"tb2w_288x256_s4", 288, 256, 4, 3, 2, 256},
     {"tb2w_160x128_s3x3", 160, 128, 3, 3, 2, 128},
     {"tb2w_544x512_s2", 544, 512, 2, 3, 2, 512},
-    // temporal blocking to depth K, levels in registers (step_f32_deep.cu): threads, K, min blocks per SM
+    // temporal blocking to depth K, levels in registers (step_f32_deep_kernel.cuh): threads, K, min blocks per SM
     {"deep1_128_minb4", 128, 1, 4, 4, 1, 1},
     {"deep2_128_minb4", 128, 2, 4, 4, 2, 1},
     {"deep4_128_minb4", 128, 4, 4, 4, 4, 1},

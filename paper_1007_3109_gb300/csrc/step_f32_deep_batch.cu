@@ -1,0 +1,117 @@
+// Temporal blocking to depth K over a list of grids (batches and server
+// ticks): the launch shape per K, the (band, strip) plan of the list and the
+// launch (the kernel is in step_f32_deep_kernel.cuh).
+#include "step_f32_deep_kernel.cuh"
+
+namespace lbrd {
+
+namespace {
+
+// Batched launch shapes per K: the single-grid choices (K = 4, 5: six warps,
+// two blocks per SM; K = 6, 8: four warps, two blocks per SM; K = 5, 8 with
+// the pulls from earlier rows first).
+template <int Q, int S, int K, bool V16>
+struct BatchShape;
+template <int Q, int S, bool V16>
+struct BatchShape<Q, S, 4, V16> : DeepKernel<Q, S, 4, 6, 4, 2, V16, true> {
+    static constexpr int NW = 6;
+    static constexpr bool PP = false;
+};
+template <int Q, int S, bool V16>
+struct BatchShape<Q, S, 5, V16> : DeepKernel<Q, S, 5, 6, 4, 2, V16, true, true> {
+    static constexpr int NW = 6;
+    static constexpr bool PP = true;
+};
+template <int Q, int S, bool V16>
+struct BatchShape<Q, S, 6, V16> : DeepKernel<Q, S, 6, 4, 4, 2, V16, true> {
+    static constexpr int NW = 4;
+    static constexpr bool PP = false;
+};
+template <int Q, int S, bool V16>
+struct BatchShape<Q, S, 8, V16> : DeepKernel<Q, S, 8, 4, 4, 2, V16, true, true> {
+    static constexpr int NW = 4;
+    static constexpr bool PP = true;
+};
+
+template <int Q, int S, int K, bool V16>
+int64_t plan_batch(DeepItem *items, int n) {
+    using BS = BatchShape<Q, S, K, V16>;
+    constexpr int WO = 34 - 2 * K;
+    unsigned full = 0;
+    if (BS::get(&full) != cudaSuccess) return -1;
+    int64_t strips = 0, ny = 1;
+    for (int i = 0; i < n; ++i) {
+        items[i].nstrips = (items[i].a.nx + WO - 1) / WO;
+        strips += items[i].nstrips;
+        ny = items[i].a.ny > ny ? items[i].a.ny : ny;
+    }
+    const int64_t nb = choose_bands(K, strips, ny, (int64_t)full * BS::NW);
+    int64_t units = 0;
+    for (int i = 0; i < n; ++i) {
+        const int64_t g = items[i].a.ny;
+        items[i].band = (g + nb - 1) / nb;
+        items[i].unit_begin = units;
+        units += items[i].nstrips * ((g + items[i].band - 1) / items[i].band);
+    }
+    return units;
+}
+
+template <int Q, int S, int K, bool V16>
+cudaError_t launch_batch(const DeepItem *items, int n, int64_t total_units, cudaStream_t st) {
+    using BS = BatchShape<Q, S, K, V16>;
+    unsigned full = 0;
+    cudaError_t e = BS::get(&full);
+    if (e != cudaSuccess) return e;
+    const int64_t nwarps = (int64_t)full * BS::NW;
+    const unsigned grid = total_units < nwarps ? (unsigned)((total_units + BS::NW - 1) / BS::NW) : full;
+    step_deep_kernel<Q, S, K, BS::NW, 4, 2, V16, true, BS::PP>
+        <<<grid, BS::NW * 32, BS::smem, st>>>(StepArgs{}, 0, 0, 0, items, n, total_units);
+    return cudaGetLastError();
+}
+
+template <int K, bool V16>
+int64_t plan_qs(int Q, int S, DeepItem *items, int n) {
+    if (Q == 9 && S == 1) return plan_batch<9, 1, K, V16>(items, n);
+    if (Q == 9 && S == 2) return plan_batch<9, 2, K, V16>(items, n);
+    if (Q == 5 && S == 1) return plan_batch<5, 1, K, V16>(items, n);
+    if (Q == 5 && S == 2) return plan_batch<5, 2, K, V16>(items, n);
+    return -1;
+}
+
+template <int K, bool V16>
+cudaError_t launch_qs(int Q, int S, const DeepItem *items, int n, int64_t total_units, cudaStream_t st) {
+    if (Q == 9 && S == 1) return launch_batch<9, 1, K, V16>(items, n, total_units, st);
+    if (Q == 9 && S == 2) return launch_batch<9, 2, K, V16>(items, n, total_units, st);
+    if (Q == 5 && S == 1) return launch_batch<5, 1, K, V16>(items, n, total_units, st);
+    if (Q == 5 && S == 2) return launch_batch<5, 2, K, V16>(items, n, total_units, st);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+int64_t batch_deep_plan(int K, int Q, int S, bool v16, DeepItem *items, int n) {
+    switch (K) {
+        case 4: return v16 ? plan_qs<4, true>(Q, S, items, n) : plan_qs<4, false>(Q, S, items, n);
+        case 5: return v16 ? plan_qs<5, true>(Q, S, items, n) : plan_qs<5, false>(Q, S, items, n);
+        case 6: return v16 ? plan_qs<6, true>(Q, S, items, n) : plan_qs<6, false>(Q, S, items, n);
+        case 8: return v16 ? plan_qs<8, true>(Q, S, items, n) : plan_qs<8, false>(Q, S, items, n);
+        default: return -1;
+    }
+}
+
+cudaError_t launch_batch_deep(int K, int Q, int S, bool v16, const DeepItem *items, int n, int64_t total_units,
+                              cudaStream_t st) {
+    switch (K) {
+        case 4: return v16 ? launch_qs<4, true>(Q, S, items, n, total_units, st)
+                           : launch_qs<4, false>(Q, S, items, n, total_units, st);
+        case 5: return v16 ? launch_qs<5, true>(Q, S, items, n, total_units, st)
+                           : launch_qs<5, false>(Q, S, items, n, total_units, st);
+        case 6: return v16 ? launch_qs<6, true>(Q, S, items, n, total_units, st)
+                           : launch_qs<6, false>(Q, S, items, n, total_units, st);
+        case 8: return v16 ? launch_qs<8, true>(Q, S, items, n, total_units, st)
+                           : launch_qs<8, false>(Q, S, items, n, total_units, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace lbrd

@@ -1,6 +1,6 @@
 // Per-site step and per-grid arguments shared by the multi-step FP32
 // kernels (two steps per launch in step_f32_tb.cu, K steps per launch in
-// step_f32_deep.cu).  collide_site is the one-step kernels' arithmetic
+// step_f32_deep_kernel.cuh).  collide_site is the one-step kernels' arithmetic
 // (density in index order, reaction, relaxation with source of Eq. relax in
 // the FP32 form fma(1 - omega, f, w (omega rho + R))), so a multi-step launch
 // gives the bits of as many single steps.

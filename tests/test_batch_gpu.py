@@ -164,7 +164,7 @@ def test_batch_two_steps_per_launch_equals_single_handles(lat, graph, steps):
 
 
 @pytest.mark.parametrize("lat", ["D2Q9", "D2Q5"])
-@pytest.mark.parametrize("K", [4, 6, 8])
+@pytest.mark.parametrize("K", [4, 5, 6, 8])
 @pytest.mark.parametrize("staging", ["16-byte", "4-byte"])
 @pytest.mark.parametrize("graph", [0, 8, 12])
 def test_batch_k_steps_per_launch_equals_single_handles(lat, K, staging, graph):
@@ -201,7 +201,7 @@ def test_batch_steps_per_launch_switch():
             b.set_steps_per_launch(2)
         b.set_steps_per_launch(1)
         b.set_steps_per_launch(6)  # the depth-K kernel takes any nx
-        for k in (0, 3, 5, 16):
+        for k in (0, 3, 7, 16):
             with pytest.raises(B.LbRdError):
                 b.set_steps_per_launch(k)
     ip = [dict(c, inplace=True) for c in _configs("fp32")[:2]]
