@@ -64,7 +64,8 @@ def test_every_fp32_variant_is_bitwise_identical(grid):
 
 @pytest.mark.parametrize("grid", [("D2Q9", 2, 70, 37, "gray_scott"), ("D2Q5", 2, 100, 9, "gray_scott"),
                                   ("D2Q9", 1, 33, 17, "linear"), ("D2Q9", 2, 100, 37, "gray_scott"),
-                                  ("D2Q9", 2, 12, 5, "gray_scott")], ids=lambda g: f"{g[0]}-S{g[1]}-{g[2]}x{g[3]}")
+                                  ("D2Q9", 2, 12, 5, "gray_scott"), ("D2Q5", 2, 44, 13, "linear")],
+                         ids=lambda g: f"{g[0]}-S{g[1]}-{g[2]}x{g[3]}-{g[4]}")
 def test_k_step_variants_over_step_counts(grid):
     """deep<K>_ variants advance K steps per launch and finish with 1 .. K
     single steps: every step count gives the bits of single steps (ragged
