@@ -98,6 +98,10 @@ const F32Variant kF32Variants[] = {
     {"deep6vp_128_minb2", 128, 6, 2, 4, 6, 4},
     {"deep5vp_192_minb2", 192, 5, 2, 4, 5, 4},
     {"deep7vp_128_minb2", 128, 7, 2, 4, 7, 4},
+    {"deep6v_128_minb2_s5", 128, 6, 2, 4, 6, 4},
+    {"deep6v_64_minb4", 64, 6, 4, 4, 6, 4},
+    {"deep5v_64_minb4", 64, 5, 4, 4, 5, 4},
+    {"deep6v_256_minb1", 256, 6, 1, 4, 6, 4},
 };
 const int kF32VariantCount = sizeof(kF32Variants) / sizeof(kF32Variants[0]);
 

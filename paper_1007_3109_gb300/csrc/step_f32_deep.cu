@@ -46,6 +46,10 @@ cudaError_t launch_step_f32_deep(int v, int Q, int S, const StepArgs &a, cudaStr
         case 22: return dispatch_deep<6, 4, 4, 2, true, true>(Q, S, a, st);
         case 23: return dispatch_deep<5, 6, 4, 2, true, true>(Q, S, a, st);
         case 24: return dispatch_deep<7, 4, 4, 2, true, true>(Q, S, a, st);
+        case 25: return dispatch_deep<6, 4, 5, 2, true>(Q, S, a, st);
+        case 26: return dispatch_deep<6, 2, 4, 4, true>(Q, S, a, st);
+        case 27: return dispatch_deep<5, 2, 4, 4, true>(Q, S, a, st);
+        case 28: return dispatch_deep<6, 8, 4, 1, true>(Q, S, a, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -119,7 +119,7 @@ def test_variant_table_on_the_host(lib):
     names = [B.lb_rd_variant_name("fp32", v) for v in range(n)]
     assert len(set(names)) == n and names[0] == "64x2_minb4"
     assert any(x.startswith("bulk") for x in names) and any(x.startswith("tb2") for x in names)
-    assert sorted(B.variant_steps(x) for x in names if x.startswith("deep")) == [1, 2, 2, 4, 4, 4, 4, 4, 4, 4, 4, 5, 5, 5, 6, 6, 6, 6, 6, 7, 8, 8, 8, 8, 8]
+    assert sorted(B.variant_steps(x) for x in names if x.startswith("deep")) == [1, 2, 2, 4, 4, 4, 4, 4, 4, 4, 4, 5, 5, 5, 5, 6, 6, 6, 6, 6, 6, 6, 6, 7, 8, 8, 8, 8, 8]
     assert B.lb_rd_variant_count("fp64") == 1
 
 
