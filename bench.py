@@ -484,6 +484,98 @@ def network_mode(args):
     return 0
 
 
+def parity_mode(args):
+    """The parity workloads at their full step counts on the GPU and on the
+    FP64 oracle: decay_128 (one species, linear reaction, D2Q9 and D2Q5,
+    FP64, 2000 steps) and gs_512 (Gray-Scott 512^2, FP64 and FP32, 20000
+    steps).  Parity: FP64 bit for bit over the whole run; FP32 pointwise after
+    1000 steps (maximum relative error per species <= 1e-3) and, as the
+    pattern then diverges under rounding, by its dominant wavelength after
+    the full run (within 2 %: the library's structure-factor peak of the GPU
+    field against the oracle's of its own field).  The GPU states fit in L2,
+    so the GPU is timed on a sample of single steps, each after a 512 MB
+    write that evicts L2, with CUDA events around every step; the oracle on
+    its full runs (host cores)."""
+    import torch
+    import oracle as orc
+    from oracle import Reaction
+    from paper_1007_3109_gb300 import analysis
+    from paper_1007_3109_gb300 import binding as B
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    cases = [("decay_128", "D2Q9", "fp64"), ("decay_128", "D2Q5", "fp64"), ("gs_512", "D2Q9", "fp64"),
+             ("gs_512", "D2Q9", "fp32")]
+    out, oracle_runs = {}, {}
+    for name, lat, prec in cases:
+        w = inputs.WORKLOADS[name]
+        steps = args.parity_steps or w["steps"]
+        early = min(1000, steps)
+        n, S, r = w["nx"], w["nspecies"], w["reaction"]
+        rho0 = inputs.initial_density(name)
+        if (name, lat) not in oracle_runs:
+            otaus = [float(t) for t in orc.tau_from_diffusion(np.array(w["D"]))]
+            reac = (Reaction("linear", kappa=r["kappa"]) if r["kind"] == "linear"
+                    else Reaction("gray_scott", F=r["F"], k=r["k"]))
+            f = orc.init(lat, rho0)
+            t0 = time.perf_counter()
+            f = orc.run(lat, otaus, reac, f, early)
+            dt = time.perf_counter() - t0
+            ref_early = orc.density(lat, f)
+            t0 = time.perf_counter()
+            f = orc.run(lat, otaus, reac, f, steps - early)
+            dt += time.perf_counter() - t0
+            oracle_runs[(name, lat)] = (ref_early, orc.density(lat, f), S * n * n * steps / dt / 1e6, dt)
+        ref_early, ref, oracle_mlups, oracle_s = oracle_runs[(name, lat)]
+        gtaus = [float(B.lb_rd_tau_from_diffusion(D)) for D in w["D"]]
+        kw = dict(kappa=r["kappa"]) if r["kind"] == "linear" else dict(F=r["F"], k=r["k"])
+        with B.Simulation(lat, S, n, n, gtaus, r["kind"], precision=prec, stream=stream.cuda_stream, **kw) as sim:
+            sim.init(rho0).step(early)
+            rho_early, _ = sim.moments()
+            sim.step(steps - early)
+            rho, _ = sim.moments()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.parity_timed)]
+            for e0, e1 in evs:
+                flush.zero_()  # same stream: the step starts with L2 holding none of the state
+                e0.record(stream)
+                B.lb_rd_step(sim.h, 1)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            step_ms = sum(e0.elapsed_time(e1) for e0, e1 in evs) / len(evs)
+
+        def rel(a, b):
+            return (np.max(np.abs(a - b), axis=(1, 2)) / np.max(np.abs(b), axis=(1, 2))).tolist()
+        case = {"steps": steps, "bitwise_equal_to_oracle": bool(np.array_equal(rho, ref)),
+                f"max_rel_err_after_{early}_steps": rel(rho_early, ref_early), "max_rel_err_full_run": rel(rho, ref),
+                "gpu_mlups": S * n * n / (step_ms / 1e3) / 1e6, "gpu_ms_per_step": step_ms,
+                "oracle_mlups": oracle_mlups, "oracle_s_full_run": oracle_s}
+        if prec == "fp64":
+            assert case["bitwise_equal_to_oracle"], (name, lat, case)
+        else:
+            assert max(case[f"max_rel_err_after_{early}_steps"]) <= 1e-3, (name, lat, prec, case)
+            lam_gpu = analysis.dominant_wavelength(rho[S - 1])["wavelength"]
+            lam_ref = orc.structure_factor_peak(ref[S - 1])["wavelength"]
+            case["wavelength_gpu_oracle"] = [lam_gpu, lam_ref]
+            assert abs(lam_gpu - lam_ref) <= 0.02 * lam_ref, (name, lat, prec, lam_gpu, lam_ref)
+        out[f"{name}/{lat}/{prec}"] = case
+    main_case = out["gs_512/D2Q9/fp64"]
+    line = {"metric": "MLUPS", "value": main_case["gpu_mlups"], "unit": "MLUPS (species-site updates/s / 1e6)",
+            "n_gpus": 1, "steps": args.parity_timed, "warmup": 0, "ms_per_step": main_case["gpu_ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "gs_512 (FP64; decay_128 and FP32 in cases)",
+                       "l2": "flushed before every timed step (512 MB write on the stream)",
+                       "timed": f"{args.parity_timed} single steps after the full run"},
+            "cases": out,
+            "cpu_baseline": {"value": main_case["oracle_mlups"], "unit": "MLUPS", "cores": orc.threads(),
+                             "kind": "oracle",
+                             "sample": f"the full {main_case['steps']}-step gs_512 run "
+                                       f"({main_case['oracle_s_full_run']:.1f} s)"},
+            "gpu_launches": int(args.parity_timed)}
+    print(json.dumps(line))
+    return 0
+
+
 def phase_mode(args):
     """gs_sweep_256 as a phase diagram (Sec. III.B-D, Fig. 6): the 1024-instance
     (F, k) sweep for its full 10000 steps in one batch per storage format;
@@ -537,7 +629,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--tune-iters", type=int, default=10)
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serving", "truncation", "phase", "network"])
+    ap.add_argument("--mode", default="step",
+                    choices=["step", "batch", "serving", "truncation", "phase", "network", "parity"])
+    ap.add_argument("--parity-steps", type=int, default=0, help="parity mode: steps of the full runs (0: the workload's)")
+    ap.add_argument("--parity-timed", type=int, default=200, help="parity mode: timed single steps (L2 flushed)")
     ap.add_argument("--phase-steps", type=int, default=10000)
     ap.add_argument("--inplace", action="store_true", help="one state copy (AA streaming)")
     ap.add_argument("--variant", default="", help="force a launch variant by name (after the autotune sweep)")
@@ -566,6 +661,8 @@ def main():
         return phase_mode(args)
     if args.mode == "network":
         return network_mode(args)
+    if args.mode == "parity":
+        return parity_mode(args)
 
     import torch
     from paper_1007_3109_gb300 import binding as B
