@@ -70,14 +70,16 @@ const F32Variant kF32Variants[] = {
     {"tb2w_288x256_s4", 288, 256, 4, 3, 2, 256},
     {"tb2w_160x128_s3x3", 160, 128, 3, 3, 2, 128},
     {"tb2w_544x512_s2", 544, 512, 2, 3, 2, 512},
-    // temporal blocking to depth K, levels in registers (step_f32_deep_kernel.cuh): threads, K, min blocks per SM
+    // temporal blocking to depth K, levels in registers (step_f32_deep_kernel.cuh): threads, K, min blocks
+    // per SM; names deep<K>[v][p]_<threads>_minb<blocks>[_s<rows staged>]: v 16-byte staging (nx % 4 == 0),
+    // p the pulls from earlier rows first, four staged rows unless _s5
     {"deep1_128_minb4", 128, 1, 4, 4, 1, 1},
     {"deep2_128_minb4", 128, 2, 4, 4, 2, 1},
     {"deep4_128_minb4", 128, 4, 4, 4, 4, 1},
     {"deep4_128_minb3", 128, 4, 3, 4, 4, 1},
     {"deep8_128_minb2", 128, 8, 2, 4, 8, 1},
     {"deep8_128_minb3", 128, 8, 3, 4, 8, 1},
-    // the same with the level-0 rows staged in 16-byte chunks (nx % 4 == 0)
+    // 16-byte staging of the level-0 rows
     {"deep2v_128_minb4", 128, 2, 4, 4, 2, 4},
     {"deep4v_128_minb4", 128, 4, 4, 4, 4, 4},
     {"deep4v_128_minb3", 128, 4, 3, 4, 4, 4},
@@ -92,7 +94,7 @@ const F32Variant kF32Variants[] = {
     {"deep5v_192_minb2", 192, 5, 2, 4, 5, 4},
     {"deep6v_192_minb2", 192, 6, 2, 4, 6, 4},
     {"deep6v_128_minb3_s5", 128, 6, 3, 4, 6, 4},
-    // the same, the pulls from earlier rows at the start of an iteration
+    // 16-byte staging, the pulls from earlier rows at the start of an iteration
     {"deep8vp_128_minb2", 128, 8, 2, 4, 8, 4},
     {"deep6vp_128_minb3_s5", 128, 6, 3, 4, 6, 4},
     {"deep6vp_128_minb2", 128, 6, 2, 4, 6, 4},
