@@ -224,8 +224,14 @@ def batch_mode(args):
         batched_ms, launches = per_launch[steps_per_launch]
         mass0 = b.moments(0)[1]
         t_batch = B.lb_rd_batch_get_time(b.b)[0]
-    # plain loop: every instance through its own handle, instance after instance
-    sims = [B.Simulation(**c) for c in cfgs]
+    # plain loop: every instance through its own handle, instance after instance,
+    # with the autotuner's choice for 256^2 (one handle tuned; handles created
+    # afterwards start from its choice, K-step variants included)
+    first = B.Simulation(**cfgs[0])
+    first.init(rho0s[0])
+    B.lb_rd_autotune(first.h, iters=5)
+    loop_variant = B.lb_rd_handle_variant_name(first.h, B.lb_rd_get_variant(first.h))
+    sims = [first] + [B.Simulation(**c) for c in cfgs[1:]]
     for sim, r in zip(sims, rho0s):
         sim.init(r).step(t_batch - K)
     torch.cuda.synchronize()
@@ -255,7 +261,7 @@ def batch_mode(args):
                          "bytes_per_site_per_launch": bps, "steps_per_launch": K / launches,
                          "effective_per_step_GBs": bps * n * n * ninst / (batched_ms / K / 1e3) / 1e9},
             "plain_loop": {"value": ssu / (loop_ms / 1e3) / 1e6, "ms_per_step": loop_ms / K,
-                           "wall_ms_per_step": loop_wall / K, "launches_per_step": ninst},
+                           "wall_ms_per_step": loop_wall / K, "variant": loop_variant},
             "speedup_vs_plain_loop": loop_ms / batched_ms, "gpu_launches": int(launches)}
     line["roofline"]["frac"] = line["roofline"]["achieved"] / peak
     if not args.no_cpu:
@@ -330,7 +336,14 @@ def serving_mode(args):
     stats = B.lb_rd_server_stats(srv)
     B.lb_rd_server_destroy(srv)
     makespan = (max(ends) - starts0) / 1e9
-    # serial FIFO plain loop on the same stream
+    # serial FIFO plain loop on the same stream; every grid side tuned beforehand
+    # (untimed), so each handle starts from the autotuner's choice for its
+    # shape, K-step variants included
+    for side in sorted(set(int(x) for x in sides)):
+        j = int(np.nonzero(sides == side)[0][0])
+        with B.Simulation(**cfg(j, server=False)) as sim:
+            sim.init(rho0s[j])
+            B.lb_rd_autotune(sim.h, iters=args.fifo_tune_iters)
     t0 = time.perf_counter()
     lat_fifo = []
     for j in range(nreq):
@@ -627,6 +640,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2000,
                     help="FP64 oracle steps of the CPU baseline sample (about 10-30 s on the host cores)")
     ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--batch-steps", type=int, default=20,
+                    help="steps of the gs_sweep_256 batched sub-measure beside the headline (0: skip)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--tune-iters", type=int, default=10)
     ap.add_argument("--mode", default="step",
@@ -646,6 +661,8 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=64.0)
     ap.add_argument("--slots", type=int, default=64)
     ap.add_argument("--tick", type=int, default=64)
+    ap.add_argument("--fifo-tune-iters", type=int, default=1,
+                    help="serving mode: autotuner iterations per grid side for the FIFO loop's handles")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -718,7 +735,6 @@ def main():
         barrier()
     launches = B.lb_rd_launch_count(sim.h) - launches0
     ms_total = ev0.elapsed_time(ev1)
-    kernel_ms, kernel_launches = ms_total, launches  # the region holds only step launches
     steps_per_launch = args.steps / max(launches, 1)
     sites = n * n
     ssu_per_step = 2 * sites
@@ -727,16 +743,33 @@ def main():
     assert np.all(np.isfinite(mass)), "non-finite mass"
     value = work / (ms_total / 1e3) / 1e6
 
-    # -- roofline of the step kernel ---------------------------------------------
+    # -- roofline of the dominant kernel -----------------------------------------
+    # The timed call repeated with per-launch CUDA events on the launching stream
+    # (lb_rd_launch_times): the same launch plan, each launch timed on its own.
+    # The dominant kernel is the (variant, steps per launch) pair with the most
+    # device time; its achieved bandwidth is the algorithmic bytes of one launch
+    # (one read and one write of the state, bps per site) over its mean launch
+    # time.  Enough repetitions for >= 30 launches of it.
     peak, peak_kind = measured_peaks()
     bps = BYTES_PER_SITE[(args.lattice, args.precision, 2)]
-    avg_launch_s = kernel_ms / 1e3 / max(kernel_launches, 1)
-    # Algorithmic bytes of one launch: one read and one write of the state.  A
-    # two-step (temporal blocking) launch moves the state once for two steps,
-    # so its per-launch figure is HBM use and the per-step figure exceeds it.
+    reps = max(1, -(-30 // max(launches, 1)))
+    B.lb_rd_set_timing(sim.h, True)
+    for _ in range(reps):
+        B.lb_rd_step(sim.h, args.steps)
+    l_ms, l_steps, l_var = B.lb_rd_launch_times(sim.h)
+    B.lb_rd_set_timing(sim.h, False)
+    by_kernel = {}
+    for t, d, v in zip(l_ms, l_steps, l_var):
+        e = by_kernel.setdefault((names[v], d), [0.0, 0])
+        e[0] += t
+        e[1] += 1
+    (variant_name, dom_steps), (dom_ms, dom_n) = max(by_kernel.items(), key=lambda kv: kv[1][0])
+    avg_launch_s = dom_ms / dom_n / 1e3
     achieved = bps * sites / avg_launch_s / 1e9
     effective = bps * sites * args.steps / (ms_total / 1e3) / 1e9
-    variant_name = names[best]
+    launch_plan = {f"{k[0]} ({k[1]} steps)": {"launches_per_call": v[1] // reps, "mean_ms": v[0] / v[1],
+                                              "share": v[0] / sum(x[0] for x in by_kernel.values())}
+                   for k, v in sorted(by_kernel.items(), key=lambda kv: -kv[1][0])}
     traffic = inst_per_launch = None
     if os.path.exists(TRAFFIC_FILE):
         with open(TRAFFIC_FILE) as fh:
@@ -823,14 +856,16 @@ def main():
                    "streaming": "in-place (AA), one state copy" if args.inplace else "ping-pong, two state copies"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "kernel": f"step_{args.precision}:{variant_name}",
-                     "steps_per_launch": steps_per_launch, "bytes_per_site_per_launch": bps,
+                     "steps_per_launch": dom_steps, "bytes_per_site_per_launch": bps,
+                     "avg_launch_ms": avg_launch_s * 1e3, "launches_timed": dom_n,
+                     "timing": f"per-launch CUDA events on the launching stream, the timed call repeated {reps}x",
+                     "launch_plan": launch_plan, "mean_steps_per_launch": steps_per_launch,
                      "effective_per_step_GBs": effective, "effective_frac": effective / peak,
-                     "peak_kind": peak_kind, "avg_launch_ms": avg_launch_s * 1e3, "single_step": single,
+                     "peak_kind": peak_kind, "single_step": single,
                      # a K-step launch moves the state once for K steps: it is bound by instruction
-                     # issue (ncu: issue active well above DRAM throughput), not by HBM
-                     "limiter": ("instruction issue (state moved once per launch of %.0f steps; ncu summary in "
-                                 "profiles/step_f32_deep_gs4096_ncu_full.md)" % steps_per_launch
-                                 if steps_per_launch > 1.5 else "hbm bandwidth"),
+                     # issue (ncu: issue active well above DRAM throughput), not by HBM alone
+                     "limiter": ("instruction issue and HBM (state moved once per launch of %d steps)" % dom_steps
+                                 if dom_steps > 1 else "hbm bandwidth"),
                      "issue": issue},
         "depth_sweep": depth or None,
         "e2e": {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -853,11 +888,80 @@ def main():
             "value": ssu1 / dt1 / 1e6, "unit": "MLUPS", "cores": 1,
             "sample": f"{args.cpu_window // 4}x{args.cpu_window // 4} window, {args.cpu_steps // 2} steps ({dt1:.1f} s)"}
     sim.close()
+    if rank == 0 and args.batch_steps > 0 and args.lattice == "D2Q9" and args.precision == "fp32":
+        line["batched"] = batched_sub_measure(args)
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
+        dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def batched_sub_measure(args):
+    """gs_sweep_256 beside the headline: 1024 Gray-Scott instances of 256^2 on
+    the (F, k) grid of the phase-diagram sweep (Sec. III), FP32, advanced
+    args.batch_steps steps (i) batched: the library's default depth-K
+    launches over the combined unit list of all instances, and (ii) by the
+    plain loop, every instance through its own handle, instance after
+    instance, each handle with the autotuner's choice for 256^2 (K-step
+    variants included).  Both timed with CUDA events on the launching stream
+    after args.warmup steps; the sampled instances of the two must agree bit
+    for bit (equal accuracy)."""
+    import torch
+    from paper_1007_3109_gb300 import binding as B
+    w = inputs.WORKLOADS["gs_sweep_256"]
+    F, k = inputs.sweep_params()
+    n, ninst = w["nx"], w["instances"]
+    taus = [float(B.lb_rd_tau_from_diffusion(D)) for D in w["D"]]
+    cfgs = [dict(lattice="D2Q9", nspecies=2, nx=n, ny=n, tau=taus, reaction="gray_scott", F=float(F[i]),
+                 k=float(k[i]), precision="fp32") for i in range(ninst)]
+    rho0s = [inputs.rho0_square(n, n, seed=w["seed"] + i) for i in range(ninst)]
+    K, W = args.batch_steps, args.warmup
+    samples = [0, ninst // 3, ninst - 1]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with B.Batch(cfgs) as b:
+        for i in range(ninst):
+            b.init(i, rho0s[i])
+        b.step(W)
+        torch.cuda.synchronize()
+        _, l0 = B.lb_rd_batch_get_time(b.b)
+        ev0.record()
+        b.step(K)
+        ev1.record()
+        torch.cuda.synchronize()
+        _, l1 = B.lb_rd_batch_get_time(b.b)
+        batched_ms = ev0.elapsed_time(ev1)
+        rho_b = [b.moments(i)[0] for i in samples]
+    # the plain loop: tune one 256^2 handle; handles created afterwards start from its choice
+    first = B.Simulation(**cfgs[0])
+    first.init(rho0s[0])
+    B.lb_rd_autotune(first.h, iters=5)
+    sims = [first] + [B.Simulation(**c) for c in cfgs[1:]]
+    for sim, r in zip(sims, rho0s):
+        sim.init(r).step(W)
+    variant = B.lb_rd_handle_variant_name(first.h, B.lb_rd_get_variant(first.h))
+    torch.cuda.synchronize()
+    c0 = sum(B.lb_rd_launch_count(sim.h) for sim in sims)
+    ev0.record()
+    for sim in sims:
+        sim.step(K)
+    ev1.record()
+    torch.cuda.synchronize()
+    loop_ms = ev0.elapsed_time(ev1)
+    loop_launches = sum(B.lb_rd_launch_count(sim.h) for sim in sims) - c0
+    same = all(np.array_equal(sims[i].moments()[0], rb) for i, rb in zip(samples, rho_b))
+    for sim in sims:
+        sim.close()
+    ssu = 2 * n * n * ninst * K
+    return {"workload": "gs_sweep_256", "instances": ninst, "nx": n, "ny": n, "steps": K, "warmup": W,
+            "value": ssu / (batched_ms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": batched_ms / K,
+            "gpu_launches": int(l1 - l0),
+            "plain_loop": {"value": ssu / (loop_ms / 1e3) / 1e6, "ms_per_step": loop_ms / K,
+                           "variant": variant, "gpu_launches": int(loop_launches)},
+            "speedup_vs_plain_loop": loop_ms / batched_ms,
+            "bitwise_equal_sampled": bool(same), "sampled_instances": samples,
+            "l2": "no flush: state of 9.66 GB (two copies) per form >> 129 MB L2"}
 
 
 def sim_state_bytes(lattice, precision, n):

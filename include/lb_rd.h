@@ -144,6 +144,11 @@ typedef struct {
     int32_t track_mass;      /* nonzero: every step also reduces sum_x rho_s in FP64 */
     int32_t streaming;       /* lb_rd_streaming */
     void *stream;            /* cudaStream_t for all work; NULL = legacy default stream */
+    int32_t tb_depth;        /* time steps per launch (temporal blocking): 0 = the autotuner's cached choice
+                                (else one step per launch); 1 = one; 2 .. 8 = a depth-K variant of that
+                                many steps (FP32 storage with two state copies and at most two species
+                                only, else EINVAL).  Batches take cfgs[0].tb_depth as their steps per
+                                launch when it is nonzero; servers and lb_rd_step_noalloc ignore it. */
 } lb_rd_config;
 
 typedef struct lb_rd_handle lb_rd_handle;
@@ -176,8 +181,14 @@ LB_RD_API int lb_rd_destroy(lb_rd_handle *h);
 LB_RD_API int lb_rd_init(lb_rd_handle *h, const double *rho0, int is_device);
 
 /* Advance nsteps >= 0 time steps of Eq. relax (collide, then stream with
- * periodic wrap).  Asynchronous on the handle's stream.  Each step is one
- * fused kernel: pull-stream, rho_s = sum_i f_i,s, R_s, BGK + source, store. */
+ * periodic wrap).  Asynchronous on the handle's stream.  Each step is the
+ * fused update: pull-stream, rho_s = sum_i f_i,s, R_s, BGK + source, store;
+ * one launch runs one step, or K steps with a temporal-blocking variant (see
+ * lb_rd_autotune).  With a depth-K variant the call runs K steps per launch
+ * and splits its last steps into launches of fewer steps (chosen from the
+ * autotuner's times per depth to finish soonest); a last launch of two or more
+ * steps also writes the densities rho(t), so that no single-step launch is
+ * needed to leave them available. */
 LB_RD_API int lb_rd_step(lb_rd_handle *h, int64_t nsteps);
 
 /* Current time step t of the handle. */
@@ -208,6 +219,13 @@ LB_RD_API int lb_rd_restore(lb_rd_handle *h, const void *host_buf, size_t bytes)
  * last reset (enable = 1 also resets). */
 LB_RD_API int lb_rd_set_timing(lb_rd_handle *h, int enable);
 LB_RD_API int lb_rd_kernel_time(lb_rd_handle *h, double *total_ms, int64_t *launches);
+/* The same events launch by launch: launch i of the timed step kernels (in
+ * order, since the last lb_rd_set_timing) took ms[i] milliseconds, advanced
+ * steps[i] time steps and ran launch variant variant[i] (lb_rd_handle_variant_name).
+ * At most max entries are written (any array may be NULL); *count (may be
+ * NULL) receives the number of timed launches.  Synchronises. */
+LB_RD_API int lb_rd_launch_times(lb_rd_handle *h, double *ms, int32_t *steps, int32_t *variant, int64_t max,
+                                 int64_t *count);
 
 /* Number of kernels this handle has launched since creation. */
 LB_RD_API int lb_rd_launch_count(const lb_rd_handle *h, int64_t *launches);
@@ -220,17 +238,21 @@ LB_RD_API int lb_rd_launch_count(const lb_rd_handle *h, int64_t *launches);
  * variant that fits the grid on the handle's own state -- reading the current
  * state and writing the spare copy, so the simulation is unchanged -- with
  * one warm-up launch and `iters` timed launches each, and selects the fastest
- * single-step variant and, if faster per step, a multi-step variant; the
+ * single-step variant and, if faster per step, a multi-step variant, and
+ * records the fastest depth-K variant of every depth with its time; the
  * choice is cached per (device, precision, lattice, species, nx, ny) and
  * handles created later with the same shape start from it.  With a K-step
- * variant lb_rd_step advances K steps per launch except for the last 1 .. K
- * steps (single steps).  times_ms (may be NULL) receives the mean time per
- * time step of each variant (-1 for a variant that does not fit), at most
- * max_times entries; *best the variant used for the bulk of the steps.
- * Synchronises.  lb_rd_set_variant forces a variant (a multi-step one is used
- * together with the current single-step variant; -1 restores the cached or
- * default choice); lb_rd_get_variant returns the variant used for the bulk of
- * the steps. */
+ * variant lb_rd_step advances K steps per launch; with a depth-K variant its
+ * last r + K min(q, 4) steps (nsteps = q K + r) go in launches of 1 .. K
+ * steps, fastest total by the recorded times (untuned: a fixed relative
+ * table), the last one writing rho; with a two-step variant the last step is
+ * single.  times_ms (may be NULL) receives the mean time per time step of
+ * each variant (-1 for a variant that does not fit), at most max_times
+ * entries; *best the variant used for the bulk of the steps.  Synchronises.
+ * lb_rd_set_variant forces a variant (a multi-step one is used together with
+ * the current single-step variant and the recorded or default depth-K
+ * variants of fewer steps; -1 restores the cached or default choice);
+ * lb_rd_get_variant returns the variant used for the bulk of the steps. */
 LB_RD_API int lb_rd_variant_count(int32_t precision, int32_t *count);
 LB_RD_API const char *lb_rd_variant_name(int32_t precision, int32_t variant);
 /* The variants of one handle's configuration: configurations with more than
@@ -276,24 +298,26 @@ LB_RD_API int lb_rd_batch_destroy(lb_rd_batch *b);
  * first lb_rd_batch_step.  Allowed only while the batch time is 0. */
 LB_RD_API int lb_rd_batch_init(lb_rd_batch *b, int32_t idx, const double *rho0, int is_device);
 
-/* Advance every instance by nsteps >= 0 steps (asynchronous).  The final step
- * also writes each instance's densities. */
+/* Advance every instance by nsteps >= 0 steps (asynchronous).  The last
+ * launch also writes each instance's densities: with depth-K launches
+ * (lb_rd_batch_set_steps_per_launch) the call runs nsteps / K launches of K
+ * steps and one launch of the nsteps % K steps left (a single step if one is
+ * left), otherwise its last step is a single step. */
 LB_RD_API int lb_rd_batch_step(lb_rd_batch *b, int64_t nsteps);
 
 /* Steps per captured CUDA graph (an even number >= 2), or 0 to launch every
  * step directly.  Default 64. */
 LB_RD_API int lb_rd_batch_set_graph(lb_rd_batch *b, int32_t steps_per_graph);
 
-/* Time steps per launch: 2 runs the two-step (temporal blocking) kernel over
- * all instances, bitwise the same as two single steps; it needs FP32
- * instances with two state copies and nx a multiple of 256.  4, 5, 6 or 8 run
- * the depth-K kernel over the (band, strip) units of all instances (FP32, two
- * state copies, any nx; bitwise the same as K single steps; the default for
- * such batches: 6 for D2Q9, 4 for D2Q5).  Otherwise EINVAL.  1: one step per
- * launch (the default for other batches).  The last step of every
- * lb_rd_batch_step call is a single step (it writes the densities); the
- * graphs of lb_rd_batch_set_graph then hold steps_per_graph / K launches.
- * Synchronises the batch's stream. */
+/* Time steps per launch, 1 .. 8: 2 runs the two-step (temporal blocking)
+ * kernel over all instances, bitwise the same as two single steps, when the
+ * instances are FP32 with two state copies and nx a multiple of 256; other
+ * values >= 2 (and 2 otherwise) run the depth-K kernel over the (band, strip)
+ * units of all instances (FP32, two state copies, any nx; bitwise the same as
+ * K single steps; the default for such batches: 6 for D2Q9, 4 for D2Q5).
+ * EINVAL if neither applies.  1: one step per launch (the default for other
+ * batches).  The graphs of lb_rd_batch_set_graph hold steps_per_graph / K
+ * launches.  Synchronises the batch's stream. */
 LB_RD_API int lb_rd_batch_set_steps_per_launch(lb_rd_batch *b, int32_t k);
 
 /* Densities and FP64 mass of instance idx at the batch's current time (as
@@ -310,11 +334,11 @@ LB_RD_API int lb_rd_batch_get_time(const lb_rd_batch *b, int64_t *t, int64_t *la
  * memory (two state copies plus the density cache) fits hbm_budget_bytes.
  * Resident requests advance together, steps_per_tick steps at a time (fewer
  * when a request finishes sooner), by launches of the batched kernels over
- * all of them: for FP32 requests with two state copies, K-step launches of the
- * depth-K kernel (K = 6 for D2Q9, 4 for D2Q5) while more than K steps of the
- * tick remain, otherwise one launch per step; the last step of a tick is a
- * single step (it writes the densities).  Requests that arrive meanwhile are
- * admitted between ticks
+ * all of them: for FP32 requests with two state copies, tick / K launches of the
+ * depth-K kernel (K = 6 for D2Q9, 4 for D2Q5) and one launch of the tick % K
+ * steps left (a single step if one is left), otherwise one launch per step;
+ * the last launch of a tick also writes the densities.  Requests that arrive
+ * meanwhile are admitted between ticks
  * as slots and memory free up.  A finished request's densities and mass are
  * copied to host memory and its device memory is released.  Each result is
  * bitwise what a single handle with the same config computes.  Any
@@ -390,8 +414,11 @@ LB_RD_API int lb_rd_server_stats(const lb_rd_server *srv, int64_t *launches, int
  * counts in the message.
  *
  * The first call on a device, with that device current, looks up the
- * array's device address (cudaGetSymbolAddress) and caches it; make that
- * first call before any stream capture.  Every call clears the counter on
+ * array's device address (cudaGetSymbolAddress) and caches it by device
+ * ordinal; make that first call before any stream capture.  Only the CUDA
+ * runtime's primary context is supported: after cudaDeviceReset (or under
+ * another context) the cached address is stale and the entry point must not
+ * be called again in that process.  Every call clears the counter on
  * its stream before the kernel.  All calls share the one array, which keeps
  * the last call's contents: calls whose work overlaps on the GPU (different
  * streams, or several host threads) race on it and must be serialised by the

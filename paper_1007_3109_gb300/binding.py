@@ -51,7 +51,7 @@ class lb_rd_reaction(ctypes.Structure):
 class lb_rd_config(ctypes.Structure):
     _fields_ = [("lattice", c_int32), ("nspecies", c_int32), ("nx", c_int64), ("ny", c_int64),
                 ("tau", c_double * MAX_SPECIES), ("reaction", lb_rd_reaction), ("precision", c_int32),
-                ("track_mass", c_int32), ("streaming", c_int32), ("stream", c_void_p)]
+                ("track_mass", c_int32), ("streaming", c_int32), ("stream", c_void_p), ("tb_depth", c_int32)]
 
 
 _LIB = None
@@ -74,6 +74,8 @@ _SIGNATURES = {
     "lb_rd_set_timing": ([c_void_p, c_int], c_int),
     "lb_rd_kernel_time": ([c_void_p, POINTER(c_double), POINTER(c_int64)], c_int),
     "lb_rd_launch_count": ([c_void_p, POINTER(c_int64)], c_int),
+    "lb_rd_launch_times": ([c_void_p, POINTER(c_double), POINTER(c_int32), POINTER(c_int32), c_int64,
+                            POINTER(c_int64)], c_int),
     "lb_rd_step_noalloc": ([POINTER(lb_rd_config), c_void_p, c_void_p, c_void_p], c_int),
     "lb_rd_variant_count": ([c_int32, POINTER(c_int32)], c_int),
     "lb_rd_variant_name": ([c_int32, c_int32], c_char_p),
@@ -141,10 +143,11 @@ def _ptr(buf, writable: bool = False):
 
 def make_config(lattice="D2Q9", nspecies=1, nx=64, ny=64, tau=(1.0, 1.0), reaction="none", kappa=0.0, F=0.0,
                 k=0.0, precision="fp32", track_mass=False, stream=None, network=None,
-                inplace=False) -> lb_rd_config:
+                inplace=False, tb_depth=0) -> lb_rd_config:
     """Config struct.  ``network`` = (rates, order, change) for
     reaction="mass_action": rate constants per step and the per-step
-    reactant exponents and net changes per species (lists of rows)."""
+    reactant exponents and net changes per species (lists of rows);
+    ``tb_depth`` time steps per launch (0: the autotuner's choice)."""
     cfg = lb_rd_config()
     cfg.lattice = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
     cfg.nspecies = int(nspecies)
@@ -172,6 +175,7 @@ def make_config(lattice="D2Q9", nspecies=1, nx=64, ny=64, tau=(1.0, 1.0), reacti
     cfg.track_mass = 1 if track_mass else 0
     cfg.streaming = 1 if inplace else 0
     cfg.stream = stream
+    cfg.tb_depth = int(tb_depth)
     return cfg
 
 
@@ -256,6 +260,17 @@ def lb_rd_kernel_time(h: int):
     ms, n = c_double(0), c_int64(0)
     _check(lib().lb_rd_kernel_time(h, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def lb_rd_launch_times(h: int, max_launches: int = 1 << 16):
+    """Per timed launch since lb_rd_set_timing(h, True): (ms, steps, variant) lists."""
+    ms = (c_double * max_launches)()
+    steps = (c_int32 * max_launches)()
+    var = (c_int32 * max_launches)()
+    n = c_int64(0)
+    _check(lib().lb_rd_launch_times(h, ms, steps, var, max_launches, ctypes.byref(n)))
+    k = min(n.value, max_launches)
+    return list(ms[:k]), list(steps[:k]), list(var[:k])
 
 
 def lb_rd_launch_count(h: int) -> int:
@@ -540,9 +555,10 @@ class Simulation:
     """Owner of one lb_rd handle (a convenience over the functions above)."""
 
     def __init__(self, lattice="D2Q9", nspecies=1, nx=64, ny=64, tau=(1.0, 1.0), reaction="none", kappa=0.0,
-                 F=0.0, k=0.0, precision="fp32", track_mass=False, stream=None, network=None, inplace=False):
+                 F=0.0, k=0.0, precision="fp32", track_mass=False, stream=None, network=None, inplace=False,
+                 tb_depth=0):
         self.cfg = make_config(lattice, nspecies, nx, ny, tau, reaction, kappa, F, k, precision, track_mass, stream,
-                               network, inplace)
+                               network, inplace, tb_depth)
         self.lattice = lattice
         self.S, self.nx, self.ny = int(nspecies), int(nx), int(ny)
         self.Q = Q_OF[lattice] if isinstance(lattice, str) else (9 if lattice == 0 else 5)

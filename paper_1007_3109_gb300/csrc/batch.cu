@@ -98,7 +98,7 @@ cudaError_t dispatch_batch(int Q, int S, const BatchItem *items, int n, int64_t 
     return cudaErrorInvalidValue;
 }
 
-int64_t pitch_for(int64_t nx) { return (nx + 31) / 32 * 32; }
+int64_t pitch_for(int64_t nx) { return state_pitch(nx); }
 
 size_t align256(size_t n) { return (n + 255) / 256 * 256; }
 
@@ -162,18 +162,18 @@ struct lb_rd_batch {
     int graph_steps = 64;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // by starting parity
     // K steps per launch: K = 2 the two-step kernel (FP32, two state copies,
-    // every nx % strip == 0), K = 4, 6, 8 the depth-K kernel (FP32, two state
-    // copies); tb_graph holds graphs of K-step launches for the current K
+    // every nx % strip == 0), otherwise the depth-K kernel (FP32, two state
+    // copies; also K = 2 when the two-step kernel does not apply); tb_graph
+    // holds graphs of K-step launches for the current K
     bool tb_ok = false;
     int steps_per_launch = 1;
     lbrd::TbwItem *d_tb[2] = {nullptr, nullptr};  // by buffer parity
     int64_t tb_units = 0;
     cudaGraphExec_t tb_graph[2] = {nullptr, nullptr};
     bool deep_ok = false, deep_v16 = false;
-    std::vector<lbrd::DeepItem> deep_base;            // per instance, without buffers
-    lbrd::DeepItem *d_deep[2] = {nullptr, nullptr};  // by buffer parity, planned for deep_K
-    int64_t deep_units = 0;
-    int deep_K = 0;
+    std::vector<lbrd::DeepItem> deep_base;  // per instance, without buffers (rho_out: its density cache)
+    lbrd::DeepItem *d_deep[9][2] = {};      // per steps per launch and buffer parity, planned on first use
+    int64_t deep_units[9] = {};
 };
 
 namespace {
@@ -203,20 +203,17 @@ void drop_graphs(lb_rd_batch *b) {
         }
 }
 
-// One launch of steps_per_launch (>= 2) steps from buffer parity `parity`.
-cudaError_t launch_multi(lb_rd_batch *b, int parity) {
-    if (b->steps_per_launch == 2)
-        return lbrd::launch_batch_tb2(b->d_tb[parity], (int)b->cfgs.size(), b->tb_units, b->Q, b->S, b->stream);
-    return lbrd::launch_batch_deep(b->steps_per_launch, b->Q, b->S, b->deep_v16, b->d_deep[parity],
-                                   (int)b->cfgs.size(), b->deep_units, b->stream);
-}
+// The K-step launches of this batch run the two-step kernel (else the depth-K kernel).
+bool uses_tb2(const lb_rd_batch *b) { return b->steps_per_launch == 2 && b->tb_ok; }
 
-// Plans and uploads the depth-K descriptors of both parities.
+// Plans and uploads the depth-K descriptors of both parities (once per K).
 cudaError_t plan_deep(lb_rd_batch *b, int K) {
+    if (K < 2 || K > 8) return cudaErrorInvalidValue;
+    if (b->deep_units[K] > 0) return cudaSuccess;
     const int n = (int)b->cfgs.size();
     std::vector<lbrd::DeepItem> v = b->deep_base;
     const int64_t units = lbrd::batch_deep_plan(K, b->Q, b->S, b->deep_v16, v.data(), n);
-    if (units < 0) return cudaErrorInvalidValue;
+    if (units <= 0) return cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
     for (int parity = 0; parity < 2 && !e; ++parity) {
         for (int i = 0; i < n; ++i) {
@@ -224,14 +221,27 @@ cudaError_t plan_deep(lb_rd_batch *b, int K) {
             v[i].a.src = parity ? c1 : c0;
             v[i].a.dst = parity ? c0 : c1;
         }
-        if (!b->d_deep[parity]) e = cudaMalloc(&b->d_deep[parity], n * sizeof(lbrd::DeepItem));
-        if (!e) e = cudaMemcpy(b->d_deep[parity], v.data(), n * sizeof(lbrd::DeepItem), cudaMemcpyHostToDevice);
+        if (!b->d_deep[K][parity]) e = cudaMalloc(&b->d_deep[K][parity], n * sizeof(lbrd::DeepItem));
+        if (!e) e = cudaMemcpy(b->d_deep[K][parity], v.data(), n * sizeof(lbrd::DeepItem), cudaMemcpyHostToDevice);
     }
-    if (!e) {
-        b->deep_units = units;
-        b->deep_K = K;
-    }
+    if (!e) b->deep_units[K] = units;
     return e;
+}
+
+// One depth-K launch of K steps from buffer parity `parity`; emit: it also
+// writes every instance's densities.
+cudaError_t launch_deep(lb_rd_batch *b, int K, int parity, bool emit) {
+    cudaError_t e = plan_deep(b, K);
+    if (e) return e;
+    return lbrd::launch_batch_deep(K, b->Q, b->S, b->deep_v16, b->d_deep[K][parity], (int)b->cfgs.size(),
+                                   b->deep_units[K], emit, b->stream);
+}
+
+// One launch of steps_per_launch (>= 2) steps from buffer parity `parity`.
+cudaError_t launch_multi(lb_rd_batch *b, int parity) {
+    if (uses_tb2(b))
+        return lbrd::launch_batch_tb2(b->d_tb[parity], (int)b->cfgs.size(), b->tb_units, b->Q, b->S, b->stream);
+    return launch_deep(b, b->steps_per_launch, parity, false);
 }
 
 }  // namespace
@@ -247,7 +257,8 @@ int lb_rd_batch_destroy(lb_rd_batch *b) {
     cudaFree(b->rho);
     for (auto p : b->d_items) cudaFree(p);
     for (auto p : b->d_tb) cudaFree(p);
-    for (auto p : b->d_deep) cudaFree(p);
+    for (auto &pk : b->d_deep)
+        for (auto p : pk) cudaFree(p);
     cudaFree(b->stage);
     cudaFree(b->partials);
     cudaFree(b->counter);
@@ -386,7 +397,7 @@ int lb_rd_batch_create(const lb_rd_config *cfgs, int32_t n, lb_rd_batch **out) {
         for (int i = 0; i < n; ++i) {
             b->deep_base[i] = lbrd::DeepItem{};
             b->deep_base[i].a = items[i].a;
-            b->deep_base[i].a.rho_out = nullptr;
+            b->deep_base[i].a.rho_out = b->rho + b->rho_off[i];
         }
         // default: the depth-K kernel, K = 6 (D2Q9) or 4 (D2Q5); should its
         // descriptors not be planned (no launch shape for this device), the
@@ -394,6 +405,12 @@ int lb_rd_batch_create(const lb_rd_config *cfgs, int32_t n, lb_rd_batch **out) {
         const int K = b->Q == 9 ? 6 : 4;
         if (!e && plan_deep(b, K) == cudaSuccess) b->steps_per_launch = K;
         cudaGetLastError();  // clear a non-sticky error of the attempt
+    }
+    if (!e && cfgs[0].tb_depth > 0) {  // the caller's steps per launch
+        b->steps_per_launch = 1;
+        const int K = cfgs[0].tb_depth;
+        if (K >= 2 && !(K == 2 && b->tb_ok)) e = plan_deep(b, K);
+        if (!e) b->steps_per_launch = K;
     }
     if (e) {
         int rc = cuda_err(e, "lb_rd_batch_create allocation");
@@ -490,6 +507,36 @@ static int capture_graph(lb_rd_batch *b, int parity, bool two = false) {
     return LB_RD_OK;
 }
 
+// K-step launches (all but the last, in graphs of graph_steps / K launches
+// where they fill one) from the current buffer parity.
+static int run_multi(lb_rd_batch *b, int64_t n_multi) {
+    const int K = b->steps_per_launch;
+    const int per_graph = b->graph_steps / K;  // K-step launches per graph
+    if (per_graph > 0 && n_multi >= per_graph) {
+        const int64_t reps = n_multi / per_graph;
+        for (int64_t r = 0; r < reps; ++r) {
+            if (!b->tb_graph[b->cur]) {  // captured once per starting parity
+                int rc = capture_graph(b, b->cur, true);
+                if (rc) return rc;
+            }
+            cudaError_t e = cudaGraphLaunch(b->tb_graph[b->cur], b->stream);
+            if (e) return cuda_err(e, "graph launch");
+            if (per_graph & 1) b->cur ^= 1;  // an odd number of launches flips the buffers
+        }
+        b->launches += reps * per_graph;
+        b->t += reps * per_graph * K;
+        n_multi -= reps * per_graph;
+    }
+    for (int64_t k = 0; k < n_multi; ++k) {
+        cudaError_t e = launch_multi(b, b->cur);
+        if (e) return cuda_err(e, "batch multi-step kernel");
+        b->cur ^= 1;
+        b->t += K;
+        b->launches++;
+    }
+    return LB_RD_OK;
+}
+
 int lb_rd_batch_step(lb_rd_batch *b, int64_t nsteps) {
     if (!b) return report_error(LB_RD_EINVAL, "batch is NULL");
     if (nsteps < 0) return report_error(LB_RD_EINVAL, "nsteps must be >= 0");
@@ -497,34 +544,28 @@ int lb_rd_batch_step(lb_rd_batch *b, int64_t nsteps) {
         if (!b->inited[i])
             return report_error(LB_RD_EINVAL, "lb_rd_batch_step: instance " + std::to_string(i) + " not initialised");
     if (nsteps == 0) return LB_RD_OK;
-    int64_t body = nsteps - 1;  // the last step also writes the densities
     const int K = b->steps_per_launch;
+    if (K >= 2 && !uses_tb2(b)) {
+        // depth-K launches; the last launch of the call (K steps, or the r =
+        // nsteps % K left over: one depth-r launch, a single step for r = 1)
+        // writes the densities
+        const int64_t q = nsteps / K, r = nsteps % K;
+        int rc = run_multi(b, r == 0 ? q - 1 : q);
+        if (rc) return rc;
+        const int d = r == 0 ? K : (int)r;
+        cudaError_t e = d == 1 ? launch_one(b, b->cur, true) : launch_deep(b, d, b->cur, true);
+        if (e) return cuda_err(e, "batch step kernel");
+        b->cur ^= 1;
+        b->t += d;
+        b->launches++;
+        return LB_RD_OK;
+    }
+    int64_t body = nsteps - 1;  // the last step also writes the densities
     if (K >= 2 && body >= K) {
-        int64_t n_two = body / K;
+        const int64_t n_two = body / K;
         body -= K * n_two;
-        const int per_graph = b->graph_steps / K;  // K-step launches per graph
-        if (per_graph > 0 && n_two >= per_graph) {
-            const int64_t reps = n_two / per_graph;
-            for (int64_t r = 0; r < reps; ++r) {
-                if (!b->tb_graph[b->cur]) {  // captured once per starting parity
-                    int rc = capture_graph(b, b->cur, true);
-                    if (rc) return rc;
-                }
-                cudaError_t e = cudaGraphLaunch(b->tb_graph[b->cur], b->stream);
-                if (e) return cuda_err(e, "graph launch");
-                if (per_graph & 1) b->cur ^= 1;  // an odd number of launches flips the buffers
-            }
-            b->launches += reps * per_graph;
-            b->t += reps * per_graph * K;
-            n_two -= reps * per_graph;
-        }
-        for (int64_t k = 0; k < n_two; ++k) {
-            cudaError_t e = launch_multi(b, b->cur);
-            if (e) return cuda_err(e, "batch multi-step kernel");
-            b->cur ^= 1;
-            b->t += K;
-            b->launches++;
-        }
+        int rc = run_multi(b, n_two);
+        if (rc) return rc;
     }
     if (b->graph_steps > 0 && body >= b->graph_steps) {
         if (!b->graph[b->cur]) {
@@ -552,15 +593,11 @@ int lb_rd_batch_step(lb_rd_batch *b, int64_t nsteps) {
 
 int lb_rd_batch_set_steps_per_launch(lb_rd_batch *b, int32_t k) {
     if (!b) return report_error(LB_RD_EINVAL, "batch is NULL");
-    if (k != 1 && k != 2 && k != 4 && k != 5 && k != 6 && k != 8)
-        return report_error(LB_RD_EINVAL, "steps per launch must be 1, 2, 4, 5, 6 or 8");
-    if (k == 2 && !b->tb_ok)
-        return report_error(LB_RD_EINVAL, "two steps per launch need FP32 instances with two state copies and "
-                                          "nx a multiple of " + std::to_string(lbrd::batch_tb2_strip()));
-    if (k >= 4 && !b->deep_ok)
-        return report_error(LB_RD_EINVAL, "4, 5, 6 or 8 steps per launch need FP32 instances with two state copies");
+    if (k < 1 || k > 8) return report_error(LB_RD_EINVAL, "steps per launch must be in [1, 8]");
+    if (k >= 2 && !b->deep_ok && !(k == 2 && b->tb_ok))
+        return report_error(LB_RD_EINVAL, "2 .. 8 steps per launch need FP32 instances with two state copies");
     cudaStreamSynchronize(b->stream);
-    if (k >= 4 && b->deep_K != k) {
+    if (k >= 2 && !(k == 2 && b->tb_ok)) {
         cudaError_t e = plan_deep(b, k);
         if (e) return cuda_err(e, "lb_rd_batch_set_steps_per_launch");
     }
@@ -568,7 +605,6 @@ int lb_rd_batch_set_steps_per_launch(lb_rd_batch *b, int32_t k) {
     b->steps_per_launch = k;
     return LB_RD_OK;
 }
-
 int lb_rd_batch_moments(lb_rd_batch *b, int32_t idx, double *rho_out, double *mass_out, int is_device) {
     if (!b) return report_error(LB_RD_EINVAL, "batch is NULL");
     if (idx < 0 || idx >= (int)b->cfgs.size()) return report_error(LB_RD_EINVAL, "index out of range");

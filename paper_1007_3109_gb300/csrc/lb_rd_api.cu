@@ -5,6 +5,7 @@
 // mass buffers and a lazily allocated FP64 staging buffer for host transfers.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -37,11 +38,10 @@ int cuda_fail(cudaError_t e, const char *what) {
     } while (0)
 
 constexpr int64_t kMaxSide = 65535;
-constexpr int64_t kPitchAlign = 32;  // elements: 128-byte rows in FP32, 256 in FP64
 
 int lattice_q(int lattice) { return lattice == LB_RD_D2Q9 ? 9 : (lattice == LB_RD_D2Q5 ? 5 : 0); }
 
-int64_t pitch_for(int64_t nx) { return (nx + kPitchAlign - 1) / kPitchAlign * kPitchAlign; }
+int64_t pitch_for(int64_t nx) { return lbrd::state_pitch(nx); }
 
 size_t rho_elem(int prec) { return prec == LB_RD_FP64 ? 8 : 4; }
 
@@ -83,15 +83,28 @@ struct lb_rd_handle {
     int inject_timeout = 0;  // one-shot test switch for the bounded-wait error path
     int variant = 0;      // single-step launch variant of the step kernel
     int tb_variant = -1;  // multi-step (temporal blocking, K steps per launch) variant, or -1
+    // depth-K variants per steps per launch d = 2 .. 8 (-1: none fits) and, once
+    // tuned, their time per step (ms): the launches that cover the last steps of a call
+    int depth_variant[9] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
+    double depth_ms[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    bool depth_tuned = false;
+    std::vector<int> event_steps;    // steps of each timed launch (events[2i], events[2i + 1])
+    std::vector<int> event_variant;  // and its launch variant
     bool general = false; // runs the general kernel
     bool inplace = false; // one state copy, AA pattern (buf[1] unused)
 };
 
 namespace {
 // Autotuner choices per (device, precision, Q, S, nx, ny): single-step
-// variant and multi-step variant (-1 if none is faster).
+// variant, multi-step variant (-1 if none is faster) and the fastest depth-K
+// variant with its time per step for every d = 2 .. 8.
+struct TuneEntry {
+    int variant = 0, tb_variant = -1;
+    int depth_variant[9] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
+    double depth_ms[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+};
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int64_t, int64_t>, std::pair<int, int>> g_tune_cache;
+std::map<std::tuple<int, int, int, int, int64_t, int64_t>, TuneEntry> g_tune_cache;
 
 std::tuple<int, int, int, int, int64_t, int64_t> tune_key(const lb_rd_handle *h) {
     int dev = 0;
@@ -118,6 +131,91 @@ bool variant_fits(const lb_rd_handle *h, int v) {
     if (h->inplace) return h->prec == LB_RD_FP64 || h->cfg.nx % lbrd::kAAVariants[v].sites == 0;
     if (h->general) return h->prec == LB_RD_FP64 || h->cfg.nx % lbrd::kGeneralVariants[v].sites == 0;
     return h->prec != LB_RD_FP32 || h->cfg.nx % lbrd::kF32Variants[v].nx_multiple == 0;
+}
+
+// A variant of the depth-K kernel (it can write the densities of its last level).
+bool is_deep(const lb_rd_handle *h, int v) {
+    return h->prec == LB_RD_FP32 && !h->general && !h->inplace && v >= 0 && lbrd::kF32Variants[v].cache == 4;
+}
+
+// Untuned depth table: per d = 2 .. 8 the first depth-K variant of d steps
+// that fits the grid, in table order.
+void default_depths(lb_rd_handle *h) {
+    for (int d = 0; d < 9; ++d) {
+        h->depth_variant[d] = -1;
+        h->depth_ms[d] = 0.0;
+    }
+    h->depth_tuned = false;
+    if (h->prec != LB_RD_FP32 || h->general || h->inplace) return;
+    for (int v = 0; v < lbrd::kF32VariantCount; ++v) {
+        const int d = lbrd::kF32Variants[v].steps;
+        if (is_deep(h, v) && d >= 2 && d <= 8 && h->depth_variant[d] < 0 && variant_fits(h, v))
+            h->depth_variant[d] = v;
+    }
+}
+
+void apply_tune(lb_rd_handle *h, const TuneEntry &t) {
+    h->variant = t.variant;
+    h->tb_variant = t.tb_variant;
+    bool tuned = false;
+    for (int d = 0; d < 9; ++d) {
+        if (t.depth_variant[d] >= 0) h->depth_variant[d] = t.depth_variant[d];
+        h->depth_ms[d] = t.depth_ms[d];
+        tuned = tuned || t.depth_ms[d] > 0.0;
+    }
+    h->depth_tuned = tuned;
+}
+
+// Launches of one lb_rd_step call: `bulk` launches of K steps, then the
+// launches of `tail` (steps per launch, largest first).  With a depth-K
+// variant the last r + K min(q, 4) steps (nsteps = q K + r) are split by
+// dynamic programming over d = 1 .. K steps per launch, each d at the time of
+// its fastest variant (the autotuner's figures, else a fixed relative table
+// of the depth sweep's shape), so that a call of any length runs close to the
+// per-step rate of the deepest launches and ends on a launch that also writes
+// rho.  Other multi-step variants (two-step kernels, which cannot write rho)
+// keep the last step single, like one-step variants.
+struct LaunchPlan {
+    int64_t bulk = 0;
+    int K = 1;
+    std::vector<int> tail;
+};
+
+LaunchPlan plan_launches(const lb_rd_handle *h, int64_t nsteps) {
+    LaunchPlan p;
+    if (nsteps <= 0) return p;
+    const int K = h->tb_variant >= 0 ? variant_steps(h, h->tb_variant) : 1;
+    if (K == 1 || !is_deep(h, h->tb_variant)) {
+        p.K = K;
+        p.bulk = K > 1 ? (nsteps - 1) / K : 0;
+        for (int64_t n = nsteps - K * p.bulk; n > 0; --n) p.tail.push_back(1);
+        return p;
+    }
+    static const double kRelStep[9] = {0, 3.45, 2.11, 1.49, 1.17, 1.01, 1.00, 1.05, 1.10};
+    double cost[9];
+    bool ok[9];
+    for (int d = 1; d <= 8; ++d) {
+        ok[d] = d == 1 || d == K || (d < K && h->depth_variant[d] >= 0);
+        const double per = h->depth_tuned && h->depth_ms[d] > 0.0 ? h->depth_ms[d] : kRelStep[d];
+        cost[d] = per * d;
+    }
+    const int64_t q = nsteps / K, r = nsteps % K;
+    const int64_t qt = q < 4 ? q : 4;
+    p.K = K;
+    p.bulk = q - qt;
+    const int T = (int)(r + K * qt);
+    std::vector<double> best(T + 1, 1e300);
+    std::vector<int> choice(T + 1, 0);
+    best[0] = 0.0;
+    for (int n = 1; n <= T; ++n)
+        for (int d = 1; d <= K && d <= n; ++d)
+            if (ok[d] && best[n - d] + cost[d] < best[n]) {
+                best[n] = best[n - d] + cost[d];
+                choice[n] = d;
+            }
+    for (int n = T; n > 0; n -= choice[n]) p.tail.push_back(choice[n]);
+    std::sort(p.tail.begin(), p.tail.end(), [](int x, int y) { return x > y; });
+    return p;
 }
 
 cudaError_t launch_step(const lb_rd_handle *h, const lbrd::StepArgs &a, int variant) {
@@ -180,6 +278,12 @@ int lb_rd_check_config(const lb_rd_config *cfg, size_t *bytes) {
         return fail(LB_RD_EINVAL, "streaming: unknown value " + std::to_string(cfg->streaming));
     if (cfg->streaming == LB_RD_STREAM_INPLACE && cfg->precision != LB_RD_FP64 && cfg->precision != LB_RD_FP32)
         return fail(LB_RD_EINVAL, "in-place streaming: FP64 or FP32 storage only");
+    if (cfg->tb_depth < 0 || cfg->tb_depth > 8)
+        return fail(LB_RD_EINVAL, "tb_depth must be in [0, 8] (0: the autotuner's choice)");
+    if (cfg->tb_depth > 1 && (cfg->precision != LB_RD_FP32 || cfg->streaming != LB_RD_STREAM_PINGPONG ||
+                              needs_general(*cfg)))
+        return fail(LB_RD_EINVAL, "tb_depth > 1 needs FP32 storage with two state copies and at most two species "
+                                  "without a mass-action network");
     if (bytes) {
         const int64_t pitch = pitch_for(cfg->nx);
         const size_t st = lbrd::state_plane_bytes(cfg->precision, Q, cfg->nspecies, cfg->ny, pitch);
@@ -254,13 +358,21 @@ int lb_rd_create(const lb_rd_config *cfg, lb_rd_handle **out) {
         lb_rd_destroy(h);
         return rc;
     }
+    default_depths(h);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(tune_key(h));
-        if (it != g_tune_cache.end()) {
-            h->variant = it->second.first;
-            h->tb_variant = it->second.second;
+        if (it != g_tune_cache.end()) apply_tune(h, it->second);
+    }
+    if (cfg->tb_depth == 1) {
+        h->tb_variant = -1;
+    } else if (cfg->tb_depth > 1) {
+        if (h->depth_variant[cfg->tb_depth] < 0) {
+            lb_rd_destroy(h);
+            return fail(LB_RD_EINVAL, "tb_depth " + std::to_string(cfg->tb_depth) + ": no launch variant of that "
+                                      "many steps fits nx = " + std::to_string(cfg->nx));
         }
+        h->tb_variant = h->depth_variant[cfg->tb_depth];
     }
     *out = h;
     return LB_RD_OK;
@@ -363,6 +475,8 @@ int lb_rd_step(lb_rd_handle *h, int64_t nsteps) {
                 LBRD_CUDA(cudaEventRecord(e1, h->stream), "event record");
                 h->events.push_back(e0);
                 h->events.push_back(e1);
+                h->event_steps.push_back(1);
+                h->event_variant.push_back(h->variant);
             }
             h->t += 1;
         }
@@ -372,16 +486,19 @@ int lb_rd_step(lb_rd_handle *h, int64_t nsteps) {
         }
         return LB_RD_OK;
     }
-    // With a K-step variant, all but the last 1 .. K steps go K at a time; the
-    // last launch is always a single step, so that the other state copy holds
-    // f*(t - 1) and rho(t) can be recomputed from it on demand.
-    const int64_t K = h->tb_variant >= 0 ? variant_steps(h, h->tb_variant) : 1;
-    const int64_t n_two = K > 1 ? (nsteps - 1) / K : 0;
-    for (int64_t n = 0; n < n_two + (nsteps - K * n_two); ++n) {
-        const bool two = n < n_two;
+    // K steps per launch for the bulk of the call, then the planned tail; a
+    // last launch of d >= 2 steps writes rho(t) (the other copy then no longer
+    // holds f*(t - 1)), a last single step leaves it to be recomputed on demand
+    // from the other copy (ensure_rho).
+    const LaunchPlan plan = plan_launches(h, nsteps);
+    const int64_t nl = plan.bulk + (int64_t)plan.tail.size();
+    for (int64_t n = 0; n < nl; ++n) {
+        const int d = n < plan.bulk ? plan.K : plan.tail[(size_t)(n - plan.bulk)];
+        const int v = d == 1 ? h->variant : (d == plan.K ? h->tb_variant : h->depth_variant[d]);
+        const bool last = n == nl - 1;
         a.src = h->buf[h->cur];
         a.dst = h->buf[h->cur ^ 1];
-        a.rho_out = nullptr;  // densities are computed on demand (ensure_rho)
+        a.rho_out = last && d >= 2 ? h->rho : nullptr;
         a.mass_out = h->cfg.track_mass ? h->mass : nullptr;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (h->timing) {
@@ -391,16 +508,19 @@ int lb_rd_step(lb_rd_handle *h, int64_t nsteps) {
         }
         a.inject_timeout = h->inject_timeout;
         h->inject_timeout = 0;
-        cudaError_t e = launch_step(h, a, two ? h->tb_variant : h->variant);
+        cudaError_t e = launch_step(h, a, v);
         if (e) return cuda_fail(e, "step kernel");
         h->launches++;
         if (h->timing) {
             LBRD_CUDA(cudaEventRecord(e1, h->stream), "event record");
             h->events.push_back(e0);
             h->events.push_back(e1);
+            h->event_steps.push_back(d);
+            h->event_variant.push_back(v);
         }
         h->cur ^= 1;
-        h->t += two ? K : 1;
+        h->t += d;
+        if (last && d >= 2) h->rho_t = h->t;
     }
     if (nsteps > 0) h->mass_fresh = h->cfg.track_mass != 0;
     return LB_RD_OK;
@@ -547,7 +667,25 @@ int lb_rd_set_timing(lb_rd_handle *h, int enable) {
     LBRD_CUDA(cudaStreamSynchronize(h->stream), "timing sync");
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     h->events.clear();
+    h->event_steps.clear();
+    h->event_variant.clear();
     h->timing = enable != 0;
+    return LB_RD_OK;
+}
+
+int lb_rd_launch_times(lb_rd_handle *h, double *ms, int32_t *steps, int32_t *variant, int64_t max, int64_t *count) {
+    if (!h) return fail(LB_RD_EINVAL, "handle is NULL");
+    if (max < 0) return fail(LB_RD_EINVAL, "max must be >= 0");
+    LBRD_CUDA(cudaStreamSynchronize(h->stream), "timing sync");
+    const int64_t n = (int64_t)h->event_steps.size();
+    for (int64_t i = 0; i < n && i < max; ++i) {
+        float t = 0.f;
+        LBRD_CUDA(cudaEventElapsedTime(&t, h->events[2 * i], h->events[2 * i + 1]), "event elapsed");
+        if (ms) ms[i] = t;
+        if (steps) steps[i] = h->event_steps[(size_t)i];
+        if (variant) variant[i] = h->event_variant[(size_t)i];
+    }
+    if (count) *count = n;
     return LB_RD_OK;
 }
 
@@ -612,8 +750,10 @@ int lb_rd_set_variant(lb_rd_handle *h, int32_t variant) {
     if (variant == -1) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(tune_key(h));
-        h->variant = it != g_tune_cache.end() ? it->second.first : 0;
-        h->tb_variant = it != g_tune_cache.end() ? it->second.second : -1;
+        default_depths(h);
+        h->variant = 0;
+        h->tb_variant = -1;
+        if (it != g_tune_cache.end()) apply_tune(h, it->second);
         return LB_RD_OK;
     }
     if (variant < 0 || variant >= handle_variant_count(h))
@@ -691,7 +831,9 @@ static int autotune_inplace(lb_rd_handle *h, int32_t iters, int32_t *best, doubl
     h->tb_variant = -1;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tune_cache[tune_key(h)] = std::make_pair(h->variant, -1);
+        TuneEntry t;
+        t.variant = h->variant;
+        g_tune_cache[tune_key(h)] = t;
     }
     if (best) *best = h->variant;
     return LB_RD_OK;
@@ -719,6 +861,7 @@ int lb_rd_autotune(lb_rd_handle *h, int32_t iters, int32_t *best, double *times_
     const int n = handle_variant_count(h);
     int best1 = -1, best2 = -1;
     double ms1 = 0.0, ms2 = 0.0;
+    TuneEntry te;
     for (int v = 0; v < n; ++v) {
         if (!variant_fits(h, v)) {  // variant not applicable to this grid
             if (times_ms && v < max_times) times_ms[v] = -1.0;
@@ -750,15 +893,22 @@ int lb_rd_autotune(lb_rd_handle *h, int32_t iters, int32_t *best, double *times_
             best2 = v;
             ms2 = per;
         }
+        if (is_deep(h, v) && steps >= 2 && (te.depth_variant[steps] < 0 || per < te.depth_ms[steps])) {
+            te.depth_variant[steps] = v;
+            te.depth_ms[steps] = per;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    h->variant = best1 >= 0 ? best1 : 0;
-    h->tb_variant = (best2 >= 0 && ms2 < ms1) ? best2 : -1;
+    te.variant = best1 >= 0 ? best1 : 0;
+    te.tb_variant = (best2 >= 0 && ms2 < ms1) ? best2 : -1;
+    te.depth_ms[1] = best1 >= 0 ? ms1 : 0.0;
+    default_depths(h);
+    apply_tune(h, te);
     const int arg = h->tb_variant >= 0 ? h->tb_variant : h->variant;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tune_cache[tune_key(h)] = std::make_pair(h->variant, h->tb_variant);
+        g_tune_cache[tune_key(h)] = te;
     }
     if (best) *best = arg;
     return LB_RD_OK;

@@ -12,6 +12,10 @@ namespace lbrd {
 
 static_assert(kMaxSpecies == LB_RD_MAX_SPECIES && kMaxReactions == LB_RD_MAX_REACTIONS, "capacities must agree");
 
+// Row pitch of every state, density and staging plane: nx rounded up to a
+// multiple of 32 elements (128-byte rows in FP32, 256 in FP64).
+inline int64_t state_pitch(int64_t nx) { return (nx + 31) / 32 * 32; }
+
 // Relaxation rates and reaction constants of a configuration in kernel form:
 // omega_s = 1 / tau_s (0 beyond nspecies) and the network of a mass-action
 // source (zeroed otherwise).
@@ -150,20 +154,22 @@ struct TbwItem {
 };
 int batch_tb2_strip();
 cudaError_t launch_batch_tb2(const TbwItem *items, int n, int64_t total_units, int Q, int S, cudaStream_t st);
-// Batched K-step launches (K = 4, 5, 6 or 8; FP32, two state copies): the
-// depth-K kernel over the (band, strip) units of a list of grids.  Item k's
-// units are [unit_begin, unit_begin + nstrips * ceil(ny / band)), strips of
-// 34 - 2K columns fastest.  batch_deep_plan fills nstrips and band of every
-// item (one band height for the list, chosen for the launch's warp count)
-// and returns the total unit count, or -1 for an unsupported K.  v16: every
-// grid has nx and pitch multiples of 4 (16-byte staging).
+// Batched K-step launches (K = 2 .. 8; FP32, two state copies): the depth-K
+// kernel over the (band, strip) units of a list of grids.  Item k's units are
+// [unit_begin, unit_begin + nstrips * ceil(ny / band)), strips of 34 - 2K
+// columns fastest.  batch_deep_plan fills nstrips and band of every item (one
+// band height for the list, chosen for the launch's warp count) and returns
+// the total unit count, or -1 for an unsupported K.  v16: every grid has nx
+// and pitch multiples of 4 (16-byte staging).  emit: the launch also writes
+// rho(t + K) of every item to its a.rho_out (the last launch of a call).
 struct DeepItem {
     StepArgs a;
     int64_t unit_begin, nstrips, band;
 };
+bool batch_deep_depth_ok(int K);
 int64_t batch_deep_plan(int K, int Q, int S, bool v16, DeepItem *items, int n);
 cudaError_t launch_batch_deep(int K, int Q, int S, bool v16, const DeepItem *items, int n, int64_t total_units,
-                              cudaStream_t st);
+                              bool emit, cudaStream_t st);
 int64_t batch_tiles_x(int64_t nx);
 int64_t batch_tiles(int64_t nx, int64_t ny);
 // mode: 0 FP32 storage, 1 bf16 deviations, 2 fp16 deviations, 3 FP64,

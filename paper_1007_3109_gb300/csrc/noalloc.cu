@@ -23,7 +23,6 @@ int report_error(int code, const std::string &msg);
 // one 256-byte slot that holds the arrival counter.  Every GPU that loads the
 // library holds this array until the process exits.
 constexpr int64_t kNoAllocSlots = 65536;
-constexpr int64_t kPitchAlign = 32;  // same row pitch rule as the handles
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocSlots + 32];
 
 namespace {
@@ -33,7 +32,8 @@ std::map<int, double *> g_scratch_addr;  // device ordinal -> device address of 
 
 // Device address of the scratch array on the current device.  In host code
 // the array's name is only a host-side stand-in, so the address is looked up
-// once per device (with that device current) and cached.
+// once per device (with that device current, in the runtime's primary
+// context) and cached by device ordinal.
 int scratch_on_current_device(double **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -90,13 +90,9 @@ extern "C" int lb_rd_step_noalloc(const lb_rd_config *cfg, const void *state_in,
     a.dst = state_out;
     a.nx = cfg->nx;
     a.ny = cfg->ny;
-    a.pitch = (cfg->nx + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
+    a.pitch = lbrd::state_pitch(cfg->nx);  // the handles' layout (lb_rd_save payload)
     a.plane = cfg->ny * a.pitch;
-    for (int s = 0; s < 2; ++s) a.omega[s] = s < S ? 1.0 / cfg->tau[s] : 0.0;
-    a.rkind = cfg->reaction.kind;
-    a.kappa = cfg->reaction.kappa;
-    a.F = cfg->reaction.F;
-    a.k = cfg->reaction.k;
+    lbrd::fill_reaction(*cfg, a.omega, &a.rkind, &a.kappa, &a.F, &a.k, &a.net);
     a.rho_out = nullptr;
     a.partials = scratch;
     a.counter = reinterpret_cast<unsigned int *>(scratch + kNoAllocSlots);

@@ -8,9 +8,10 @@
 //   2. advances every resident request by one tick of up to steps_per_tick
 //      steps (never past the earliest finishing request): FP32 requests with
 //      two state copies by K-step launches of the depth-K kernel over all
-//      resident requests (K = 6 for D2Q9, 4 for D2Q5) while more than K steps
-//      of the tick remain, the rest one batched launch per step, the last
-//      step of the tick also writing their densities,
+//      resident requests (K = 6 for D2Q9, 4 for D2Q5) and one shorter
+//      depth-K launch for the steps left (a single step if one is left),
+//      other requests one batched launch per step; the tick's last launch
+//      also writes their densities,
 //   3. copies the results of finished requests to host memory, releases
 //      their device memory and wakes pollers.
 // Submit and poll only touch host state under the server mutex.
@@ -204,13 +205,13 @@ int ensure_items(lb_rd_server *s, size_t n) {
 }
 
 int ensure_deep(lb_rd_server *s, size_t n) {
-    if (s->deep_cap >= 2 * n) return LB_RD_OK;
+    if (s->deep_cap >= 3 * n) return LB_RD_OK;
     cudaStreamSynchronize(s->stream);
     cudaFree(s->d_deep);
     cudaFreeHost(s->h_deep);
     s->d_deep = nullptr;
     s->h_deep = nullptr;
-    const size_t cap = 2 * std::max<size_t>(n, 64);
+    const size_t cap = 3 * std::max<size_t>(n, 64);
     if (cudaMalloc(&s->d_deep, cap * sizeof(lbrd::DeepItem)) != cudaSuccess) return LB_RD_ENOMEM;
     if (cudaMallocHost(&s->h_deep, cap * sizeof(lbrd::DeepItem)) != cudaSuccess) return LB_RD_ENOMEM;
     s->deep_cap = cap;
@@ -230,16 +231,21 @@ void run_tick(lb_rd_server *s) {
         act.clear();
         return;
     }
-    // K-step launches: FP32 requests with two state copies, while more than K
-    // steps of the tick remain (the last step is a single step writing rho)
+    // K-step launches: FP32 requests with two state copies run the tick as
+    // q = tick / K depth-K launches and, for the r = tick % K steps left, one
+    // depth-r launch (r >= 2) or one single step (r = 1); the tick's last
+    // launch writes the densities.  Other requests: one launch per step.
     bool any_inplace = false;
     for (Request *r : act) any_inplace = any_inplace || r->cfg.streaming == LB_RD_STREAM_INPLACE;
     const int K = s->Q == 9 ? 6 : 4;
-    int64_t n_multi = (s->mode == 0 && !any_inplace) ? (tick - 1) / K : 0;
+    const bool deep = s->mode == 0 && !any_inplace && tick >= 2;
+    int64_t n_multi = deep ? tick / K : 0;
+    int rem = deep ? (int)(tick % K) : 0;  // steps of the depth-r launch (0: none)
+    if (rem == 1) rem = 0;                 // one single step instead
     bool v16 = true;
     for (Request *r : act) v16 = v16 && r->cfg.nx % 4 == 0 && r->pitch % 4 == 0;
-    int64_t deep_units = 0;
-    if (n_multi > 0 && ensure_deep(s, n) == LB_RD_OK) {
+    int64_t deep_units = 0, rem_units = 0;
+    if ((n_multi > 0 || rem > 0) && ensure_deep(s, n) == LB_RD_OK) {
         for (size_t i = 0; i < n; ++i) {  // parity 0 relative to each request's current copy
             Request *r = act[i];
             const lb_rd_config &c = r->cfg;
@@ -255,21 +261,35 @@ void run_tick(lb_rd_server *s) {
             d.a.k = c.reaction.k;
             d.a.src = r->buf[r->cur];
             d.a.dst = r->buf[r->cur ^ 1];
+            d.a.rho_out = r->rho;
             s->h_deep[i] = d;
         }
-        deep_units = lbrd::batch_deep_plan(K, s->Q, s->cfg.nspecies, v16, s->h_deep, (int)n);
+        if (rem > 0) {  // the depth-r launch follows the n_multi K-step launches
+            const int par = (int)(n_multi & 1);
+            for (size_t i = 0; i < n; ++i) {
+                s->h_deep[2 * n + i] = s->h_deep[i];
+                s->h_deep[2 * n + i].a.src = act[i]->buf[act[i]->cur ^ par];
+                s->h_deep[2 * n + i].a.dst = act[i]->buf[act[i]->cur ^ par ^ 1];
+            }
+            rem_units = lbrd::batch_deep_plan(rem, s->Q, s->cfg.nspecies, v16, s->h_deep + 2 * n, (int)n);
+        }
+        if (n_multi > 0) deep_units = lbrd::batch_deep_plan(K, s->Q, s->cfg.nspecies, v16, s->h_deep, (int)n);
         for (size_t i = 0; i < n; ++i) {  // parity 1: the copies swapped
             s->h_deep[n + i] = s->h_deep[i];
             s->h_deep[n + i].a.src = act[i]->buf[act[i]->cur ^ 1];
             s->h_deep[n + i].a.dst = act[i]->buf[act[i]->cur];
         }
-        if (deep_units > 0)
-            cudaMemcpyAsync(s->d_deep, s->h_deep, 2 * n * sizeof(lbrd::DeepItem), cudaMemcpyHostToDevice, s->stream);
+        if ((n_multi == 0 || deep_units > 0) && (rem == 0 || rem_units > 0))
+            cudaMemcpyAsync(s->d_deep, s->h_deep, 3 * n * sizeof(lbrd::DeepItem), cudaMemcpyHostToDevice, s->stream);
     }
-    if (deep_units <= 0) n_multi = 0;
-    // launches of the tick: n_multi K-step launches, then single steps; each
-    // launch swaps the two copies once
-    const int64_t L = n_multi + (tick - K * n_multi);
+    if ((n_multi > 0 && deep_units <= 0) || (rem > 0 && rem_units <= 0)) {
+        n_multi = 0;  // no plan: one launch per step
+        rem = 0;
+    }
+    const int64_t n_single = tick - K * n_multi - rem;
+    // launches of the tick: n_multi K-step launches, the depth-r launch, then
+    // single steps; each launch swaps the two copies once
+    const int64_t L = n_multi + (rem > 0 ? 1 : 0) + n_single;
     // descriptor sets: [0] even launches, [1] odd launches, [2] the tick's last launch (writes rho)
     int64_t total = 0;
     for (size_t i = 0; i < n; ++i) {
@@ -307,7 +327,11 @@ void run_tick(lb_rd_server *s) {
     const int S = s->cfg.nspecies;
     for (int64_t l = 0; l < L && !e; ++l) {
         if (l < n_multi) {
-            e = lbrd::launch_batch_deep(K, s->Q, S, v16, s->d_deep + (l & 1) * n, (int)n, deep_units, s->stream);
+            e = lbrd::launch_batch_deep(K, s->Q, S, v16, s->d_deep + (l & 1) * n, (int)n, deep_units, l == L - 1,
+                                        s->stream);
+        } else if (l == n_multi && rem > 0) {
+            e = lbrd::launch_batch_deep(rem, s->Q, S, v16, s->d_deep + 2 * n, (int)n, rem_units, l == L - 1,
+                                        s->stream);
         } else {
             const lbrd::BatchItem *items = s->d_items + (l == L - 1 ? 2 : (l & 1)) * n;
             e = lbrd::launch_batch_step(any_inplace ? 4 : s->mode, s->Q, S, items, (int)n, total, s->stream);

@@ -104,6 +104,9 @@ const F32Variant kF32Variants[] = {
     {"deep6v_64_minb4", 64, 6, 4, 4, 6, 4},
     {"deep5v_64_minb4", 64, 5, 4, 4, 5, 4},
     {"deep6v_256_minb1", 256, 6, 1, 4, 6, 4},
+    // three steps per launch (with the others, the last steps of a call)
+    {"deep3v_128_minb3", 128, 3, 3, 4, 3, 4},
+    {"deep3_128_minb3", 128, 3, 3, 4, 3, 1},
 };
 const int kF32VariantCount = sizeof(kF32Variants) / sizeof(kF32Variants[0]);
 

@@ -50,6 +50,8 @@ cudaError_t launch_step_f32_deep(int v, int Q, int S, const StepArgs &a, cudaStr
         case 26: return dispatch_deep<6, 2, 4, 4, true>(Q, S, a, st);
         case 27: return dispatch_deep<5, 2, 4, 4, true>(Q, S, a, st);
         case 28: return dispatch_deep<6, 8, 4, 1, true>(Q, S, a, st);
+        case 29: return dispatch_deep<3, 4, 4, 3, true>(Q, S, a, st);
+        case 30: return dispatch_deep<3, 4, 4, 3>(Q, S, a, st);
         default: return cudaErrorInvalidValue;
     }
 }

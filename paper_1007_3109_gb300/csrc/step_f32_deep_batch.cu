@@ -8,28 +8,51 @@ namespace lbrd {
 namespace {
 
 // Batched launch shapes per K: the single-grid choices (K = 4, 5: six warps,
-// two blocks per SM; K = 6, 8: four warps, two blocks per SM; K = 5, 8 with
-// the pulls from earlier rows first).
+// two blocks per SM; K = 6, 7, 8: four warps, two blocks per SM; K = 5, 7, 8
+// with the pulls from earlier rows first; K = 2, 3, which cover the last steps
+// of a call or a tick: four warps, four and three blocks per SM).
 template <int Q, int S, int K, bool V16>
 struct BatchShape;
 template <int Q, int S, bool V16>
+struct BatchShape<Q, S, 2, V16> : DeepKernel<Q, S, 2, 4, 4, 4, V16, true> {
+    static constexpr int NW = 4;
+    static constexpr int MINB = 4;
+    static constexpr bool PP = false;
+};
+template <int Q, int S, bool V16>
+struct BatchShape<Q, S, 3, V16> : DeepKernel<Q, S, 3, 4, 4, 3, V16, true> {
+    static constexpr int NW = 4;
+    static constexpr int MINB = 3;
+    static constexpr bool PP = false;
+};
+template <int Q, int S, bool V16>
 struct BatchShape<Q, S, 4, V16> : DeepKernel<Q, S, 4, 6, 4, 2, V16, true> {
     static constexpr int NW = 6;
+    static constexpr int MINB = 2;
     static constexpr bool PP = false;
 };
 template <int Q, int S, bool V16>
 struct BatchShape<Q, S, 5, V16> : DeepKernel<Q, S, 5, 6, 4, 2, V16, true, true> {
     static constexpr int NW = 6;
+    static constexpr int MINB = 2;
     static constexpr bool PP = true;
 };
 template <int Q, int S, bool V16>
 struct BatchShape<Q, S, 6, V16> : DeepKernel<Q, S, 6, 4, 4, 2, V16, true> {
     static constexpr int NW = 4;
+    static constexpr int MINB = 2;
     static constexpr bool PP = false;
+};
+template <int Q, int S, bool V16>
+struct BatchShape<Q, S, 7, V16> : DeepKernel<Q, S, 7, 4, 4, 2, V16, true, true> {
+    static constexpr int NW = 4;
+    static constexpr int MINB = 2;
+    static constexpr bool PP = true;
 };
 template <int Q, int S, bool V16>
 struct BatchShape<Q, S, 8, V16> : DeepKernel<Q, S, 8, 4, 4, 2, V16, true, true> {
     static constexpr int NW = 4;
+    static constexpr int MINB = 2;
     static constexpr bool PP = true;
 };
 
@@ -57,15 +80,15 @@ int64_t plan_batch(DeepItem *items, int n) {
 }
 
 template <int Q, int S, int K, bool V16>
-cudaError_t launch_batch(const DeepItem *items, int n, int64_t total_units, cudaStream_t st) {
+cudaError_t launch_batch(const DeepItem *items, int n, int64_t total_units, bool emit, cudaStream_t st) {
     using BS = BatchShape<Q, S, K, V16>;
     unsigned full = 0;
     cudaError_t e = BS::get(&full);
     if (e != cudaSuccess) return e;
     const int64_t nwarps = (int64_t)full * BS::NW;
     const unsigned grid = total_units < nwarps ? (unsigned)((total_units + BS::NW - 1) / BS::NW) : full;
-    step_deep_kernel<Q, S, K, BS::NW, 4, 2, V16, true, BS::PP>
-        <<<grid, BS::NW * 32, BS::smem, st>>>(StepArgs{}, 0, 0, 0, items, n, total_units);
+    step_deep_kernel<Q, S, K, BS::NW, 4, BS::MINB, V16, true, BS::PP>
+        <<<grid, BS::NW * 32, BS::smem, st>>>(StepArgs{}, 0, 0, 0, items, n, total_units, emit ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -79,37 +102,48 @@ int64_t plan_qs(int Q, int S, DeepItem *items, int n) {
 }
 
 template <int K, bool V16>
-cudaError_t launch_qs(int Q, int S, const DeepItem *items, int n, int64_t total_units, cudaStream_t st) {
-    if (Q == 9 && S == 1) return launch_batch<9, 1, K, V16>(items, n, total_units, st);
-    if (Q == 9 && S == 2) return launch_batch<9, 2, K, V16>(items, n, total_units, st);
-    if (Q == 5 && S == 1) return launch_batch<5, 1, K, V16>(items, n, total_units, st);
-    if (Q == 5 && S == 2) return launch_batch<5, 2, K, V16>(items, n, total_units, st);
+cudaError_t launch_qs(int Q, int S, const DeepItem *items, int n, int64_t total_units, bool emit, cudaStream_t st) {
+    if (Q == 9 && S == 1) return launch_batch<9, 1, K, V16>(items, n, total_units, emit, st);
+    if (Q == 9 && S == 2) return launch_batch<9, 2, K, V16>(items, n, total_units, emit, st);
+    if (Q == 5 && S == 1) return launch_batch<5, 1, K, V16>(items, n, total_units, emit, st);
+    if (Q == 5 && S == 2) return launch_batch<5, 2, K, V16>(items, n, total_units, emit, st);
     return cudaErrorInvalidValue;
+}
+
+template <int K>
+cudaError_t launch_v(int Q, int S, bool v16, const DeepItem *items, int n, int64_t total_units, bool emit,
+                     cudaStream_t st) {
+    return v16 ? launch_qs<K, true>(Q, S, items, n, total_units, emit, st)
+               : launch_qs<K, false>(Q, S, items, n, total_units, emit, st);
 }
 
 }  // namespace
 
+bool batch_deep_depth_ok(int K) { return K >= 2 && K <= 8; }
+
 int64_t batch_deep_plan(int K, int Q, int S, bool v16, DeepItem *items, int n) {
     switch (K) {
+        case 2: return v16 ? plan_qs<2, true>(Q, S, items, n) : plan_qs<2, false>(Q, S, items, n);
+        case 3: return v16 ? plan_qs<3, true>(Q, S, items, n) : plan_qs<3, false>(Q, S, items, n);
         case 4: return v16 ? plan_qs<4, true>(Q, S, items, n) : plan_qs<4, false>(Q, S, items, n);
         case 5: return v16 ? plan_qs<5, true>(Q, S, items, n) : plan_qs<5, false>(Q, S, items, n);
         case 6: return v16 ? plan_qs<6, true>(Q, S, items, n) : plan_qs<6, false>(Q, S, items, n);
+        case 7: return v16 ? plan_qs<7, true>(Q, S, items, n) : plan_qs<7, false>(Q, S, items, n);
         case 8: return v16 ? plan_qs<8, true>(Q, S, items, n) : plan_qs<8, false>(Q, S, items, n);
         default: return -1;
     }
 }
 
 cudaError_t launch_batch_deep(int K, int Q, int S, bool v16, const DeepItem *items, int n, int64_t total_units,
-                              cudaStream_t st) {
+                              bool emit, cudaStream_t st) {
     switch (K) {
-        case 4: return v16 ? launch_qs<4, true>(Q, S, items, n, total_units, st)
-                           : launch_qs<4, false>(Q, S, items, n, total_units, st);
-        case 5: return v16 ? launch_qs<5, true>(Q, S, items, n, total_units, st)
-                           : launch_qs<5, false>(Q, S, items, n, total_units, st);
-        case 6: return v16 ? launch_qs<6, true>(Q, S, items, n, total_units, st)
-                           : launch_qs<6, false>(Q, S, items, n, total_units, st);
-        case 8: return v16 ? launch_qs<8, true>(Q, S, items, n, total_units, st)
-                           : launch_qs<8, false>(Q, S, items, n, total_units, st);
+        case 2: return launch_v<2>(Q, S, v16, items, n, total_units, emit, st);
+        case 3: return launch_v<3>(Q, S, v16, items, n, total_units, emit, st);
+        case 4: return launch_v<4>(Q, S, v16, items, n, total_units, emit, st);
+        case 5: return launch_v<5>(Q, S, v16, items, n, total_units, emit, st);
+        case 6: return launch_v<6>(Q, S, v16, items, n, total_units, emit, st);
+        case 7: return launch_v<7>(Q, S, v16, items, n, total_units, emit, st);
+        case 8: return launch_v<8>(Q, S, v16, items, n, total_units, emit, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -17,7 +17,11 @@
 //   * level K is stored to HBM.
 // Level m is valid on lanes m - 1 .. 32 - m (one halo column lost on each
 // side per level), so a warp writes 34 - 2K columns, and from iteration 2K of
-// its band on (the first 2K iterations fill the pipeline).  Each level is the
+// its band on (the first 2K iterations fill the pipeline).  With `emit` set
+// the launch also writes rho(t + K) = sum_i f_i,s of level K (the pre-collision
+// density of Eq. relax at the new time) to the grid's density plane, 4 bytes
+// per species and site: the last launch of a call leaves the density cache
+// current without a separate pass.  Each level is the
 // fused step of the one-step kernels (tb::collide_site): K levels give the
 // bits of K single steps.  PP variants take the pulls of levels 2 .. K from
 // the rows of earlier iterations (e_iy >= 0) at the start of an iteration,
@@ -79,7 +83,7 @@ __host__ __device__ __forceinline__ int64_t wrap_mod(int64_t a, int64_t n) {
 template <int Q, int S, int K, int NW, int NS, int MINB, bool V16, bool BATCH, bool PP>
 __global__ void __launch_bounds__(NW * 32, MINB)
     step_deep_kernel(StepArgs a, int64_t nstrips, int64_t nbands, int64_t band, const DeepItem *__restrict__ items,
-                     int nitems, int64_t total_units) {
+                     int nitems, int64_t total_units, int emit) {
     using L = Lattice<Q>;
     constexpr int SQ = S * Q;
     constexpr int CW = V16 ? 40 : 34;  // staged columns of a warp row
@@ -93,7 +97,10 @@ __global__ void __launch_bounds__(NW * 32, MINB)
     float *ring = smem + (size_t)w * NS * kRow;
     const unsigned ring_s = static_cast<unsigned>(__cvta_generic_to_shared(ring));
     SegArgs g;
-    if (!BATCH) load_seg(a, g);
+    if (!BATCH) {
+        load_seg(a, g);
+        if (!emit) g.rho_out = nullptr;
+    }
     double acc[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[s] = 0.0;
@@ -106,6 +113,7 @@ __global__ void __launch_bounds__(NW * 32, MINB)
         if constexpr (BATCH) {
             while (it + 1 < nitems && items[it + 1].unit_begin <= u) ++it;
             load_seg(items[it].a, g);
+            if (!emit) g.rho_out = nullptr;
             local = u - items[it].unit_begin;
             ns = items[it].nstrips;
             bh = items[it].band;
@@ -250,6 +258,7 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                     for (int s = 0; s < S; ++s) {
 #pragma unroll
                         for (int i = 0; i < Q; ++i) dst[(int64_t)(s * Q + i) * g.plane + y * g.pitch + x] = f[s][i];
+                        if (g.rho_out) static_cast<float *>(g.rho_out)[(int64_t)s * g.plane + y * g.pitch + x] = rho[s];
                         sum[s] += rho[s];
                     }
                 }
@@ -318,7 +327,7 @@ cudaError_t launch_deep(const StepArgs &a, cudaStream_t st) {
     const int64_t units = nstrips * nbands;
     const unsigned grid = units < nwarps ? (unsigned)((units + NW - 1) / NW) : full;
     step_deep_kernel<Q, S, K, NW, NS, MINB, V16, false, PP>
-        <<<grid, NW * 32, DK::smem, st>>>(a, nstrips, nbands, band, nullptr, 0, 0);
+        <<<grid, NW * 32, DK::smem, st>>>(a, nstrips, nbands, band, nullptr, 0, 0, a.rho_out != nullptr);
     return cudaGetLastError();
 }
 

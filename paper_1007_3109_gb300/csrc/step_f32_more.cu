@@ -17,7 +17,7 @@ cudaError_t launch_step_f32_variant_b(int v, int Q, int S, const StepArgs &a, cu
             return per_tile ? cudaErrorInvalidValue : launch_step_f32_tb2(v - 14, Q, S, a, st);
         case 28: case 29: case 30: case 31: case 32: case 33: case 34: case 35: case 36: case 37:
         case 38: case 39: case 40: case 41: case 42: case 43: case 44: case 45: case 46: case 47:
-        case 48: case 49: case 50: case 51: case 52: case 53: case 54: case 55: case 56:
+        case 48: case 49: case 50: case 51: case 52: case 53: case 54: case 55: case 56: case 57: case 58:
             return per_tile ? cudaErrorInvalidValue : launch_step_f32_deep(v - 28, Q, S, a, st);
         default: return cudaErrorInvalidValue;
     }

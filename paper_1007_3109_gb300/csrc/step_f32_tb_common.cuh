@@ -43,6 +43,7 @@ __device__ __forceinline__ void collide_site(const Args &a, float (&f)[S][Q], fl
 struct SegArgs {
     const void *src;
     void *dst;
+    void *rho_out;  // rho of the stored level ([s][y][pitch] float), or null
     int64_t nx, ny, pitch, plane;
     float omega[2];
     int rkind;
@@ -52,6 +53,7 @@ struct SegArgs {
 __device__ __forceinline__ void load_seg(const StepArgs &a, SegArgs &g) {
     g.src = a.src;
     g.dst = a.dst;
+    g.rho_out = a.rho_out;
     g.nx = a.nx;
     g.ny = a.ny;
     g.pitch = a.pitch;

@@ -75,6 +75,11 @@ def _cfg(**kw):
     (dict(lattice=7), "lattice"),
     (dict(precision=9), "precision"),
     (dict(reaction=5), "reaction"),
+    (dict(tb_depth=9), "tb_depth"),
+    (dict(tb_depth=-1), "tb_depth"),
+    (dict(tb_depth=4, precision="fp64"), "tb_depth > 1"),
+    (dict(tb_depth=2, inplace=True), "tb_depth > 1"),
+    (dict(tb_depth=6, precision="fp32_bf16dev"), "tb_depth > 1"),
 ])
 def test_config_validation_rejects(lib, kw, msg):
     with pytest.raises(B.LbRdError) as ei:
@@ -99,6 +104,10 @@ def test_config_validation_accepts_and_sizes(lib):
     assert n64 > n
     nh = B.lb_rd_check_config(_cfg(precision="fp32_bf16dev"))
     assert nh < n
+    # steps per launch do not change the memory (the last field of the struct reaches the library)
+    for d in range(9):
+        assert B.lb_rd_check_config(_cfg(tb_depth=d)) == n
+    assert B.lb_rd_check_config(_cfg(tb_depth=1, precision="fp64")) == n64
 
 
 def test_server_and_batch_reject_bad_configs_on_the_host(lib):
@@ -119,7 +128,8 @@ def test_variant_table_on_the_host(lib):
     names = [B.lb_rd_variant_name("fp32", v) for v in range(n)]
     assert len(set(names)) == n and names[0] == "64x2_minb4"
     assert any(x.startswith("bulk") for x in names) and any(x.startswith("tb2") for x in names)
-    assert sorted(B.variant_steps(x) for x in names if x.startswith("deep")) == [1, 2, 2, 4, 4, 4, 4, 4, 4, 4, 4, 5, 5, 5, 5, 6, 6, 6, 6, 6, 6, 6, 6, 7, 8, 8, 8, 8, 8]
+    assert sorted(B.variant_steps(x) for x in names if x.startswith("deep")) == \
+        [1, 2, 2, 3, 3, 4, 4, 4, 4, 4, 4, 4, 4, 5, 5, 5, 5, 6, 6, 6, 6, 6, 6, 6, 6, 7, 8, 8, 8, 8, 8]
     assert B.lb_rd_variant_count("fp64") == 1
 
 

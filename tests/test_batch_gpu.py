@@ -164,15 +164,18 @@ def test_batch_two_steps_per_launch_equals_single_handles(lat, graph, steps):
 
 
 @pytest.mark.parametrize("lat", ["D2Q9", "D2Q5"])
-@pytest.mark.parametrize("K", [4, 5, 6, 8])
+@pytest.mark.parametrize("K", [2, 3, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("staging", ["16-byte", "4-byte"])
 @pytest.mark.parametrize("graph", [0, 8, 12])
 def test_batch_k_steps_per_launch_equals_single_handles(lat, K, staging, graph):
-    """K = 4, 6, 8 steps per launch run the depth-K kernel over the (band,
-    strip) units of all instances (ragged strips, bands of a few rows); each
-    instance gives the bits of a single handle.  All nx multiples of 4: the
-    16-byte staging; otherwise 4-byte copies.  Graph 12: an odd number of
-    K-step launches per graph for K = 4 and 8."""
+    """K = 2 .. 8 steps per launch run the depth-K kernel over the (band,
+    strip) units of all instances (ragged strips, bands of a few rows; K = 2
+    here too, as not every nx is a multiple of 256); each call of 21 steps
+    runs 21 // K launches of K steps and one of the 21 % K left (a single
+    step for one), the last writing the densities; each instance gives the
+    bits of a single handle.  All nx multiples of 4: the 16-byte staging;
+    otherwise 4-byte copies.  Graph 12: an odd number of K-step launches per
+    graph for K = 4 and 8."""
     shapes = [(64, 48), (100, 37), (36, 70), (8, 3), (256, 16)]
     if staging == "4-byte":
         shapes += [(70, 9), (33, 20)]
@@ -190,21 +193,22 @@ def test_batch_k_steps_per_launch_equals_single_handles(lat, K, staging, graph):
             rho, _ = b.moments(j)
             ref_rho, _ = _single(c, _rho0(c, j), 2 * steps)
             np.testing.assert_array_equal(rho, ref_rho, err_msg=f"instance {j}")
-    # one init launch per instance; per call 20 // K launches of K steps, then 20 % K + 1 single steps
-    assert launches == len(cfgs) + 2 * (20 // K + 20 % K + 1)
+    # one init launch per instance; per call 21 // K launches of K steps and one for the 21 % K left
+    assert launches == len(cfgs) + 2 * (steps // K + (1 if steps % K else 0))
 
 
 def test_batch_steps_per_launch_switch():
     cfgs = _configs("fp32")  # includes nx not a multiple of 256
     with B.Batch(cfgs) as b:
-        with pytest.raises(B.LbRdError):
-            b.set_steps_per_launch(2)
+        b.set_steps_per_launch(2)  # the depth-K kernel of two steps (the two-step kernel needs nx % 256 == 0)
         b.set_steps_per_launch(1)
         b.set_steps_per_launch(6)  # the depth-K kernel takes any nx
-        for k in (0, 3, 7, 16):
+        b.set_steps_per_launch(3)
+        for k in (0, 9, 16, -1):
             with pytest.raises(B.LbRdError):
                 b.set_steps_per_launch(k)
     ip = [dict(c, inplace=True) for c in _configs("fp32")[:2]]
     with B.Batch(ip) as b:
-        with pytest.raises(B.LbRdError):
-            b.set_steps_per_launch(4)  # in-place instances: one state copy
+        for k in (2, 4):
+            with pytest.raises(B.LbRdError):
+                b.set_steps_per_launch(k)  # in-place instances: one state copy

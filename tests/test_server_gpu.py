@@ -71,10 +71,10 @@ def test_results_identical_alone_and_in_the_mix():
 
 @pytest.mark.parametrize("tick", [5, 16, 64])
 def test_d2q5_k_step_ticks_equal_single_handles(tick):
-    """A D2Q5 server: ticks longer than K = 4 steps advance the resident
-    requests by four-step launches of the depth-K kernel (nx % 4 != 0 among
-    them: 4-byte staging for the whole tick), then single steps; every result
-    is bitwise a single handle's."""
+    """A D2Q5 server: ticks advance the resident requests by four-step
+    launches of the depth-K kernel (nx % 4 != 0 among them: 4-byte staging
+    for the whole tick) and one launch of the steps left; every result is
+    bitwise a single handle's."""
     sides = [(64, 41), (36, 17), (70, 9), (128, 30)]
     reqs = []
     for j, (side, steps) in enumerate(sides):
@@ -90,6 +90,28 @@ def test_d2q5_k_step_ticks_equal_single_handles(tick):
             np.testing.assert_array_equal(rho, ref_rho)
         if tick > 5:
             assert B.lb_rd_server_stats(srv)["launches"] < sum(r[2] for r in reqs) // 2
+    finally:
+        B.lb_rd_server_destroy(srv)
+
+
+@pytest.mark.parametrize("tick,launches", [(64, 11), (13, 3), (6, 1), (5, 1), (1, 1)])
+def test_d2q9_tick_launches(tick, launches):
+    """One D2Q9 request of `tick` steps is one tick: tick // 6 six-step
+    launches and one launch of the tick % 6 steps left (a single step when
+    one is left), the last writing the densities: a 64-step tick is ten
+    six-step launches and one four-step launch, with no single step.  The
+    result is bitwise a single handle's."""
+    kw, rho0, _ = _request(3, 96, 1, tick)
+    srv = B.lb_rd_server_create(hbm_budget_bytes=1 << 30, max_slots=4, steps_per_tick=tick)
+    try:
+        t = B.lb_rd_submit(srv, B.make_config(**kw), rho0, tick)
+        rc, rho, mass, _ = _wait(srv, t, 2, kw["nx"])
+        assert rc == B.LB_RD_OK
+        ref_rho, ref_mass = _alone(kw, rho0, tick)
+        np.testing.assert_array_equal(rho, ref_rho)
+        np.testing.assert_allclose(mass, ref_mass, rtol=1e-12)
+        st = B.lb_rd_server_stats(srv)
+        assert (st["ticks"], st["launches"]) == (1, launches)
     finally:
         B.lb_rd_server_destroy(srv)
 

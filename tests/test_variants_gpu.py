@@ -1,7 +1,7 @@
 """Launch variants and the autotuner.
 
 Every FP32 launch variant (tile shape, register budget, cache policy, TMA
-bulk-copy staging, temporal blocking of 2, 4, 5, 6, 7 or 8 steps per launch)
+bulk-copy staging, temporal blocking of 2 .. 8 steps per launch)
 performs the same per-site operations in the same order, so their states
 must agree bit for bit; the autotuner must not advance or change the
 simulation state.
@@ -67,13 +67,14 @@ def test_every_fp32_variant_is_bitwise_identical(grid):
                                   ("D2Q9", 2, 12, 5, "gray_scott"), ("D2Q5", 2, 44, 13, "linear")],
                          ids=lambda g: f"{g[0]}-S{g[1]}-{g[2]}x{g[3]}-{g[4]}")
 def test_k_step_variants_over_step_counts(grid):
-    """deep<K>_ variants advance K steps per launch and finish with 1 .. K
-    single steps: every step count gives the bits of single steps (ragged
-    last strip, bands of a few rows)."""
+    """deep<K>_ variants advance K steps per launch and cover the last steps
+    of a call with launches of fewer steps: every step count gives the bits of
+    single steps (ragged last strip, bands of a few rows), and the densities
+    the last launch writes equal those of single steps."""
     lat, S, nx, ny, reac = grid
     names = [B.lb_rd_variant_name("fp32", v) for v in range(B.lb_rd_variant_count("fp32"))]
     deep = [v for v, n in enumerate(names) if n.startswith("deep")]
-    assert sorted({B.variant_steps(names[v]) for v in deep}) == [1, 2, 4, 5, 6, 7, 8]
+    assert sorted({B.variant_steps(names[v]) for v in deep}) == [1, 2, 3, 4, 5, 6, 7, 8]
     assert any(re.match(r"deep\dvp?_", names[v]) for v in deep)
     for steps in (1, 2, 7, 8, 9, 17, 33):
         ref = _run(lat, S, nx, ny, reac, 0, steps=steps)
@@ -86,6 +87,70 @@ def test_k_step_variants_over_step_counts(grid):
             np.testing.assert_array_equal(f, ref[2], err_msg=f"{names[v]} steps={steps}")
             np.testing.assert_array_equal(rho, ref[0], err_msg=f"{names[v]} steps={steps}")
             np.testing.assert_allclose(mass, ref[1], rtol=1e-6, err_msg=f"{names[v]} steps={steps}")
+
+
+@pytest.mark.parametrize("nx,ny", [(64, 48), (70, 37)])
+def test_k_step_calls_end_on_a_launch_that_writes_rho(nx, ny):
+    """With a depth-K variant, the launches of a call (per
+    lb_rd_launch_times) add up to its steps and run at most one single step
+    (the plan minimises the estimated time: several single steps never are);
+    a call of 20 = 4 x 5 steps runs no single step.  When the last launch has
+    two or more steps it writes rho(t), so lb_rd_moments then launches only
+    the export; after a last single step rho(t) is recomputed from the other
+    copy (one more launch).  Densities, masses and distributions equal those
+    of single steps after every call."""
+    rho0 = inputs.rho0_square(nx, ny, seed=44, side=max(2, min(nx, ny) // 3))
+    kw = dict(lattice="D2Q9", nspecies=2, nx=nx, ny=ny, tau=[0.8, 0.65], reaction="gray_scott", F=0.04, k=0.06,
+              precision="fp32", track_mass=True)
+    names = [B.lb_rd_variant_name("fp32", v) for v in range(B.lb_rd_variant_count("fp32"))]
+    for name in ("deep6v_128_minb2", "deep8_128_minb2", "deep4_128_minb3"):
+        if name.startswith("deep6v") and nx % 4:
+            continue
+        with B.Simulation(**kw) as sim, B.Simulation(**kw) as ref:
+            sim.set_variant(names.index(name))
+            sim.init(rho0)
+            ref.init(rho0)
+            B.lb_rd_set_timing(sim.h, True)
+            prev = 0
+            for n in (2, 7, 20, 33, 1, 13):
+                sim.step(n)
+                ref.step(n)
+                _, steps, var = B.lb_rd_launch_times(sim.h)
+                new, prev = steps[prev:], len(steps)
+                assert sum(new) == n and new.count(1) <= 1, (name, n, new)
+                assert all(B.variant_steps(names[v]) == d for v, d in zip(var, steps)), (name, n)
+                if n == 20:
+                    assert 1 not in new, (name, new)
+                l0 = B.lb_rd_launch_count(sim.h)
+                rho, mass = sim.moments()
+                launched = B.lb_rd_launch_count(sim.h) - l0
+                assert launched == (1 if new[-1] >= 2 else 2), (name, n, new, launched)
+                rref, mref = ref.moments()
+                np.testing.assert_array_equal(rho, rref, err_msg=f"{name} after {n}")
+                np.testing.assert_allclose(mass, mref, rtol=1e-6)
+                np.testing.assert_array_equal(sim.distributions(), ref.distributions())
+
+
+def test_tb_depth_config_field():
+    """lb_rd_config.tb_depth selects the steps per launch at creation: a
+    depth-K variant of that many steps (the same bits as single steps), 1 a
+    single-step variant; EINVAL where no variant of that depth fits."""
+    nx, ny = 68, 21
+    rho0 = inputs.rho0_square(nx, ny, seed=45, side=7)
+    kw = dict(lattice="D2Q9", nspecies=2, nx=nx, ny=ny, tau=[0.8, 0.65], reaction="gray_scott", F=0.04, k=0.06,
+              precision="fp32")
+    with B.Simulation(**kw, tb_depth=1) as ref:
+        ref.init(rho0).step(23)
+        want = ref.moments()[0]
+        assert B.variant_steps(B.lb_rd_handle_variant_name(ref.h, B.lb_rd_get_variant(ref.h))) == 1
+    for d in range(2, 9):
+        with B.Simulation(**kw, tb_depth=d) as sim:
+            assert B.variant_steps(B.lb_rd_handle_variant_name(sim.h, B.lb_rd_get_variant(sim.h))) == d
+            sim.init(rho0).step(23)
+            np.testing.assert_array_equal(sim.moments()[0], want, err_msg=f"tb_depth {d}")
+    with pytest.raises(B.LbRdError) as ei:
+        B.Simulation(**dict(kw, nx=70), tb_depth=6)  # depth 6 only with 16-byte staging (nx % 4 == 0)
+    assert ei.value.status == B.LB_RD_EINVAL
 
 
 @pytest.mark.parametrize("lat", ["D2Q9", "D2Q5"])
