@@ -49,9 +49,11 @@ def _check_two_calls(kw, rho0, warm=3):
             expected_mass.append(sim.mass())
             expected_states.append(_state_bytes(sim.save(), S, nx, ny, precision))
 
-    # caller-owned device buffers (allocated by the caller, not by the library)
+    # caller-owned device buffers (allocated by the caller, not by the library); the
+    # row padding (pitch beyond nx) is never written, so the destination starts
+    # zeroed like a handle's buffers and the whole buffers can be compared
     a = torch.frombuffer(bytearray(start), dtype=torch.uint8).cuda()
-    b = torch.empty_like(a)
+    b = torch.zeros_like(a)
     mass = torch.zeros(S, dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
     for call, (src, dst) in enumerate([(a, b), (b, a)]):
