@@ -300,9 +300,10 @@ def serving_mode(args):
     steps = np.maximum(1, np.round(req["steps"] * args.steps_scale)).astype(np.int64)
     sides, scales = req["side"], req["scale"]
     ssu = 2 * sides.astype(np.float64) ** 2 * steps
-    capacity = args.capacity_mlups * 1e6  # SSU/s the GPU sustains (the step benchmark's figure)
+    capacity = args.capacity_mlups * 1e6  # SSU/s the server sustains on this stream (a saturated run's figure)
     rate = args.load * capacity / ssu.mean()
-    arrivals = req["arrival_s"] / rate  # the seeded unit-rate stream, rescaled
+    # the seeded unit-rate stream, rescaled; load 0: every request submitted at once (saturation)
+    arrivals = req["arrival_s"] / rate if args.load > 0 else np.zeros(nreq)
     F, k = w["reaction"]["F"], w["reaction"]["k"]
 
     def cfg(j, server=True):
@@ -336,6 +337,35 @@ def serving_mode(args):
     stats = B.lb_rd_server_stats(srv)
     B.lb_rd_server_destroy(srv)
     makespan = (max(ends) - starts0) / 1e9
+    fifo = None
+    if not args.no_fifo:
+        fifo = fifo_loop(args, B, cfg, sides, rho0s, steps, arrivals, nreq)
+    total = ssu.sum()
+    line = {"metric": "MLUPS", "value": total / makespan / 1e6, "unit": "MLUPS (species-site updates/s / 1e6)",
+            "n_gpus": 1, "steps": int(steps.sum()), "warmup": 0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "gs_serving", "requests": nreq, "steps_scale": args.steps_scale,
+                       "load": args.load, "capacity_mlups": args.capacity_mlups, "budget_gb": args.budget_gb,
+                       "slots": args.slots, "steps_per_tick": args.tick,
+                       "arrival_rate_per_s": rate if args.load > 0 else None,
+                       "inplace_requests": int(sum(1 for j in range(nreq) if cfg(j)["inplace"])),
+                       "total_ssu": float(total), "makespan_s": makespan},
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "max": float(np.max(lat))},
+            "server": stats, "gpu_launches": stats["launches"]}
+    if fifo is not None:
+        lat_fifo, makespan_fifo = fifo
+        line["fifo_plain_loop"] = {"value": total / makespan_fifo / 1e6, "makespan_s": makespan_fifo,
+                                   "latency_s": {"p50": float(np.percentile(lat_fifo, 50)),
+                                                 "p99": float(np.percentile(lat_fifo, 99))},
+                                   "handles": "autotuned per grid side before the replay (untimed)"}
+    print(json.dumps(line))
+    return 0
+
+
+def fifo_loop(args, B, cfg, sides, rho0s, steps, arrivals, nreq):
+    """The serving stream replayed against a serial first-in first-out loop
+    of plain handles: (latencies, makespan)."""
     # serial FIFO plain loop on the same stream; every grid side tuned beforehand
     # (untimed), so each handle starts from the autotuner's choice for its
     # shape, K-step variants included
@@ -354,23 +384,7 @@ def serving_mode(args):
             sim.init(rho0s[j]).step(int(steps[j]))
             sim.moments()
         lat_fifo.append(time.perf_counter() - t0 - arrivals[j])
-    makespan_fifo = time.perf_counter() - t0
-    total = ssu.sum()
-    line = {"metric": "MLUPS", "value": total / makespan / 1e6, "unit": "MLUPS (species-site updates/s / 1e6)",
-            "n_gpus": 1, "steps": int(steps.sum()), "warmup": 0, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "gs_serving", "requests": nreq, "steps_scale": args.steps_scale,
-                       "load": args.load, "capacity_mlups": args.capacity_mlups, "budget_gb": args.budget_gb,
-                       "slots": args.slots, "steps_per_tick": args.tick, "arrival_rate_per_s": rate,
-                       "inplace_requests": int(sum(1 for j in range(nreq) if cfg(j)["inplace"]))},
-            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                          "max": float(np.max(lat))},
-            "fifo_plain_loop": {"value": total / makespan_fifo / 1e6,
-                                "latency_s": {"p50": float(np.percentile(lat_fifo, 50)),
-                                              "p99": float(np.percentile(lat_fifo, 99))}},
-            "server": stats, "gpu_launches": stats["launches"]}
-    print(json.dumps(line))
-    return 0
+    return lat_fifo, time.perf_counter() - t0
 
 
 def truncation_mode(args):
@@ -661,6 +675,7 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=64.0)
     ap.add_argument("--slots", type=int, default=64)
     ap.add_argument("--tick", type=int, default=64)
+    ap.add_argument("--no-fifo", action="store_true", help="serving mode: skip the FIFO plain-loop baseline")
     ap.add_argument("--fifo-tune-iters", type=int, default=1,
                     help="serving mode: autotuner iterations per grid side for the FIFO loop's handles")
     args = ap.parse_args()

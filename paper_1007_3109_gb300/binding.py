@@ -296,17 +296,17 @@ def lb_rd_variant_name(precision, variant: int) -> str:
 
 def variant_steps(name: str) -> int:
     """Time steps per launch of an FP32 launch variant, from its name: tb2*_
-    variants two, deep<K>_, deep<K>v_ and deep<K>vp_ variants K, the others
-    one."""
-    m = re.match(r"deep(\d+)v?p?_", name)
+    variants two, deep<K><letters>_ variants K, the others one."""
+    m = re.match(r"deep(\d+)[a-z]*_", name)
     if m:
         return int(m.group(1))
     return 2 if name.startswith("tb2") else 1
 
 
-def lb_rd_autotune(h: int, iters: int = 20, max_times: int = 64):
-    """Returns (best variant, mean ms per time step of every variant; -1 where
-    a variant does not fit the grid)."""
+def lb_rd_autotune(h: int, iters: int = 20, max_times: int = 0):
+    """Returns (best variant, mean ms per time step of every variant of the
+    handle; -1 where a variant does not fit the grid)."""
+    max_times = max_times or lb_rd_handle_variant_count(h)
     best = c_int32(0)
     times = (c_double * max_times)()
     _check(lib().lb_rd_autotune(h, int(iters), ctypes.byref(best), times, max_times))

@@ -99,6 +99,7 @@ cudaError_t launch_step_f32_variant_b(int v, int Q, int S, const StepArgs &a, cu
 cudaError_t launch_step_f32_bulk(int v, int Q, int S, const StepArgs &a, cudaStream_t st);
 cudaError_t launch_step_f32_tb2(int v, int Q, int S, const StepArgs &a, cudaStream_t st);
 cudaError_t launch_step_f32_deep(int v, int Q, int S, const StepArgs &a, cudaStream_t st);
+cudaError_t launch_step_f32_pair(int v, int Q, int S, const StepArgs &a, cudaStream_t st);
 StepShape step_shape_f32(int64_t nx, int64_t ny);
 cudaError_t launch_step_f32(int Q, int S, const StepArgs &a, cudaStream_t st);
 cudaError_t launch_init_f32(int Q, int S, const InitArgs &a, cudaStream_t st);

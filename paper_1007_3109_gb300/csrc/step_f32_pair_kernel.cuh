@@ -1,0 +1,300 @@
+// FP32 temporal blocking to depth K with two columns per lane: the depth-K
+// scheme of step_f32_deep_kernel.cuh (K time steps of Eq. relax per pass over
+// HBM, intermediate levels in registers, a warp walking a strip of columns
+// down a band of rows) on a 64-column warp window.
+//
+// Lane l holds the adjacent columns xb + 2l and xb + 2l + 1.  A pull from the
+// left neighbour (e_ix = +1) takes the lane's own first column for its second
+// one and the second column of lane l - 1 (a warp shuffle) for its first one;
+// e_ix = -1 mirrors it.  So a level costs one shuffle per shifted direction
+// for two sites, and each level loses one column per side of a 64-column
+// window instead of a 32-column one: with the left halo HL (K rounded up to
+// an even count) a warp writes 64 - 2 HL columns, e.g. 56 of 64 at K = 4
+// against 26 of 32 for one column per lane.  The price is twice the carried
+// registers per level, which bounds K.
+//
+//   * level 0 (f*(t)): rows staged per warp by cp.async in 16-byte chunks
+//     (nx and the row pitch multiples of 4): the window's 64 columns start at
+//     xb (even), inside the 17 aligned chunks from a0 = xb rounded down to a
+//     multiple of 4; lanes 0-15 copy chunk `lane` of the even planes, lanes
+//     16-31 chunk `lane - 16` of the odd planes, lane p < S Q chunk 16 of
+//     plane p.  Waits only on the warp's own copy groups.
+//   * level 1 pulls the lane's column pair of every plane from the staged row
+//     of its e_iy (one 8-byte shared load) and shifts it like the levels
+//     above; level m > 1 pulls from level m - 1 carried in registers (the row
+//     of this iteration for e_iy = -1, the previous one for e_iy = 0, the one
+//     before for e_iy = +1), exactly as the one-column kernel.
+//   * level 1 is valid on window columns 1 .. 62 and level m on m .. 63 - m;
+//     level K is stored for columns HL .. 63 - HL (8-byte stores), and with
+//     `emit` rho(t + K) of level K as well.
+// Each level is tb::collide_site per column: K levels give the bits of K
+// single steps.  Units, bands, the periodic wrap and the FP64 mass reduction
+// are those of the one-column kernel.
+#pragma once
+
+#include "step_f32_deep_kernel.cuh"
+
+namespace lbrd {
+
+namespace {
+
+template <int K>
+struct PairGeom {
+    static constexpr int HL = (K + 1) / 2 * 2;  // left (and right) halo columns of the window, even
+    static constexpr int WO = 64 - 2 * HL;      // output columns per warp, even
+};
+
+template <int Q, int S, int K, int NW, int NS, int MINB, bool BATCH, bool PP>
+__global__ void __launch_bounds__(NW * 32, MINB)
+    step_pair_kernel(StepArgs a, int64_t nstrips, int64_t nbands, int64_t band, const DeepItem *__restrict__ items,
+                     int nitems, int64_t total_units, int emit) {
+    using L = Lattice<Q>;
+    constexpr int SQ = S * Q;
+    constexpr int CW = 68;          // staged columns of a warp row: 17 chunks of four
+    constexpr int kRow = SQ * CW;   // one staged row, all planes
+    constexpr int P = NS - 3;       // rows staged ahead of use
+    constexpr int HL = PairGeom<K>::HL;
+    constexpr int WO = PairGeom<K>::WO;
+    constexpr int KC = K > 1 ? K - 1 : 1;
+    static_assert(K >= 1 && K <= 8 && NS >= 4 && WO > 0, "depth 1 .. 8, at least four staged rows");
+    extern __shared__ __align__(16) float smem[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float *ring = smem + (size_t)w * NS * kRow;
+    const unsigned ring_s = static_cast<unsigned>(__cvta_generic_to_shared(ring));
+    SegArgs g;
+    if (!BATCH) {
+        load_seg(a, g);
+        if (!emit) g.rho_out = nullptr;
+    }
+    double acc[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) acc[s] = 0.0;
+    const int64_t nwarps = (int64_t)gridDim.x * NW;
+    const int64_t units = BATCH ? total_units : nstrips * nbands;
+    const int cch = lane & 15, cpar = lane >> 4;  // copy role: chunk, plane parity
+    int it = 0;
+    for (int64_t u = (int64_t)blockIdx.x * NW + w; u < units; u += nwarps) {
+        int64_t local = u, ns = nstrips, bh = band;
+        if constexpr (BATCH) {
+            while (it + 1 < nitems && items[it + 1].unit_begin <= u) ++it;
+            load_seg(items[it].a, g);
+            if (!emit) g.rho_out = nullptr;
+            local = u - items[it].unit_begin;
+            ns = items[it].nstrips;
+            bh = items[it].band;
+        }
+        const float *__restrict__ src = static_cast<const float *>(g.src);
+        float *__restrict__ dst = static_cast<float *>(g.dst);
+        const int64_t b = local / ns, strip = local - b * ns;
+        const int64_t y0 = b * bh;
+        const int64_t ly = g.ny - y0 < bh ? g.ny - y0 : bh;
+        const int64_t xb = strip * WO - HL;            // first window column (even)
+        const int64_t a0 = xb - wrap_mod(xb, 4);       // first staged column
+        const int o = (int)(xb - a0);                  // staged column of xb: 0 or 2
+        const int64_t offA = (int64_t)cpar * g.plane + wrap_mod(a0 + 4 * cch, g.nx);
+        const int64_t offB = (int64_t)(lane < SQ ? lane : 0) * g.plane + wrap_mod(a0 + 64, g.nx);
+        const int64_t nrows = ly + 2 * K;
+        int64_t yl = wrap_mod(y0 - K, g.ny);
+        auto stage = [&](int64_t j, int slot) {
+            if (j < nrows) {
+                const float *row = src + yl * g.pitch;
+                const unsigned d = ring_s + (unsigned)(slot * kRow + cpar * CW + 4 * cch) * 4u;
+                const float *sp = row + offA;
+                int64_t pl2 = 2 * g.plane;
+                asm volatile("" : "+l"(pl2));  // no plane multiples kept live across the row loop
+#pragma unroll
+                for (int r = 0; r < (SQ + 1) / 2; ++r)
+                    if (cpar + 2 * r < SQ) cp_async16(d + (unsigned)(2 * r * CW * 4), sp + r * pl2);
+                if (lane < SQ) cp_async16(ring_s + (unsigned)(slot * kRow + lane * CW + 64) * 4u, row + offB);
+            }
+            yl = yl + 1 == g.ny ? 0 : yl + 1;
+            cp_async_commit();
+        };
+#pragma unroll
+        for (int jj = 0; jj < P; ++jj) stage(jj, jj);
+        // carried levels 1 .. K - 1, both columns: E0 the previous row's
+        // e_iy = 0 components, P1 / P2 the e_iy = +1 components of the
+        // previous row and of the one before
+        float E0[KC][2][S][Q], P1[KC][2][S][Q], P2[KC][2][S][Q];
+#pragma unroll
+        for (int m = 0; m < KC; ++m)
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int s = 0; s < S; ++s)
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) E0[m][c][s][i] = P1[m][c][s][i] = P2[m][c][s][i] = 0.f;
+        float sum[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) sum[s] = 0.f;
+        int sl = 0;
+        for (int64_t j = 0; j < nrows; ++j) {
+            stage(j + P, sl + P >= NS ? sl + P - NS : sl + P);
+            cp_async_wait<P>();
+            __syncwarp();
+            const int s1 = sl == 0 ? NS - 1 : sl - 1, s2 = s1 == 0 ? NS - 1 : s1 - 1;
+            // staged rows of iterations j - 2, j - 1, j: pulled with e_iy = +1, 0, -1
+            const float *rows0[3] = {ring + s2 * kRow + o + 2 * lane, ring + s1 * kRow + o + 2 * lane,
+                                     ring + sl * kRow + o + 2 * lane};
+            float f0[S][Q], f1[S][Q], rho0[S], rho1[S];
+            float hp0[KC][S][Q], hp1[KC][S][Q];
+            if constexpr (PP) {
+#pragma unroll
+                for (int m = 1; m < K; ++m)
+#pragma unroll
+                    for (int s = 0; s < S; ++s)
+#pragma unroll
+                        for (int i = 0; i < Q; ++i)
+                            if (L::ey(i) >= 0) {
+                                const float v0 = L::ey(i) == 0 ? E0[m - 1][0][s][i] : P2[m - 1][0][s][i];
+                                const float v1 = L::ey(i) == 0 ? E0[m - 1][1][s][i] : P2[m - 1][1][s][i];
+                                hp0[m - 1][s][i] = L::ex(i) > 0   ? __shfl_up_sync(kFullMask, v1, 1)
+                                                   : L::ex(i) < 0 ? v1
+                                                                  : v0;
+                                hp1[m - 1][s][i] = L::ex(i) > 0   ? v0
+                                                   : L::ex(i) < 0 ? __shfl_down_sync(kFullMask, v0, 1)
+                                                                  : v1;
+                                if (L::ey(i) > 0) {
+                                    P2[m - 1][0][s][i] = P1[m - 1][0][s][i];
+                                    P2[m - 1][1][s][i] = P1[m - 1][1][s][i];
+                                }
+                            }
+            }
+            // level 1 from the staged rows
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const float2 v = *reinterpret_cast<const float2 *>(rows0[1 - L::ey(i)] + (s * Q + i) * CW);
+                    f0[s][i] = L::ex(i) > 0 ? __shfl_up_sync(kFullMask, v.y, 1) : (L::ex(i) < 0 ? v.y : v.x);
+                    f1[s][i] = L::ex(i) > 0 ? v.x : (L::ex(i) < 0 ? __shfl_down_sync(kFullMask, v.x, 1) : v.y);
+                }
+            collide_site<Q, S>(g, f0, rho0);
+            collide_site<Q, S>(g, f1, rho1);
+#pragma unroll
+            for (int m = 1; m < K; ++m) {  // level m + 1 from level m (carried index m - 1)
+                if constexpr (PP) {
+#pragma unroll
+                    for (int s = 0; s < S; ++s)
+#pragma unroll
+                        for (int i = 0; i < Q; ++i) {
+                            if (L::ey(i) > 0) {
+                                P1[m - 1][0][s][i] = f0[s][i];
+                                P1[m - 1][1][s][i] = f1[s][i];
+                            } else if (L::ey(i) == 0) {
+                                E0[m - 1][0][s][i] = f0[s][i];
+                                E0[m - 1][1][s][i] = f1[s][i];
+                            }
+                            const float v0 = f0[s][i], v1 = f1[s][i];
+                            f0[s][i] = L::ey(i) >= 0 ? hp0[m - 1][s][i]
+                                       : L::ex(i) > 0 ? __shfl_up_sync(kFullMask, v1, 1)
+                                       : L::ex(i) < 0 ? v1
+                                                      : v0;
+                            f1[s][i] = L::ey(i) >= 0 ? hp1[m - 1][s][i]
+                                       : L::ex(i) > 0 ? v0
+                                       : L::ex(i) < 0 ? __shfl_down_sync(kFullMask, v0, 1)
+                                                      : v1;
+                        }
+                } else {
+                    float h0[S][Q], h1[S][Q];
+#pragma unroll
+                    for (int s = 0; s < S; ++s)
+#pragma unroll
+                        for (int i = 0; i < Q; ++i) {
+                            const float v0 = L::ey(i) < 0    ? f0[s][i]
+                                             : L::ey(i) == 0 ? E0[m - 1][0][s][i]
+                                                             : P2[m - 1][0][s][i];
+                            const float v1 = L::ey(i) < 0    ? f1[s][i]
+                                             : L::ey(i) == 0 ? E0[m - 1][1][s][i]
+                                                             : P2[m - 1][1][s][i];
+                            h0[s][i] = L::ex(i) > 0 ? __shfl_up_sync(kFullMask, v1, 1) : (L::ex(i) < 0 ? v1 : v0);
+                            h1[s][i] = L::ex(i) > 0 ? v0 : (L::ex(i) < 0 ? __shfl_down_sync(kFullMask, v0, 1) : v1);
+                        }
+#pragma unroll
+                    for (int s = 0; s < S; ++s)
+#pragma unroll
+                        for (int i = 0; i < Q; ++i) {
+                            if (L::ey(i) > 0) {
+                                P2[m - 1][0][s][i] = P1[m - 1][0][s][i];
+                                P2[m - 1][1][s][i] = P1[m - 1][1][s][i];
+                                P1[m - 1][0][s][i] = f0[s][i];
+                                P1[m - 1][1][s][i] = f1[s][i];
+                            } else if (L::ey(i) == 0) {
+                                E0[m - 1][0][s][i] = f0[s][i];
+                                E0[m - 1][1][s][i] = f1[s][i];
+                            }
+                            f0[s][i] = h0[s][i];
+                            f1[s][i] = h1[s][i];
+                        }
+                }
+                collide_site<Q, S>(g, f0, rho0);
+                collide_site<Q, S>(g, f1, rho1);
+            }
+            if (j >= 2 * K) {  // level K of row y0 + j - 2K: window columns HL .. 63 - HL
+                const int64_t x = xb + 2 * lane;
+                if (lane >= HL / 2 && lane < (HL + WO) / 2 && x < g.nx) {
+                    const int64_t y = y0 + j - 2 * K;
+                    int64_t pl = g.plane;
+                    asm volatile("" : "+l"(pl));  // no plane multiples kept live across the row loop
+                    float *dp = dst + y * g.pitch + x;
+#pragma unroll
+                    for (int s = 0; s < S; ++s) {
+#pragma unroll
+                        for (int i = 0; i < Q; ++i)
+                            *reinterpret_cast<float2 *>(dp + (s * Q + i) * pl) = make_float2(f0[s][i], f1[s][i]);
+                        if (g.rho_out)
+                            *reinterpret_cast<float2 *>(static_cast<float *>(g.rho_out) + s * pl + y * g.pitch +
+                                                        x) = make_float2(rho0[s], rho1[s]);
+                        sum[s] += rho0[s] + rho1[s];
+                    }
+                }
+            }
+            __syncwarp();  // every lane has read slot j - 2 before iteration j + 1 stages into it
+            sl = sl + 1 == NS ? 0 : sl + 1;
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s) acc[s] += (double)sum[s];
+    }
+    cp_async_wait<0>();
+    if (a.mass_out) block_mass_reduce<S, NW * 32>(acc, a.partials, a.counter, a.mass_out);
+}
+
+template <int Q, int S, int K, int NW, int NS, int MINB, bool BATCH, bool PP = false>
+struct PairKernel {
+    static constexpr size_t smem = (size_t)NW * NS * S * Q * 68 * sizeof(float);
+    static cudaError_t get(unsigned *full) {
+        auto kern = step_pair_kernel<Q, S, K, NW, NS, MINB, BATCH, PP>;
+        static std::atomic<bool> configured[64] = {};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev < 64 && !configured[dev].load()) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            configured[dev].store(true);
+        }
+        *full = persistent_blocks(kern, NW * 32, INT64_MAX, smem);
+        return cudaSuccess;
+    }
+};
+
+template <int Q, int S, int K, int NW, int NS, int MINB, bool PP>
+cudaError_t launch_pair(const StepArgs &a, cudaStream_t st) {
+    constexpr int WO = PairGeom<K>::WO;
+    if (a.nx % 4 != 0 || a.pitch % 4 != 0) return cudaErrorInvalidValue;
+    using PK = PairKernel<Q, S, K, NW, NS, MINB, false, PP>;
+    unsigned full = 0;
+    cudaError_t e = PK::get(&full);
+    if (e != cudaSuccess) return e;
+    const int64_t nstrips = (a.nx + WO - 1) / WO;
+    const int64_t nwarps = (int64_t)full * NW;
+    const int64_t nb = choose_bands(K, nstrips, a.ny, nwarps);
+    const int64_t band = (a.ny + nb - 1) / nb, nbands = (a.ny + band - 1) / band;
+    const int64_t units = nstrips * nbands;
+    const unsigned grid = units < nwarps ? (unsigned)((units + NW - 1) / NW) : full;
+    step_pair_kernel<Q, S, K, NW, NS, MINB, false, PP>
+        <<<grid, NW * 32, PK::smem, st>>>(a, nstrips, nbands, band, nullptr, 0, 0, a.rho_out != nullptr);
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace lbrd

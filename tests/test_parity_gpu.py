@@ -249,3 +249,49 @@ def test_gs_8192_sampled_windows(lat, variant):
         assert np.all(rel_err(got, ref) <= 1e-5), (y0, x0, rel_err(got, ref))
     # whole-field invariant at full size: mass change equals the summed source
     assert np.all(np.isfinite(mass))
+
+
+# Reduced storage after 13 steps: the bounds of the 150-step runs of the
+# noisy square (test_reduced_gpu.py), calibrated on a CPU emulation of the
+# storage scheme as max |error| over the species' scale (its largest value in
+# the field); rounding errors grow with the step count, so they bound 13
+# steps too.  The scale here is max |rho0_s| over the whole grid: a window of
+# v-noise only (|v| ~ 1e-3) holds deviations whose 16-bit rounding is small in
+# absolute terms but not against that window's own maximum.  In-place (one
+# state copy) is bitwise the two-copy FP32 path.
+STORAGE_TOL = {"fp32_bf16dev": 6e-4, "fp32_fp16dev": 1e-4, "fp32_inplace": 1e-5}
+
+
+@pytest.mark.parametrize("lat", ["D2Q9", "D2Q5"])
+@pytest.mark.parametrize("storage", ["fp32_bf16dev", "fp32_fp16dev", "fp32_inplace"])
+def test_gs_8192_sampled_windows_other_storage(lat, storage):
+    """The gs_8192 workload at full size (8192^2, two species) in the other
+    storage formats, each with the autotuner's launch variant as the
+    benchmark would run it: FP32 rho* + bf16 or fp16 deviations, and FP32
+    with one state copy streamed in place.  At that size the launches run
+    other tile and persistent-grid counts than any small grid; the oracle on
+    windows with a margin of T + 1 gives the exact reference inside (see
+    test_gs_8192_sampled_windows), compared at the storage's tolerance."""
+    w = inputs.WORKLOADS["gs_8192"]
+    n, T = w["nx"], 13
+    rho0 = inputs.initial_density("gs_8192")
+    scale = np.max(np.abs(rho0), axis=(1, 2))
+    taus = [float(t) for t in orc.tau_from_diffusion(np.array(w["D"]))]
+    reac = Reaction("gray_scott", F=w["reaction"]["F"], k=w["reaction"]["k"])
+    precision = "fp32" if storage == "fp32_inplace" else storage
+    with B.Simulation(lat, 2, n, n, taus, "gray_scott", F=reac.F, k=reac.k, precision=precision,
+                      inplace=storage == "fp32_inplace", track_mass=True) as sim:
+        sim.init(rho0)
+        B.lb_rd_autotune(sim.h, iters=2)
+        sim.step(T)
+        rho, mass = sim.moments()
+    px, py = inputs.spot_positions(w["seed"], n, n, 4)
+    m = T + 1
+    for (y0, x0) in [(0, 0), (n - 20, n - 30), (int(py[0]), int(px[0])), (int(py[1]) - 10, int(px[1]) + 5), (4000, 123)]:
+        hw = 48
+        sub0 = np.ascontiguousarray(_window(rho0, y0 - m, x0 - m, hw + 2 * m, hw + 2 * m))
+        ref = oracle_density(lat, taus, reac, sub0, T)[:, m:m + hw, m:m + hw]
+        got = _window(rho, y0, x0, hw, hw)
+        err = np.max(np.abs(got - ref), axis=(1, 2)) / scale
+        assert np.all(err <= STORAGE_TOL[storage]), (storage, y0, x0, err)
+    assert np.all(np.isfinite(mass))

@@ -46,10 +46,10 @@ def test_every_fp32_variant_is_bitwise_identical(grid):
         name = B.lb_rd_variant_name("fp32", v)
         out = _run(lat, S, nx, ny, reac, v)
         if out is None:
-            # bulk-copy variants and deep<K>v(p)_ variants (16-byte staging) need nx % 4 == 0, two-step variants
+            # bulk-copy variants and deep<K>v*_ variants (16-byte staging) need nx % 4 == 0, two-step variants
             # (tb2[iw]_<threads>x<strip>_...) nx % strip == 0; the other deep<K>_ variants fit any grid
             m = re.match(r"tb2[iw]?_\d+x(\d+)_", name)
-            assert ((name.startswith("bulk") or re.match(r"deep\dvp?_", name)) and nx % 4) or \
+            assert ((name.startswith("bulk") or re.match(r"deep\dv", name)) and nx % 4) or \
                 (m and nx % int(m.group(1))), name
             continue
         ran += 1
@@ -75,13 +75,13 @@ def test_k_step_variants_over_step_counts(grid):
     names = [B.lb_rd_variant_name("fp32", v) for v in range(B.lb_rd_variant_count("fp32"))]
     deep = [v for v, n in enumerate(names) if n.startswith("deep")]
     assert sorted({B.variant_steps(names[v]) for v in deep}) == [1, 2, 3, 4, 5, 6, 7, 8]
-    assert any(re.match(r"deep\dvp?_", names[v]) for v in deep)
+    assert any(re.match(r"deep\dv", names[v]) for v in deep)
     for steps in (1, 2, 7, 8, 9, 17, 33):
         ref = _run(lat, S, nx, ny, reac, 0, steps=steps)
         for v in deep:
             out = _run(lat, S, nx, ny, reac, v, steps=steps)
             if out is None:  # 16-byte staging needs nx % 4 == 0
-                assert re.match(r"deep\dvp?_", names[v]) and nx % 4, names[v]
+                assert re.match(r"deep\dv", names[v]) and nx % 4, names[v]
                 continue
             rho, mass, f = out
             np.testing.assert_array_equal(f, ref[2], err_msg=f"{names[v]} steps={steps}")
