@@ -117,6 +117,8 @@ const F32Variant kF32Variants[] = {
     {"deep6vwp_128_minb1", 128, 6, 1, 4, 6, 4},
     {"deep4vwp_64_minb4_s5", 64, 4, 4, 4, 4, 4},
     {"deep3vwp_128_minb2_s5", 128, 3, 2, 4, 3, 4},
+    {"deep5vwp_128_minb2_s5", 128, 5, 2, 4, 5, 4},
+    {"deep5vw_128_minb2_s5", 128, 5, 2, 4, 5, 4},
 };
 const int kF32VariantCount = sizeof(kF32Variants) / sizeof(kF32Variants[0]);
 

@@ -29,6 +29,8 @@ cudaError_t launch_step_f32_pair(int v, int Q, int S, const StepArgs &a, cudaStr
         case 6: return dispatch_pair<6, 4, 4, 1, true>(Q, S, a, st);
         case 7: return dispatch_pair<4, 2, 5, 4, true>(Q, S, a, st);
         case 8: return dispatch_pair<3, 4, 5, 2, true>(Q, S, a, st);
+        case 9: return dispatch_pair<5, 4, 5, 2, true>(Q, S, a, st);
+        case 10: return dispatch_pair<5, 4, 5, 2, false>(Q, S, a, st);
         default: return cudaErrorInvalidValue;
     }
 }

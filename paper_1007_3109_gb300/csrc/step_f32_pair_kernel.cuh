@@ -85,19 +85,21 @@ __global__ void __launch_bounds__(NW * 32, MINB)
         }
         const float *__restrict__ src = static_cast<const float *>(g.src);
         float *__restrict__ dst = static_cast<float *>(g.dst);
+        // rows and columns fit 32 bits (sides <= 65535); plane offsets need 64
+        const int nx = (int)g.nx, ny = (int)g.ny;
         const int64_t b = local / ns, strip = local - b * ns;
-        const int64_t y0 = b * bh;
-        const int64_t ly = g.ny - y0 < bh ? g.ny - y0 : bh;
-        const int64_t xb = strip * WO - HL;            // first window column (even)
-        const int64_t a0 = xb - wrap_mod(xb, 4);       // first staged column
-        const int o = (int)(xb - a0);                  // staged column of xb: 0 or 2
-        const int64_t offA = (int64_t)cpar * g.plane + wrap_mod(a0 + 4 * cch, g.nx);
-        const int64_t offB = (int64_t)(lane < SQ ? lane : 0) * g.plane + wrap_mod(a0 + 64, g.nx);
-        const int64_t nrows = ly + 2 * K;
-        int64_t yl = wrap_mod(y0 - K, g.ny);
-        auto stage = [&](int64_t j, int slot) {
+        const int y0 = (int)(b * bh);
+        const int ly = ny - y0 < (int)bh ? ny - y0 : (int)bh;
+        const int xb = (int)(strip * WO) - HL;  // first window column (even)
+        const int a0 = xb - (int)wrap_mod(xb, 4);  // first staged column
+        const int o = xb - a0;                     // staged column of xb: 0 or 2
+        const int64_t offA = (int64_t)cpar * g.plane + wrap_mod(a0 + 4 * cch, nx);
+        const int64_t offB = (int64_t)(lane < SQ ? lane : 0) * g.plane + wrap_mod(a0 + 64, nx);
+        const int nrows = ly + 2 * K;
+        int yl = (int)wrap_mod(y0 - K, ny);
+        auto stage = [&](int j, int slot) {
             if (j < nrows) {
-                const float *row = src + yl * g.pitch;
+                const float *row = src + (int64_t)yl * g.pitch;
                 const unsigned d = ring_s + (unsigned)(slot * kRow + cpar * CW + 4 * cch) * 4u;
                 const float *sp = row + offA;
                 int64_t pl2 = 2 * g.plane;
@@ -107,7 +109,7 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                     if (cpar + 2 * r < SQ) cp_async16(d + (unsigned)(2 * r * CW * 4), sp + r * pl2);
                 if (lane < SQ) cp_async16(ring_s + (unsigned)(slot * kRow + lane * CW + 64) * 4u, row + offB);
             }
-            yl = yl + 1 == g.ny ? 0 : yl + 1;
+            yl = yl + 1 == ny ? 0 : yl + 1;
             cp_async_commit();
         };
 #pragma unroll
@@ -128,7 +130,7 @@ __global__ void __launch_bounds__(NW * 32, MINB)
 #pragma unroll
         for (int s = 0; s < S; ++s) sum[s] = 0.f;
         int sl = 0;
-        for (int64_t j = 0; j < nrows; ++j) {
+        for (int j = 0; j < nrows; ++j) {
             stage(j + P, sl + P >= NS ? sl + P - NS : sl + P);
             cp_async_wait<P>();
             __syncwarp();
@@ -231,20 +233,21 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                 collide_site<Q, S>(g, f1, rho1);
             }
             if (j >= 2 * K) {  // level K of row y0 + j - 2K: window columns HL .. 63 - HL
-                const int64_t x = xb + 2 * lane;
-                if (lane >= HL / 2 && lane < (HL + WO) / 2 && x < g.nx) {
-                    const int64_t y = y0 + j - 2 * K;
+                const int x = xb + 2 * lane;
+                if (lane >= HL / 2 && lane < (HL + WO) / 2 && x < nx) {
+                    const int y = y0 + j - 2 * K;
                     int64_t pl = g.plane;
                     asm volatile("" : "+l"(pl));  // no plane multiples kept live across the row loop
-                    float *dp = dst + y * g.pitch + x;
+                    const int64_t yx = (int64_t)y * g.pitch + x;
+                    float *dp = dst + yx;
 #pragma unroll
                     for (int s = 0; s < S; ++s) {
 #pragma unroll
                         for (int i = 0; i < Q; ++i)
                             *reinterpret_cast<float2 *>(dp + (s * Q + i) * pl) = make_float2(f0[s][i], f1[s][i]);
                         if (g.rho_out)
-                            *reinterpret_cast<float2 *>(static_cast<float *>(g.rho_out) + s * pl + y * g.pitch +
-                                                        x) = make_float2(rho0[s], rho1[s]);
+                            *reinterpret_cast<float2 *>(static_cast<float *>(g.rho_out) + s * pl + yx) =
+                                make_float2(rho0[s], rho1[s]);
                         sum[s] += rho0[s] + rho1[s];
                     }
                 }

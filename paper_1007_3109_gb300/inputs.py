@@ -171,6 +171,27 @@ WORKLOADS = {
 }
 
 
+def fourier_perturbation(L: int, seed: int, nmax: int = 10) -> np.ndarray:
+    """Two zero-mean fields on an L x L periodic grid, shape (2, L, L): per field
+    the sum over mode numbers (a, b), 0 < a^2 + b^2 <= nmax^2, b >= 0, of
+    A cos(2 pi (a x + b y) / L + phi) with A = U(-1, 1) and phi = 2 pi U(0, 1)
+    from SplitMix64(seed, field, mode index), scaled to max |.| = 1.  A function
+    of (x / L, y / L) alone: the same perturbation at every grid size, for
+    the diffusion-rescaling runs of Sec. IV."""
+    x = np.arange(L, dtype=np.float64) / L
+    modes = [(a, b) for a in range(-nmax, nmax + 1) for b in range(0, nmax + 1)
+             if 0 < a * a + b * b <= nmax * nmax]
+    idx = np.arange(len(modes), dtype=np.uint64)
+    out = np.zeros((2, L, L))
+    for s in range(2):
+        amp = 2.0 * uniform01(seed, 10 + s, 0, idx) - 1.0
+        ph = 2.0 * np.pi * uniform01(seed, 10 + s, 1, idx)
+        for (a, b), A, p in zip(modes, amp, ph):
+            out[s] += A * np.cos(2.0 * np.pi * (a * x[None, :] + b * x[:, None]) + p)
+    out -= out.mean(axis=(1, 2), keepdims=True)
+    return out / np.abs(out).max(axis=(1, 2), keepdims=True)
+
+
 def coupled_gs_network(F1=0.037, k1=0.06, F2=0.03, k2=0.055, c=0.001):
     """Reaction steps of two Gray-Scott pairs (u1, v1, u2, v2) coupled by a
     slow exchange of the autocatalyst, as (rates, order, change) rows:
