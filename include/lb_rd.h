@@ -146,9 +146,11 @@ typedef struct {
     void *stream;            /* cudaStream_t for all work; NULL = legacy default stream */
     int32_t tb_depth;        /* time steps per launch (temporal blocking): 0 = the autotuner's cached choice
                                 (else one step per launch); 1 = one; 2 .. 8 = a depth-K variant of that
-                                many steps (FP32 storage with two state copies and at most two species
-                                only, else EINVAL).  Batches take cfgs[0].tb_depth as their steps per
-                                launch when it is nonzero; servers and lb_rd_step_noalloc ignore it. */
+                                many steps (FP32 or 16-bit deviation storage with two state copies and
+                                at most two species only, else EINVAL; lb_rd_create also fails with
+                                EINVAL when no variant of that depth fits the grid).  Batches take
+                                cfgs[0].tb_depth as their steps per launch when it is nonzero; servers
+                                and lb_rd_step_noalloc ignore it. */
 } lb_rd_config;
 
 typedef struct lb_rd_handle lb_rd_handle;
@@ -232,9 +234,10 @@ LB_RD_API int lb_rd_launch_count(const lb_rd_handle *h, int64_t *launches);
 
 /* Launch variants and the autotuner.  The step kernel of a precision comes in
  * several launch variants (tile shape, register budget, cache policy, TMA
- * bulk-copy staging, temporal blocking of K = 2, 4 .. 8 steps per launch:
- * FP32 variants named tb2*_ (two steps) and deep<K>_ (K steps, the deep1_
- * form one step); see lb_rd_variant_name).  lb_rd_autotune times every
+ * bulk-copy staging, temporal blocking of K = 2 .. 8 steps per launch:
+ * FP32 variants named tb2*_ (two steps) and deep<K>*_ (K steps, the deep1_
+ * form one step; deep<K>vw*_ with two columns per lane), 16-bit deviation
+ * variants hdeep<K>_ (K steps); see lb_rd_variant_name).  lb_rd_autotune times every
  * variant that fits the grid on the handle's own state -- reading the current
  * state and writing the spare copy, so the simulation is unchanged -- with
  * one warm-up launch and `iters` timed launches each, and selects the fastest
@@ -314,7 +317,9 @@ LB_RD_API int lb_rd_batch_set_graph(lb_rd_batch *b, int32_t steps_per_graph);
  * instances are FP32 with two state copies and nx a multiple of 256; other
  * values >= 2 (and 2 otherwise) run the depth-K kernel over the (band, strip)
  * units of all instances (FP32, two state copies, any nx; bitwise the same as
- * K single steps; the default for such batches: 6 for D2Q9, 4 for D2Q5).
+ * K single steps; for K <= 5 (D2Q9) or 6 (D2Q5) its form with two columns per
+ * lane; the default for such batches: 4 for D2Q9, 6 for D2Q5); 16-bit
+ * deviation storage runs its own depth-K kernel, K = 2 .. 5 (default 4).
  * EINVAL if neither applies.  1: one step per launch (the default for other
  * batches).  The graphs of lb_rd_batch_set_graph hold steps_per_graph / K
  * launches.  Synchronises the batch's stream. */
@@ -334,8 +339,10 @@ LB_RD_API int lb_rd_batch_get_time(const lb_rd_batch *b, int64_t *t, int64_t *la
  * memory (two state copies plus the density cache) fits hbm_budget_bytes.
  * Resident requests advance together, steps_per_tick steps at a time (fewer
  * when a request finishes sooner), by launches of the batched kernels over
- * all of them: for FP32 requests with two state copies, tick / K launches of the
- * depth-K kernel (K = 6 for D2Q9, 4 for D2Q5) and one launch of the tick % K
+ * all of them: for FP32 and 16-bit deviation requests with two state copies,
+ * tick / K launches of the depth-K kernel (K as the batches' default: 4 for
+ * D2Q9 and 6 for D2Q5 in FP32, 4 in 16-bit storage) and one launch of the
+ * tick % K
  * steps left (a single step if one is left), otherwise one launch per step;
  * the last launch of a tick also writes the densities.  Requests that arrive
  * meanwhile are admitted between ticks

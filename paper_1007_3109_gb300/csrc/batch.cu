@@ -206,13 +206,17 @@ void drop_graphs(lb_rd_batch *b) {
 // The K-step launches of this batch run the two-step kernel (else the depth-K kernel).
 bool uses_tb2(const lb_rd_batch *b) { return b->steps_per_launch == 2 && b->tb_ok; }
 
+// 16-bit deviation storage: the depth-K launches run its own kernel (K <= 5).
+bool half_batch(const lb_rd_batch *b) { return b->mode == 1 || b->mode == 2; }
+
 // Plans and uploads the depth-K descriptors of both parities (once per K).
 cudaError_t plan_deep(lb_rd_batch *b, int K) {
-    if (K < 2 || K > 8) return cudaErrorInvalidValue;
+    if (K < 2 || K > (half_batch(b) ? 5 : 8)) return cudaErrorInvalidValue;
     if (b->deep_units[K] > 0) return cudaSuccess;
     const int n = (int)b->cfgs.size();
     std::vector<lbrd::DeepItem> v = b->deep_base;
-    const int64_t units = lbrd::batch_deep_plan(K, b->Q, b->S, b->deep_v16, v.data(), n);
+    const int64_t units = half_batch(b) ? lbrd::batch_half_deep_plan(K, b->Q, b->S, b->mode - 1, v.data(), n)
+                                        : lbrd::batch_deep_plan(K, b->Q, b->S, b->deep_v16, v.data(), n);
     if (units <= 0) return cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
     for (int parity = 0; parity < 2 && !e; ++parity) {
@@ -233,6 +237,9 @@ cudaError_t plan_deep(lb_rd_batch *b, int K) {
 cudaError_t launch_deep(lb_rd_batch *b, int K, int parity, bool emit) {
     cudaError_t e = plan_deep(b, K);
     if (e) return e;
+    if (half_batch(b))
+        return lbrd::launch_batch_half_deep(K, b->Q, b->S, b->mode - 1, b->d_deep[K][parity], (int)b->cfgs.size(),
+                                            b->deep_units[K], emit, b->stream);
     return lbrd::launch_batch_deep(K, b->Q, b->S, b->deep_v16, b->d_deep[K][parity], (int)b->cfgs.size(),
                                    b->deep_units[K], emit, b->stream);
 }
@@ -385,8 +392,8 @@ int lb_rd_batch_create(const lb_rd_config *cfgs, int32_t n, lb_rd_batch **out) {
         }
         b->steps_per_launch = 2;
     }
-    // depth-K descriptors (planned when K >= 4 is selected): FP32 with two state copies
-    b->deep_ok = prec == LB_RD_FP32;
+    // depth-K descriptors: FP32 or 16-bit deviation storage with two state copies
+    b->deep_ok = prec == LB_RD_FP32 || half;
     b->deep_v16 = true;
     for (int i = 0; i < n; ++i) {
         if (b->inplace[i]) b->deep_ok = false;
@@ -399,10 +406,11 @@ int lb_rd_batch_create(const lb_rd_config *cfgs, int32_t n, lb_rd_batch **out) {
             b->deep_base[i].a = items[i].a;
             b->deep_base[i].a.rho_out = b->rho + b->rho_off[i];
         }
-        // default: the depth-K kernel, K = 6 (D2Q9) or 4 (D2Q5); should its
+        // default: the depth-K kernel, K = 4 (D2Q9) or 6 (D2Q5) in its
+        // two-column form, K = 4 for 16-bit deviation storage; should its
         // descriptors not be planned (no launch shape for this device), the
         // batch keeps the previous default
-        const int K = b->Q == 9 ? 6 : 4;
+        const int K = half ? 4 : lbrd::batch_deep_default_k(b->Q);
         if (!e && plan_deep(b, K) == cudaSuccess) b->steps_per_launch = K;
         cudaGetLastError();  // clear a non-sticky error of the attempt
     }
@@ -595,7 +603,10 @@ int lb_rd_batch_set_steps_per_launch(lb_rd_batch *b, int32_t k) {
     if (!b) return report_error(LB_RD_EINVAL, "batch is NULL");
     if (k < 1 || k > 8) return report_error(LB_RD_EINVAL, "steps per launch must be in [1, 8]");
     if (k >= 2 && !b->deep_ok && !(k == 2 && b->tb_ok))
-        return report_error(LB_RD_EINVAL, "2 .. 8 steps per launch need FP32 instances with two state copies");
+        return report_error(LB_RD_EINVAL, "2 .. 8 steps per launch need FP32 or 16-bit deviation instances with two "
+                                          "state copies");
+    if (k > 5 && half_batch(b))
+        return report_error(LB_RD_EINVAL, "16-bit deviation storage: at most 5 steps per launch");
     cudaStreamSynchronize(b->stream);
     if (k >= 2 && !(k == 2 && b->tb_ok)) {
         cudaError_t e = plan_deep(b, k);

@@ -123,8 +123,12 @@ int handle_variant_count(const lb_rd_handle *h) {
     return variant_count(h->prec);
 }
 
+bool is_half(const lb_rd_handle *h) { return h->prec == LB_RD_FP32_BF16DEV || h->prec == LB_RD_FP32_FP16DEV; }
+
 int variant_steps(const lb_rd_handle *h, int v) {
-    return h->prec == LB_RD_FP32 && !h->general ? lbrd::kF32Variants[v].steps : 1;
+    if (h->general || h->inplace || v < 0) return 1;
+    if (h->prec == LB_RD_FP32) return lbrd::kF32Variants[v].steps;
+    return is_half(h) ? lbrd::kHalfVariantSteps[v] : 1;
 }
 
 bool variant_fits(const lb_rd_handle *h, int v) {
@@ -133,9 +137,12 @@ bool variant_fits(const lb_rd_handle *h, int v) {
     return h->prec != LB_RD_FP32 || h->cfg.nx % lbrd::kF32Variants[v].nx_multiple == 0;
 }
 
-// A variant of the depth-K kernel (it can write the densities of its last level).
+// A variant of a depth-K kernel (it can write the densities of its last level):
+// the FP32 ones and the 16-bit deviation ones of two or more steps.
 bool is_deep(const lb_rd_handle *h, int v) {
-    return h->prec == LB_RD_FP32 && !h->general && !h->inplace && v >= 0 && lbrd::kF32Variants[v].cache == 4;
+    if (h->general || h->inplace || v < 0) return false;
+    if (h->prec == LB_RD_FP32) return lbrd::kF32Variants[v].cache == 4;
+    return is_half(h) && lbrd::kHalfVariantSteps[v] >= 2;
 }
 
 // Untuned depth table: per d = 2 .. 8 the first depth-K variant of d steps
@@ -146,9 +153,8 @@ void default_depths(lb_rd_handle *h) {
         h->depth_ms[d] = 0.0;
     }
     h->depth_tuned = false;
-    if (h->prec != LB_RD_FP32 || h->general || h->inplace) return;
-    for (int v = 0; v < lbrd::kF32VariantCount; ++v) {
-        const int d = lbrd::kF32Variants[v].steps;
+    for (int v = 0; v < handle_variant_count(h); ++v) {
+        const int d = variant_steps(h, v);
         if (is_deep(h, v) && d >= 2 && d <= 8 && h->depth_variant[d] < 0 && variant_fits(h, v))
             h->depth_variant[d] = v;
     }
@@ -280,10 +286,10 @@ int lb_rd_check_config(const lb_rd_config *cfg, size_t *bytes) {
         return fail(LB_RD_EINVAL, "in-place streaming: FP64 or FP32 storage only");
     if (cfg->tb_depth < 0 || cfg->tb_depth > 8)
         return fail(LB_RD_EINVAL, "tb_depth must be in [0, 8] (0: the autotuner's choice)");
-    if (cfg->tb_depth > 1 && (cfg->precision != LB_RD_FP32 || cfg->streaming != LB_RD_STREAM_PINGPONG ||
+    if (cfg->tb_depth > 1 && (cfg->precision == LB_RD_FP64 || cfg->streaming != LB_RD_STREAM_PINGPONG ||
                               needs_general(*cfg)))
-        return fail(LB_RD_EINVAL, "tb_depth > 1 needs FP32 storage with two state copies and at most two species "
-                                  "without a mass-action network");
+        return fail(LB_RD_EINVAL, "tb_depth > 1 needs FP32 or 16-bit deviation storage with two state copies and "
+                                  "at most two species without a mass-action network");
     if (bytes) {
         const int64_t pitch = pitch_for(cfg->nx);
         const size_t st = lbrd::state_plane_bytes(cfg->precision, Q, cfg->nspecies, cfg->ny, pitch);

@@ -109,7 +109,10 @@ cudaError_t launch_init_f32(int Q, int S, const InitArgs &a, cudaStream_t st);
 StepShape step_shape_half(int64_t nx, int64_t ny);
 cudaError_t launch_step_half(int Q, int S, int half_kind, const StepArgs &a, cudaStream_t st);
 extern const char *const kHalfVariantNames[];
+extern const int kHalfVariantSteps[];  // time steps per launch of each variant
 extern const int kHalfVariantCount;
+// Depth-K launches of the 16-bit deviation step (variant v of that family).
+cudaError_t launch_step_half_deep(int v, int Q, int S, int half_kind, const StepArgs &a, cudaStream_t st);
 cudaError_t launch_step_half_variant(int v, int Q, int S, int half_kind, const StepArgs &a, cudaStream_t st);
 cudaError_t launch_init_half(int Q, int S, int half_kind, const InitArgs &a, cudaStream_t st);
 
@@ -156,18 +159,29 @@ struct TbwItem {
 int batch_tb2_strip();
 cudaError_t launch_batch_tb2(const TbwItem *items, int n, int64_t total_units, int Q, int S, cudaStream_t st);
 // Batched K-step launches (K = 2 .. 8; FP32, two state copies): the depth-K
-// kernel over the (band, strip) units of a list of grids.  Item k's units are
-// [unit_begin, unit_begin + nstrips * ceil(ny / band)), strips of 34 - 2K
-// columns fastest.  batch_deep_plan fills nstrips and band of every item (one
-// band height for the list, chosen for the launch's warp count) and returns
-// the total unit count, or -1 for an unsupported K.  v16: every grid has nx
+// kernel over the (band, strip) units of a list of grids (for K <= 5 (D2Q9)
+// or 6 (D2Q5) its two-column form).  Item k's units
+// are [unit_begin, unit_begin + nstrips * ceil(ny / band)), strips of the
+// kernel's output columns (34 - 2K, or 64 - 2 HL) fastest.  batch_deep_plan
+// fills nstrips and band of every item (one band height in rows for the whole
+// list, chosen for the launch's warp count) and returns the total unit count,
+// or -1 for an unsupported K.  v16: every grid has nx
 // and pitch multiples of 4 (16-byte staging).  emit: the launch also writes
 // rho(t + K) of every item to its a.rho_out (the last launch of a call).
 struct DeepItem {
     StepArgs a;
     int64_t unit_begin, nstrips, band;
 };
+// The same over 16-bit deviation storage (K = 2 .. 5; half_kind 0 bf16, 1 fp16;
+// any nx a multiple of 4), the depth-K kernel of step_half_deep_kernel.cuh.
+int64_t batch_half_deep_plan(int K, int Q, int S, int half_kind, DeepItem *items, int n);
+cudaError_t launch_batch_half_deep(int K, int Q, int S, int half_kind, const DeepItem *items, int n,
+                                   int64_t total_units, bool emit, cudaStream_t st);
 bool batch_deep_depth_ok(int K);
+// Default steps per launch of a list of grids: 4 (D2Q9) / 6 (D2Q5), the
+// deepest two-column forms that keep every carried level in registers when
+// the grid's parameters come from a descriptor (K = 5 D2Q9 spills there).
+int batch_deep_default_k(int Q);
 int64_t batch_deep_plan(int K, int Q, int S, bool v16, DeepItem *items, int n);
 cudaError_t launch_batch_deep(int K, int Q, int S, bool v16, const DeepItem *items, int n, int64_t total_units,
                               bool emit, cudaStream_t st);

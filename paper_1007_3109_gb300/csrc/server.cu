@@ -8,7 +8,8 @@
 //   2. advances every resident request by one tick of up to steps_per_tick
 //      steps (never past the earliest finishing request): FP32 requests with
 //      two state copies by K-step launches of the depth-K kernel over all
-//      resident requests (K = 6 for D2Q9, 4 for D2Q5) and one shorter
+//      resident requests (K = 4 for D2Q9, 6 for D2Q5: the two-column form;
+//      16-bit deviation storage its own kernel, K = 4) and one shorter
 //      depth-K launch for the steps left (a single step if one is left),
 //      other requests one batched launch per step; the tick's last launch
 //      also writes their densities,
@@ -231,19 +232,22 @@ void run_tick(lb_rd_server *s) {
         act.clear();
         return;
     }
-    // K-step launches: FP32 requests with two state copies run the tick as
-    // q = tick / K depth-K launches and, for the r = tick % K steps left, one
+    // K-step launches: FP32 and 16-bit deviation requests with two state
+    // copies run the tick as q = tick / K depth-K launches (FP32:
+    // lbrd::batch_deep_default_k; 16-bit storage: 4) and, for the r = tick % K
+    // steps left, one
     // depth-r launch (r >= 2) or one single step (r = 1); the tick's last
     // launch writes the densities.  Other requests: one launch per step.
     bool any_inplace = false;
     for (Request *r : act) any_inplace = any_inplace || r->cfg.streaming == LB_RD_STREAM_INPLACE;
-    const int K = s->Q == 9 ? 6 : 4;
-    const bool deep = s->mode == 0 && !any_inplace && tick >= 2;
+    bool v16 = true;
+    for (Request *r : act) v16 = v16 && r->cfg.nx % 4 == 0 && r->pitch % 4 == 0;
+    const bool half = s->mode == 1 || s->mode == 2;  // 16-bit deviation storage: its own depth-K kernel
+    const int K = half ? 4 : lbrd::batch_deep_default_k(s->Q);
+    const bool deep = (s->mode == 0 || half) && !any_inplace && tick >= 2;
     int64_t n_multi = deep ? tick / K : 0;
     int rem = deep ? (int)(tick % K) : 0;  // steps of the depth-r launch (0: none)
     if (rem == 1) rem = 0;                 // one single step instead
-    bool v16 = true;
-    for (Request *r : act) v16 = v16 && r->cfg.nx % 4 == 0 && r->pitch % 4 == 0;
     int64_t deep_units = 0, rem_units = 0;
     if ((n_multi > 0 || rem > 0) && ensure_deep(s, n) == LB_RD_OK) {
         for (size_t i = 0; i < n; ++i) {  // parity 0 relative to each request's current copy
@@ -271,9 +275,13 @@ void run_tick(lb_rd_server *s) {
                 s->h_deep[2 * n + i].a.src = act[i]->buf[act[i]->cur ^ par];
                 s->h_deep[2 * n + i].a.dst = act[i]->buf[act[i]->cur ^ par ^ 1];
             }
-            rem_units = lbrd::batch_deep_plan(rem, s->Q, s->cfg.nspecies, v16, s->h_deep + 2 * n, (int)n);
+            rem_units = half ? lbrd::batch_half_deep_plan(rem, s->Q, s->cfg.nspecies, s->mode - 1, s->h_deep + 2 * n,
+                                                          (int)n)
+                             : lbrd::batch_deep_plan(rem, s->Q, s->cfg.nspecies, v16, s->h_deep + 2 * n, (int)n);
         }
-        if (n_multi > 0) deep_units = lbrd::batch_deep_plan(K, s->Q, s->cfg.nspecies, v16, s->h_deep, (int)n);
+        if (n_multi > 0)
+            deep_units = half ? lbrd::batch_half_deep_plan(K, s->Q, s->cfg.nspecies, s->mode - 1, s->h_deep, (int)n)
+                              : lbrd::batch_deep_plan(K, s->Q, s->cfg.nspecies, v16, s->h_deep, (int)n);
         for (size_t i = 0; i < n; ++i) {  // parity 1: the copies swapped
             s->h_deep[n + i] = s->h_deep[i];
             s->h_deep[n + i].a.src = act[i]->buf[act[i]->cur ^ 1];
@@ -327,11 +335,15 @@ void run_tick(lb_rd_server *s) {
     const int S = s->cfg.nspecies;
     for (int64_t l = 0; l < L && !e; ++l) {
         if (l < n_multi) {
-            e = lbrd::launch_batch_deep(K, s->Q, S, v16, s->d_deep + (l & 1) * n, (int)n, deep_units, l == L - 1,
-                                        s->stream);
+            e = half ? lbrd::launch_batch_half_deep(K, s->Q, S, s->mode - 1, s->d_deep + (l & 1) * n, (int)n,
+                                                    deep_units, l == L - 1, s->stream)
+                     : lbrd::launch_batch_deep(K, s->Q, S, v16, s->d_deep + (l & 1) * n, (int)n, deep_units,
+                                               l == L - 1, s->stream);
         } else if (l == n_multi && rem > 0) {
-            e = lbrd::launch_batch_deep(rem, s->Q, S, v16, s->d_deep + 2 * n, (int)n, rem_units, l == L - 1,
-                                        s->stream);
+            e = half ? lbrd::launch_batch_half_deep(rem, s->Q, S, s->mode - 1, s->d_deep + 2 * n, (int)n, rem_units,
+                                                    l == L - 1, s->stream)
+                     : lbrd::launch_batch_deep(rem, s->Q, S, v16, s->d_deep + 2 * n, (int)n, rem_units, l == L - 1,
+                                               s->stream);
         } else {
             const lbrd::BatchItem *items = s->d_items + (l == L - 1 ? 2 : (l & 1)) * n;
             e = lbrd::launch_batch_step(any_inplace ? 4 : s->mode, s->Q, S, items, (int)n, total, s->stream);

@@ -107,7 +107,8 @@ const F32Variant kF32Variants[] = {
     // three steps per launch (with the others, the last steps of a call)
     {"deep3v_128_minb3", 128, 3, 3, 4, 3, 4},
     {"deep3_128_minb3", 128, 3, 3, 4, 3, 1},
-    // two columns per lane (step_f32_pair_kernel.cuh), 16-byte staging: deep<K>vw[p]_
+    // two columns per lane (step_f32_pair_kernel.cuh), 16-byte staging: deep<K>vw[p]_ (nx a multiple
+    // of 4), deep<K>vw[p]a_ (any nx)
     {"deep4vw_128_minb2", 128, 4, 2, 4, 4, 4},
     {"deep4vwp_128_minb2", 128, 4, 2, 4, 4, 4},
     {"deep4vw_128_minb2_s5", 128, 4, 2, 4, 4, 4},
@@ -119,6 +120,10 @@ const F32Variant kF32Variants[] = {
     {"deep3vwp_128_minb2_s5", 128, 3, 2, 4, 3, 4},
     {"deep5vwp_128_minb2_s5", 128, 5, 2, 4, 5, 4},
     {"deep5vw_128_minb2_s5", 128, 5, 2, 4, 5, 4},
+    {"deep5vwpa_128_minb2", 128, 5, 2, 4, 5, 1},
+    {"deep4vwa_128_minb2", 128, 4, 2, 4, 4, 1},
+    {"deep6vwpa_128_minb1", 128, 6, 1, 4, 6, 1},
+    {"deep3vwpa_128_minb2_s5", 128, 3, 2, 4, 3, 1},
 };
 const int kF32VariantCount = sizeof(kF32Variants) / sizeof(kF32Variants[0]);
 

@@ -2,10 +2,25 @@
 // ticks): the launch shape per K, the (band, strip) plan of the list and the
 // launch (the kernel is in step_f32_deep_kernel.cuh).
 #include "step_f32_deep_kernel.cuh"
+#include "step_f32_pair_kernel.cuh"
 
 namespace lbrd {
 
 namespace {
+
+// Two columns per lane (step_f32_pair_kernel.cuh) where that form is the
+// faster one: depths whose carried levels fit the register file without
+// heavy spills (K <= 5 for D2Q9, K <= 6 for D2Q5); its any-nx form unless
+// every grid has nx a multiple of 4.  Four warps, the pulls from earlier rows
+// first, five staged rows below K = 5.
+template <int Q, int K, bool V16>
+struct UsePair {
+    static constexpr bool value = Q == 9 ? K <= 5 : K <= 6;
+};
+template <int Q, int S, int K, bool V16>
+struct PairShape : PairKernel<Q, S, K, 4, (K < 5 ? 5 : 4), (K == 6 ? 1 : 2), true, true, !V16> {
+    static constexpr int NW = 4, NS = K < 5 ? 5 : 4, MINB = K == 6 ? 1 : 2;
+};
 
 // Batched launch shapes per K: the single-grid choices (K = 4, 5: six warps,
 // two blocks per SM; K = 6, 7, 8: four warps, two blocks per SM; K = 5, 7, 8
@@ -58,37 +73,50 @@ struct BatchShape<Q, S, 8, V16> : DeepKernel<Q, S, 8, 4, 4, 2, V16, true, true> 
 
 template <int Q, int S, int K, bool V16>
 int64_t plan_batch(DeepItem *items, int n) {
-    using BS = BatchShape<Q, S, K, V16>;
-    constexpr int WO = 34 - 2 * K;
+    constexpr bool pair = UsePair<Q, K, V16>::value;
+    constexpr int WO = pair ? PairGeom<K>::WO : 34 - 2 * K;
+    int NW = 0;
     unsigned full = 0;
-    if (BS::get(&full) != cudaSuccess) return -1;
-    int64_t strips = 0, ny = 1;
-    for (int i = 0; i < n; ++i) {
-        items[i].nstrips = (items[i].a.nx + WO - 1) / WO;
-        strips += items[i].nstrips;
-        ny = items[i].a.ny > ny ? items[i].a.ny : ny;
+    cudaError_t ge;
+    if constexpr (pair) {  // only the kernels a list can run are instantiated
+        NW = PairShape<Q, S, K, V16>::NW;
+        ge = PairShape<Q, S, K, V16>::get(&full);
+    } else {
+        NW = BatchShape<Q, S, K, V16>::NW;
+        ge = BatchShape<Q, S, K, V16>::get(&full);
     }
-    const int64_t nb = choose_bands(K, strips, ny, (int64_t)full * BS::NW);
+    if (ge != cudaSuccess) return -1;
+    for (int i = 0; i < n; ++i) items[i].nstrips = (items[i].a.nx + WO - 1) / WO;
+    const int64_t h = choose_band_height(K, items, n, (int64_t)full * NW);
     int64_t units = 0;
     for (int i = 0; i < n; ++i) {
-        const int64_t g = items[i].a.ny;
-        items[i].band = (g + nb - 1) / nb;
+        items[i].band = h;
         items[i].unit_begin = units;
-        units += items[i].nstrips * ((g + items[i].band - 1) / items[i].band);
+        units += items[i].nstrips * ((items[i].a.ny + h - 1) / h);
     }
     return units;
 }
 
 template <int Q, int S, int K, bool V16>
 cudaError_t launch_batch(const DeepItem *items, int n, int64_t total_units, bool emit, cudaStream_t st) {
-    using BS = BatchShape<Q, S, K, V16>;
     unsigned full = 0;
-    cudaError_t e = BS::get(&full);
-    if (e != cudaSuccess) return e;
-    const int64_t nwarps = (int64_t)full * BS::NW;
-    const unsigned grid = total_units < nwarps ? (unsigned)((total_units + BS::NW - 1) / BS::NW) : full;
-    step_deep_kernel<Q, S, K, BS::NW, 4, BS::MINB, V16, true, BS::PP>
-        <<<grid, BS::NW * 32, BS::smem, st>>>(StepArgs{}, 0, 0, 0, items, n, total_units, emit ? 1 : 0);
+    if constexpr (UsePair<Q, K, V16>::value) {
+        using PS = PairShape<Q, S, K, V16>;
+        cudaError_t e = PS::get(&full);
+        if (e != cudaSuccess) return e;
+        const int64_t nwarps = (int64_t)full * PS::NW;
+        const unsigned grid = total_units < nwarps ? (unsigned)((total_units + PS::NW - 1) / PS::NW) : full;
+        step_pair_kernel<Q, S, K, PS::NW, PS::NS, PS::MINB, true, true, !V16>
+            <<<grid, PS::NW * 32, PS::smem, st>>>(StepArgs{}, 0, 0, 0, items, n, total_units, emit ? 1 : 0);
+    } else {
+        using BS = BatchShape<Q, S, K, V16>;
+        cudaError_t e = BS::get(&full);
+        if (e != cudaSuccess) return e;
+        const int64_t nwarps = (int64_t)full * BS::NW;
+        const unsigned grid = total_units < nwarps ? (unsigned)((total_units + BS::NW - 1) / BS::NW) : full;
+        step_deep_kernel<Q, S, K, BS::NW, 4, BS::MINB, V16, true, BS::PP>
+            <<<grid, BS::NW * 32, BS::smem, st>>>(StepArgs{}, 0, 0, 0, items, n, total_units, emit ? 1 : 0);
+    }
     return cudaGetLastError();
 }
 
@@ -120,6 +148,8 @@ cudaError_t launch_v(int Q, int S, bool v16, const DeepItem *items, int n, int64
 }  // namespace
 
 bool batch_deep_depth_ok(int K) { return K >= 2 && K <= 8; }
+
+int batch_deep_default_k(int Q) { return Q == 9 ? 4 : 6; }
 
 int64_t batch_deep_plan(int K, int Q, int S, bool v16, DeepItem *items, int n) {
     switch (K) {

@@ -293,6 +293,37 @@ int64_t choose_bands(int K, int64_t nstrips, int64_t ny, int64_t nwarps) {
     return nb;
 }
 
+// Band height (rows) for a list of grids (items with nstrips and a.ny set):
+// every grid is cut into bands of h rows (its last band shorter), one height
+// for the whole list, so that a small grid is not cut into bands of a few
+// rows that each pay the 2K pipeline-fill rows.  The height minimises the
+// estimated time of the round-robin deal of the units to nwarps warps: the
+// rows each warp walks on average (every band of a grid adds 2K) plus one
+// unit for the last round's imbalance.
+int64_t choose_band_height(int K, const DeepItem *items, int n, int64_t nwarps) {
+    static const int64_t kCand[] = {4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768,
+                                    1024, 1536, 2048, 3072, 4096, 6144, 8192, 16384, 32768, 65536};
+    int64_t maxny = 1;
+    for (int i = 0; i < n; ++i) maxny = items[i].a.ny > maxny ? items[i].a.ny : maxny;
+    int64_t best_h = maxny;
+    double best = 1e300;
+    for (int64_t h : kCand) {
+        const int64_t hh = h < maxny ? h : maxny;
+        double rows = 0.0;
+        for (int i = 0; i < n; ++i) {
+            const int64_t nb = (items[i].a.ny + hh - 1) / hh;
+            rows += (double)items[i].nstrips * (double)(items[i].a.ny + 2 * K * nb);
+        }
+        const double cost = rows / (double)nwarps + (double)(hh + 2 * K);
+        if (cost < best) {
+            best = cost;
+            best_h = hh;
+        }
+        if (h >= maxny) break;
+    }
+    return best_h;
+}
+
 template <int Q, int S, int K, int NW, int NS, int MINB, bool V16, bool BATCH, bool PP = false>
 struct DeepKernel {
     static constexpr size_t smem = (size_t)NW * NS * S * Q * (V16 ? 40 : 34) * sizeof(float);

@@ -6,12 +6,12 @@ namespace lbrd {
 
 namespace {
 
-template <int K, int NW, int NS, int MINB, bool PP>
+template <int K, int NW, int NS, int MINB, bool PP, bool ANY = false>
 cudaError_t dispatch_pair(int Q, int S, const StepArgs &a, cudaStream_t st) {
-    if (Q == 9 && S == 1) return launch_pair<9, 1, K, NW, NS, MINB, PP>(a, st);
-    if (Q == 9 && S == 2) return launch_pair<9, 2, K, NW, NS, MINB, PP>(a, st);
-    if (Q == 5 && S == 1) return launch_pair<5, 1, K, NW, NS, MINB, PP>(a, st);
-    if (Q == 5 && S == 2) return launch_pair<5, 2, K, NW, NS, MINB, PP>(a, st);
+    if (Q == 9 && S == 1) return launch_pair<9, 1, K, NW, NS, MINB, PP, ANY>(a, st);
+    if (Q == 9 && S == 2) return launch_pair<9, 2, K, NW, NS, MINB, PP, ANY>(a, st);
+    if (Q == 5 && S == 1) return launch_pair<5, 1, K, NW, NS, MINB, PP, ANY>(a, st);
+    if (Q == 5 && S == 2) return launch_pair<5, 2, K, NW, NS, MINB, PP, ANY>(a, st);
     return cudaErrorInvalidValue;
 }
 
@@ -31,6 +31,11 @@ cudaError_t launch_step_f32_pair(int v, int Q, int S, const StepArgs &a, cudaStr
         case 8: return dispatch_pair<3, 4, 5, 2, true>(Q, S, a, st);
         case 9: return dispatch_pair<5, 4, 5, 2, true>(Q, S, a, st);
         case 10: return dispatch_pair<5, 4, 5, 2, false>(Q, S, a, st);
+        // any nx
+        case 11: return dispatch_pair<5, 4, 4, 2, true, true>(Q, S, a, st);
+        case 12: return dispatch_pair<4, 4, 4, 2, false, true>(Q, S, a, st);
+        case 13: return dispatch_pair<6, 4, 4, 1, true, true>(Q, S, a, st);
+        case 14: return dispatch_pair<3, 4, 5, 2, true, true>(Q, S, a, st);
         default: return cudaErrorInvalidValue;
     }
 }

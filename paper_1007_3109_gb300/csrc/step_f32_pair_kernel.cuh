@@ -14,19 +14,24 @@
 // registers per level, which bounds K.
 //
 //   * level 0 (f*(t)): rows staged per warp by cp.async in 16-byte chunks
-//     (nx and the row pitch multiples of 4): the window's 64 columns start at
+//     (the row pitch is a multiple of 32): the window's 64 columns start at
 //     xb (even), inside the 17 aligned chunks from a0 = xb rounded down to a
 //     multiple of 4; lanes 0-15 copy chunk `lane` of the even planes, lanes
 //     16-31 chunk `lane - 16` of the odd planes, lane p < S Q chunk 16 of
-//     plane p.  Waits only on the warp's own copy groups.
+//     plane p.  nx a multiple of 4: no chunk straddles the periodic seam.
+//     The ANY form takes any nx: a chunk that reaches past the seam (edge
+//     strips only) is copied column by column with wrapped indices; kept
+//     apart because the extra paths slow the loop body down even where they
+//     never run.  Waits only on the warp's own copy groups.
 //   * level 1 pulls the lane's column pair of every plane from the staged row
 //     of its e_iy (one 8-byte shared load) and shifts it like the levels
 //     above; level m > 1 pulls from level m - 1 carried in registers (the row
 //     of this iteration for e_iy = -1, the previous one for e_iy = 0, the one
 //     before for e_iy = +1), exactly as the one-column kernel.
 //   * level 1 is valid on window columns 1 .. 62 and level m on m .. 63 - m;
-//     level K is stored for columns HL .. 63 - HL (8-byte stores), and with
-//     `emit` rho(t + K) of level K as well.
+//     level K is stored for columns HL .. 63 - HL (8-byte stores; the last
+//     column of an odd nx alone in the ANY form), and with `emit` rho(t + K)
+//     of level K too.
 // Each level is tb::collide_site per column: K levels give the bits of K
 // single steps.  Units, bands, the periodic wrap and the FP64 mass reduction
 // are those of the one-column kernel.
@@ -38,13 +43,26 @@ namespace lbrd {
 
 namespace {
 
+// Periodic wrap of a column index in 32-bit arithmetic (inlined, unlike a
+// 64-bit remainder, which would put a call into the row loop).
+__device__ __forceinline__ int wrap32(int a, int n) {
+    const int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ void cp_async4s(unsigned dst, const float *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+}
+
 template <int K>
 struct PairGeom {
     static constexpr int HL = (K + 1) / 2 * 2;  // left (and right) halo columns of the window, even
     static constexpr int WO = 64 - 2 * HL;      // output columns per warp, even
 };
 
-template <int Q, int S, int K, int NW, int NS, int MINB, bool BATCH, bool PP>
+// ANY: grids of any nx (the seam chunks copied column by column, the last
+// column of an odd nx stored alone); otherwise nx must be a multiple of 4.
+template <int Q, int S, int K, int NW, int NS, int MINB, bool BATCH, bool PP, bool ANY = false>
 __global__ void __launch_bounds__(NW * 32, MINB)
     step_pair_kernel(StepArgs a, int64_t nstrips, int64_t nbands, int64_t band, const DeepItem *__restrict__ items,
                      int nitems, int64_t total_units, int emit) {
@@ -93,8 +111,13 @@ __global__ void __launch_bounds__(NW * 32, MINB)
         const int xb = (int)(strip * WO) - HL;  // first window column (even)
         const int a0 = xb - (int)wrap_mod(xb, 4);  // first staged column
         const int o = xb - a0;                     // staged column of xb: 0 or 2
-        const int64_t offA = (int64_t)cpar * g.plane + wrap_mod(a0 + 4 * cch, nx);
-        const int64_t offB = (int64_t)(lane < SQ ? lane : 0) * g.plane + wrap_mod(a0 + 64, nx);
+        // this lane's chunks start at columns cA and cB; a chunk that reaches past the
+        // periodic seam (edge strips only, nx not a multiple of 4) is copied column by
+        // column with wrapped indices, the others in one 16-byte copy
+        const int cA = a0 + 4 * cch, cB = a0 + 64;
+        const bool cleanA = !ANY || (cA >= 0 && cA + 4 <= nx), cleanB = !ANY || (cB >= 0 && cB + 4 <= nx);
+        const int64_t offA = (int64_t)cpar * g.plane + (ANY ? (cleanA ? cA : 0) : wrap_mod(cA, nx));
+        const int64_t offB = (int64_t)(lane < SQ ? lane : 0) * g.plane + (ANY ? (cleanB ? cB : 0) : wrap_mod(cB, nx));
         const int nrows = ly + 2 * K;
         int yl = (int)wrap_mod(y0 - K, ny);
         auto stage = [&](int j, int slot) {
@@ -104,10 +127,26 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                 const float *sp = row + offA;
                 int64_t pl2 = 2 * g.plane;
                 asm volatile("" : "+l"(pl2));  // no plane multiples kept live across the row loop
+                if (!ANY || cleanA) {
 #pragma unroll
-                for (int r = 0; r < (SQ + 1) / 2; ++r)
-                    if (cpar + 2 * r < SQ) cp_async16(d + (unsigned)(2 * r * CW * 4), sp + r * pl2);
-                if (lane < SQ) cp_async16(ring_s + (unsigned)(slot * kRow + lane * CW + 64) * 4u, row + offB);
+                    for (int r = 0; r < (SQ + 1) / 2; ++r)
+                        if (cpar + 2 * r < SQ) cp_async16(d + (unsigned)(2 * r * CW * 4), sp + r * pl2);
+                } else if constexpr (ANY) {
+                    for (int r = 0; r < (SQ + 1) / 2; ++r)
+                        if (cpar + 2 * r < SQ)
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                cp_async4s(d + (unsigned)((2 * r * CW + e) * 4), sp + r * pl2 + wrap32(cA + e, nx));
+                }
+                if (lane < SQ) {
+                    const unsigned db = ring_s + (unsigned)(slot * kRow + lane * CW + 64) * 4u;
+                    if (!ANY || cleanB) {
+                        cp_async16(db, row + offB);
+                    } else if constexpr (ANY) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) cp_async4s(db + 4u * e, row + offB + wrap32(cB + e, nx));
+                    }
+                }
             }
             yl = yl + 1 == ny ? 0 : yl + 1;
             cp_async_commit();
@@ -240,15 +279,25 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                     asm volatile("" : "+l"(pl));  // no plane multiples kept live across the row loop
                     const int64_t yx = (int64_t)y * g.pitch + x;
                     float *dp = dst + yx;
+                    if (!ANY || x + 1 < nx) {  // both columns (x is even: 8-byte stores)
 #pragma unroll
-                    for (int s = 0; s < S; ++s) {
+                        for (int s = 0; s < S; ++s) {
 #pragma unroll
-                        for (int i = 0; i < Q; ++i)
-                            *reinterpret_cast<float2 *>(dp + (s * Q + i) * pl) = make_float2(f0[s][i], f1[s][i]);
-                        if (g.rho_out)
-                            *reinterpret_cast<float2 *>(static_cast<float *>(g.rho_out) + s * pl + yx) =
-                                make_float2(rho0[s], rho1[s]);
-                        sum[s] += rho0[s] + rho1[s];
+                            for (int i = 0; i < Q; ++i)
+                                *reinterpret_cast<float2 *>(dp + (s * Q + i) * pl) = make_float2(f0[s][i], f1[s][i]);
+                            if (g.rho_out)
+                                *reinterpret_cast<float2 *>(static_cast<float *>(g.rho_out) + s * pl + yx) =
+                                    make_float2(rho0[s], rho1[s]);
+                            sum[s] += rho0[s] + rho1[s];
+                        }
+                    } else if constexpr (ANY) {  // the last column of an odd nx
+#pragma unroll
+                        for (int s = 0; s < S; ++s) {
+#pragma unroll
+                            for (int i = 0; i < Q; ++i) dp[(s * Q + i) * pl] = f0[s][i];
+                            if (g.rho_out) static_cast<float *>(g.rho_out)[s * pl + yx] = rho0[s];
+                            sum[s] += rho0[s];
+                        }
                     }
                 }
             }
@@ -262,11 +311,11 @@ __global__ void __launch_bounds__(NW * 32, MINB)
     if (a.mass_out) block_mass_reduce<S, NW * 32>(acc, a.partials, a.counter, a.mass_out);
 }
 
-template <int Q, int S, int K, int NW, int NS, int MINB, bool BATCH, bool PP = false>
+template <int Q, int S, int K, int NW, int NS, int MINB, bool BATCH, bool PP = false, bool ANY = false>
 struct PairKernel {
     static constexpr size_t smem = (size_t)NW * NS * S * Q * 68 * sizeof(float);
     static cudaError_t get(unsigned *full) {
-        auto kern = step_pair_kernel<Q, S, K, NW, NS, MINB, BATCH, PP>;
+        auto kern = step_pair_kernel<Q, S, K, NW, NS, MINB, BATCH, PP, ANY>;
         static std::atomic<bool> configured[64] = {};
         int dev = 0;
         cudaGetDevice(&dev);
@@ -280,11 +329,11 @@ struct PairKernel {
     }
 };
 
-template <int Q, int S, int K, int NW, int NS, int MINB, bool PP>
+template <int Q, int S, int K, int NW, int NS, int MINB, bool PP, bool ANY = false>
 cudaError_t launch_pair(const StepArgs &a, cudaStream_t st) {
     constexpr int WO = PairGeom<K>::WO;
-    if (a.nx % 4 != 0 || a.pitch % 4 != 0) return cudaErrorInvalidValue;
-    using PK = PairKernel<Q, S, K, NW, NS, MINB, false, PP>;
+    if ((!ANY && a.nx % 4 != 0) || a.pitch % 4 != 0) return cudaErrorInvalidValue;
+    using PK = PairKernel<Q, S, K, NW, NS, MINB, false, PP, ANY>;
     unsigned full = 0;
     cudaError_t e = PK::get(&full);
     if (e != cudaSuccess) return e;
@@ -294,7 +343,7 @@ cudaError_t launch_pair(const StepArgs &a, cudaStream_t st) {
     const int64_t band = (a.ny + nb - 1) / nb, nbands = (a.ny + band - 1) / band;
     const int64_t units = nstrips * nbands;
     const unsigned grid = units < nwarps ? (unsigned)((units + NW - 1) / NW) : full;
-    step_pair_kernel<Q, S, K, NW, NS, MINB, false, PP>
+    step_pair_kernel<Q, S, K, NW, NS, MINB, false, PP, ANY>
         <<<grid, NW * 32, PK::smem, st>>>(a, nstrips, nbands, band, nullptr, 0, 0, a.rho_out != nullptr);
     return cudaGetLastError();
 }

@@ -1,0 +1,101 @@
+// 16-bit deviation storage with temporal blocking to depth K over a list of
+// grids (batches): launch shapes per K, the (band, strip) plan of the list and
+// the launch (the kernel is in step_half_deep_kernel.cuh).
+#include "step_half_deep_kernel.cuh"
+
+namespace lbrd {
+
+namespace {
+
+// Four warps per block; resident blocks per SM by the depth's registers.
+template <int K>
+struct HalfShape {
+    static constexpr int NW = 4, NS = 4, MINB = K <= 2 ? 4 : (K <= 4 ? 3 : 2);
+};
+
+template <int Q, int S, int H, int K>
+int64_t plan_half_batch(DeepItem *items, int n) {
+    using HS = HalfShape<K>;
+    using HK = HalfDeepKernel<Q, S, H, K, HS::NW, HS::NS, HS::MINB, true>;
+    constexpr int WO = 34 - 2 * K;
+    unsigned full = 0;
+    if (HK::get(&full) != cudaSuccess) return -1;
+    for (int i = 0; i < n; ++i) items[i].nstrips = (items[i].a.nx + WO - 1) / WO;
+    const int64_t h = choose_band_height(K, items, n, (int64_t)full * HS::NW);
+    int64_t units = 0;
+    for (int i = 0; i < n; ++i) {
+        items[i].band = h;
+        items[i].unit_begin = units;
+        units += items[i].nstrips * ((items[i].a.ny + h - 1) / h);
+    }
+    return units;
+}
+
+template <int Q, int S, int H, int K>
+cudaError_t launch_half_batch(const DeepItem *items, int n, int64_t total_units, bool emit, cudaStream_t st) {
+    using HS = HalfShape<K>;
+    using HK = HalfDeepKernel<Q, S, H, K, HS::NW, HS::NS, HS::MINB, true>;
+    unsigned full = 0;
+    cudaError_t e = HK::get(&full);
+    if (e != cudaSuccess) return e;
+    const int64_t nwarps = (int64_t)full * HS::NW;
+    const unsigned grid = total_units < nwarps ? (unsigned)((total_units + HS::NW - 1) / HS::NW) : full;
+    step_half_deep_kernel<Q, S, H, K, HS::NW, HS::NS, HS::MINB, true>
+        <<<grid, HS::NW * 32, HK::smem, st>>>(StepArgs{}, 0, 0, 0, items, n, total_units, emit ? 1 : 0);
+    return cudaGetLastError();
+}
+
+template <int H, int K>
+int64_t plan_qs(int Q, int S, DeepItem *items, int n) {
+    if (Q == 9 && S == 1) return plan_half_batch<9, 1, H, K>(items, n);
+    if (Q == 9 && S == 2) return plan_half_batch<9, 2, H, K>(items, n);
+    if (Q == 5 && S == 1) return plan_half_batch<5, 1, H, K>(items, n);
+    if (Q == 5 && S == 2) return plan_half_batch<5, 2, H, K>(items, n);
+    return -1;
+}
+
+template <int H, int K>
+cudaError_t launch_qs(int Q, int S, const DeepItem *items, int n, int64_t total_units, bool emit, cudaStream_t st) {
+    if (Q == 9 && S == 1) return launch_half_batch<9, 1, H, K>(items, n, total_units, emit, st);
+    if (Q == 9 && S == 2) return launch_half_batch<9, 2, H, K>(items, n, total_units, emit, st);
+    if (Q == 5 && S == 1) return launch_half_batch<5, 1, H, K>(items, n, total_units, emit, st);
+    if (Q == 5 && S == 2) return launch_half_batch<5, 2, H, K>(items, n, total_units, emit, st);
+    return cudaErrorInvalidValue;
+}
+
+template <int H>
+int64_t plan_k(int K, int Q, int S, DeepItem *items, int n) {
+    switch (K) {
+        case 2: return plan_qs<H, 2>(Q, S, items, n);
+        case 3: return plan_qs<H, 3>(Q, S, items, n);
+        case 4: return plan_qs<H, 4>(Q, S, items, n);
+        case 5: return plan_qs<H, 5>(Q, S, items, n);
+        default: return -1;
+    }
+}
+
+template <int H>
+cudaError_t launch_k(int K, int Q, int S, const DeepItem *items, int n, int64_t total_units, bool emit,
+                     cudaStream_t st) {
+    switch (K) {
+        case 2: return launch_qs<H, 2>(Q, S, items, n, total_units, emit, st);
+        case 3: return launch_qs<H, 3>(Q, S, items, n, total_units, emit, st);
+        case 4: return launch_qs<H, 4>(Q, S, items, n, total_units, emit, st);
+        case 5: return launch_qs<H, 5>(Q, S, items, n, total_units, emit, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+int64_t batch_half_deep_plan(int K, int Q, int S, int half_kind, DeepItem *items, int n) {
+    return half_kind ? plan_k<1>(K, Q, S, items, n) : plan_k<0>(K, Q, S, items, n);
+}
+
+cudaError_t launch_batch_half_deep(int K, int Q, int S, int half_kind, const DeepItem *items, int n,
+                                   int64_t total_units, bool emit, cudaStream_t st) {
+    return half_kind ? launch_k<1>(K, Q, S, items, n, total_units, emit, st)
+                     : launch_k<0>(K, Q, S, items, n, total_units, emit, st);
+}
+
+}  // namespace lbrd

@@ -79,7 +79,7 @@ def _cfg(**kw):
     (dict(tb_depth=-1), "tb_depth"),
     (dict(tb_depth=4, precision="fp64"), "tb_depth > 1"),
     (dict(tb_depth=2, inplace=True), "tb_depth > 1"),
-    (dict(tb_depth=6, precision="fp32_bf16dev"), "tb_depth > 1"),
+    (dict(tb_depth=3, nspecies=3, tau=(0.8,) * 3, reaction="none"), "tb_depth > 1"),
 ])
 def test_config_validation_rejects(lib, kw, msg):
     with pytest.raises(B.LbRdError) as ei:
@@ -133,6 +133,10 @@ def test_variant_table_on_the_host(lib):
     assert sum(B.variant_steps(x) == 1 for x in names) == 15  # 14 one-step kernels and deep1_
     assert all(B.variant_steps(x) == int(x[4]) for x in names if x.startswith("deep"))
     assert B.lb_rd_variant_count("fp64") == 1
+    half = [B.lb_rd_variant_name("fp32_bf16dev", v) for v in range(B.lb_rd_variant_count("fp32_bf16dev"))]
+    assert half == [B.lb_rd_variant_name("fp32_fp16dev", v) for v in range(len(half))]
+    assert sorted(set(B.variant_steps(x) for x in half)) == [1, 2, 3, 4, 5]
+    assert all(B.variant_steps(x) == int(x[5]) for x in half if x.startswith("hdeep"))
 
 
 def test_null_arguments_are_errors_not_crashes(lib):

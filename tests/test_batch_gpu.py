@@ -197,6 +197,31 @@ def test_batch_k_steps_per_launch_equals_single_handles(lat, K, staging, graph):
     assert launches == len(cfgs) + 2 * (steps // K + (1 if steps % K else 0))
 
 
+@pytest.mark.parametrize("precision", ["fp32_bf16dev", "fp32_fp16dev"])
+@pytest.mark.parametrize("K", [2, 3, 4, 5])
+def test_batch_half_k_steps_per_launch_equals_single_handles(precision, K):
+    """16-bit deviation storage: K = 2 .. 5 steps per launch run its depth-K
+    kernel over the (band, strip) units of all instances (each level holds
+    rho* and the deviations rounded as a single step stores them); each
+    instance gives the bits of a single handle (which runs single steps),
+    over calls of 21 steps (21 // K launches of K and one of the rest)."""
+    shapes = [(64, 48), (100, 37), (36, 70), (8, 3), (256, 16), (68, 9)]
+    cfgs = [dict(lattice="D2Q9", nspecies=2, nx=nx, ny=ny, tau=[0.8 + 0.05 * j, 0.65], reaction="gray_scott",
+                 F=0.03 + 0.004 * j, k=0.06 - 0.002 * j, precision=precision) for j, (nx, ny) in enumerate(shapes)]
+    steps = 21
+    with B.Batch(cfgs) as b:
+        b.set_steps_per_launch(K)
+        for j, c in enumerate(cfgs):
+            b.init(j, _rho0(c, j))
+        b.step(steps).step(steps)
+        _, launches = B.lb_rd_batch_get_time(b.b)
+        for j, c in enumerate(cfgs):
+            rho, _ = b.moments(j)
+            ref_rho, _ = _single(dict(c, tb_depth=1), _rho0(c, j), 2 * steps)
+            np.testing.assert_array_equal(rho, ref_rho, err_msg=f"instance {j}")
+    assert launches == len(cfgs) + 2 * (steps // K + (1 if steps % K else 0))
+
+
 def test_batch_steps_per_launch_switch():
     cfgs = _configs("fp32")  # includes nx not a multiple of 256
     with B.Batch(cfgs) as b:

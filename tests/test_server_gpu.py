@@ -71,10 +71,10 @@ def test_results_identical_alone_and_in_the_mix():
 
 @pytest.mark.parametrize("tick", [5, 16, 64])
 def test_d2q5_k_step_ticks_equal_single_handles(tick):
-    """A D2Q5 server: ticks advance the resident requests by four-step
-    launches of the depth-K kernel (nx % 4 != 0 among them: 4-byte staging
-    for the whole tick) and one launch of the steps left; every result is
-    bitwise a single handle's."""
+    """A D2Q5 server: ticks advance the resident requests by six-step
+    launches of the two-column depth-K kernel (nx % 4 != 0 among them: the
+    chunks at the periodic seam copied column by column) and one launch of
+    the steps left; every result is bitwise a single handle's."""
     sides = [(64, 41), (36, 17), (70, 9), (128, 30)]
     reqs = []
     for j, (side, steps) in enumerate(sides):
@@ -94,13 +94,13 @@ def test_d2q5_k_step_ticks_equal_single_handles(tick):
         B.lb_rd_server_destroy(srv)
 
 
-@pytest.mark.parametrize("tick,launches", [(64, 11), (13, 3), (6, 1), (5, 1), (1, 1)])
+@pytest.mark.parametrize("tick,launches", [(64, 16), (63, 16), (14, 4), (6, 2), (5, 2), (1, 1)])
 def test_d2q9_tick_launches(tick, launches):
-    """One D2Q9 request of `tick` steps is one tick: tick // 6 six-step
-    launches and one launch of the tick % 6 steps left (a single step when
-    one is left), the last writing the densities: a 64-step tick is ten
-    six-step launches and one four-step launch, with no single step.  The
-    result is bitwise a single handle's."""
+    """One D2Q9 request of `tick` steps (the two-column depth-K kernel,
+    K = 4) is one tick: tick // 4 four-step launches and one launch of the
+    tick % 4 steps left (a single step when one is left), the last writing
+    the densities: a 64-step tick is sixteen four-step launches, with no
+    single step.  The result is bitwise a single handle's."""
     kw, rho0, _ = _request(3, 96, 1, tick)
     srv = B.lb_rd_server_create(hbm_budget_bytes=1 << 30, max_slots=4, steps_per_tick=tick)
     try:
@@ -229,3 +229,28 @@ def test_inplace_requests_mix_and_double_the_residents():
             assert (s2["start_ns"] < s1["end_ns"]) == concurrent, (inplace, s1, s2)
         finally:
             B.lb_rd_server_destroy(srv)
+
+
+@pytest.mark.parametrize("precision", ["fp32_bf16dev", "fp32_fp16dev"])
+def test_half_storage_requests_equal_single_handles(precision):
+    """A server of 16-bit deviation storage: ticks run the 16-bit depth-K
+    kernel (K = 4 steps per launch, one launch for the rest) over all
+    resident requests; every result is bitwise a single handle's (which runs
+    single steps: each level rounds the deviations as a single step stores
+    them)."""
+    sides = [(64, 41), (36, 17), (68, 9), (128, 30)]
+    reqs = []
+    for j, (side, steps) in enumerate(sides):
+        kw, rho0, _ = _request(60 + j, side, 1 + j % 2, steps)
+        reqs.append((dict(kw, precision=precision), rho0, steps))
+    srv = B.lb_rd_server_create(hbm_budget_bytes=1 << 30, max_slots=4, steps_per_tick=16, precision=precision)
+    try:
+        tickets = [B.lb_rd_submit(srv, B.make_config(**kw), rho0, steps) for kw, rho0, steps in reqs]
+        for (kw, rho0, steps), t in zip(reqs, tickets):
+            rc, rho, mass, _ = _wait(srv, t, 2, kw["nx"])
+            assert rc == B.LB_RD_OK
+            ref_rho, _ = _alone(dict(kw, tb_depth=1), rho0, steps)
+            np.testing.assert_array_equal(rho, ref_rho)
+        assert B.lb_rd_server_stats(srv)["launches"] < sum(r[2] for r in reqs) // 2
+    finally:
+        B.lb_rd_server_destroy(srv)

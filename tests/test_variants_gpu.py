@@ -149,7 +149,7 @@ def test_tb_depth_config_field():
             sim.init(rho0).step(23)
             np.testing.assert_array_equal(sim.moments()[0], want, err_msg=f"tb_depth {d}")
     with pytest.raises(B.LbRdError) as ei:
-        B.Simulation(**dict(kw, nx=70), tb_depth=6)  # depth 6 only with 16-byte staging (nx % 4 == 0)
+        B.Simulation(**dict(kw, nx=70), tb_depth=7)  # depth 7 only with 16-byte staging (nx % 4 == 0)
     assert ei.value.status == B.LB_RD_EINVAL
 
 
