@@ -318,7 +318,7 @@ def serving_mode(args):
 
     # continuous batching
     srv = B.lb_rd_server_create(hbm_budget_bytes=int(args.budget_gb * 1e9), max_slots=args.slots,
-                                steps_per_tick=args.tick)
+                                steps_per_tick=args.tick, tick_sites=args.tick_sites)
     t0 = time.perf_counter()
     tickets = []
     for j in range(nreq):
@@ -346,7 +346,7 @@ def serving_mode(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "gs_serving", "requests": nreq, "steps_scale": args.steps_scale,
                        "load": args.load, "capacity_mlups": args.capacity_mlups, "budget_gb": args.budget_gb,
-                       "slots": args.slots, "steps_per_tick": args.tick,
+                       "slots": args.slots, "steps_per_tick": args.tick, "tick_sites": args.tick_sites,
                        "arrival_rate_per_s": rate if args.load > 0 else None,
                        "inplace_requests": int(sum(1 for j in range(nreq) if cfg(j)["inplace"])),
                        "total_ssu": float(total), "makespan_s": makespan},
@@ -676,6 +676,9 @@ def main():
     ap.add_argument("--slots", type=int, default=64)
     ap.add_argument("--tick", type=int, default=64)
     ap.add_argument("--no-fifo", action="store_true", help="serving mode: skip the FIFO plain-loop baseline")
+    ap.add_argument("--tick-sites", type=int, default=0,
+                    help="serving mode: ticks advance the least-remaining-work requests making up this many sites "
+                         "(0: every resident request, every tick)")
     ap.add_argument("--fifo-tune-iters", type=int, default=1,
                     help="serving mode: autotuner iterations per grid side for the FIFO loop's handles")
     args = ap.parse_args()

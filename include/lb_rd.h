@@ -358,6 +358,12 @@ typedef struct {
     int32_t steps_per_tick;   /* steps between admission points, >= 1 */
     int32_t lattice, nspecies, precision;
     void *stream;             /* NULL: the server creates its own stream */
+    int64_t tick_sites;       /* 0: every resident request advances in every tick (processor sharing);
+                                 > 0: a tick advances the resident requests with the least remaining work
+                                 (sites x steps left) first, as many as make up at least tick_sites sites
+                                 together (all if fewer), the others waiting for a later tick: short
+                                 requests finish sooner, a long one can wait while shorter ones keep
+                                 arriving */
 } lb_rd_server_config;
 
 typedef struct {

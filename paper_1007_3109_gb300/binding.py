@@ -379,7 +379,8 @@ def lb_rd_batch_get_time(b: int):
 
 class lb_rd_server_config(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", c_size_t), ("max_slots", c_int32), ("steps_per_tick", c_int32),
-                ("lattice", c_int32), ("nspecies", c_int32), ("precision", c_int32), ("stream", c_void_p)]
+                ("lattice", c_int32), ("nspecies", c_int32), ("precision", c_int32), ("stream", c_void_p),
+                ("tick_sites", c_int64)]
 
 
 class lb_rd_request_stats(ctypes.Structure):
@@ -388,9 +389,9 @@ class lb_rd_request_stats(ctypes.Structure):
 
 
 def lb_rd_server_create(hbm_budget_bytes, max_slots=64, steps_per_tick=64, lattice="D2Q9", nspecies=2,
-                        precision="fp32", stream=None) -> int:
+                        precision="fp32", stream=None, tick_sites=0) -> int:
     cfg = lb_rd_server_config(int(hbm_budget_bytes), int(max_slots), int(steps_per_tick), LATTICES[lattice],
-                              int(nspecies), PRECISIONS[precision], stream)
+                              int(nspecies), PRECISIONS[precision], stream, int(tick_sites))
     s = c_void_p()
     _check(lib().lb_rd_server_create(ctypes.byref(cfg), ctypes.byref(s)))
     return s.value
@@ -434,10 +435,10 @@ class Server:
     """Owner of one lb_rd_server (continuous batching of simulation requests)."""
 
     def __init__(self, hbm_budget_bytes, max_slots=64, steps_per_tick=64, lattice="D2Q9", nspecies=2,
-                 precision="fp32", stream=None):
+                 precision="fp32", stream=None, tick_sites=0):
         self.nspecies = int(nspecies)
         self.s = lb_rd_server_create(hbm_budget_bytes, max_slots, steps_per_tick, lattice, nspecies, precision,
-                                     stream)
+                                     stream, tick_sites)
         self._shape = {}
 
     def submit(self, rho0, nsteps, **config) -> int:

@@ -219,8 +219,36 @@ int ensure_deep(lb_rd_server *s, size_t n) {
     return LB_RD_OK;
 }
 
+// The resident requests one tick advances: all of them, or with tick_sites
+// > 0 those with the least remaining work (sites x steps left) first, as
+// many as make up at least tick_sites sites together.
+std::vector<Request *> pick_tick_set(const lb_rd_server *s) {
+    std::vector<Request *> v = s->active;
+    if (s->cfg.tick_sites <= 0 || v.size() < 2) return v;
+    std::stable_sort(v.begin(), v.end(), [](const Request *a, const Request *b) {
+        return (double)a->cfg.nx * (double)a->cfg.ny * (double)a->remaining <
+               (double)b->cfg.nx * (double)b->cfg.ny * (double)b->remaining;
+    });
+    int64_t sites = 0;
+    size_t k = 0;
+    while (k < v.size() && sites < s->cfg.tick_sites) {
+        sites += v[k]->cfg.nx * v[k]->cfg.ny;
+        ++k;
+    }
+    v.resize(k);
+    return v;
+}
+
+// Drops the finished requests from the resident list.
+void prune_active(lb_rd_server *s) {
+    std::vector<Request *> still;
+    for (Request *r : s->active)
+        if (r->state != kDone) still.push_back(r);
+    s->active.swap(still);
+}
+
 void run_tick(lb_rd_server *s) {
-    std::vector<Request *> &act = s->active;
+    std::vector<Request *> act = pick_tick_set(s);
     const size_t n = act.size();
     int64_t tick = s->cfg.steps_per_tick;
     for (Request *r : act) tick = std::min(tick, r->remaining);
@@ -229,7 +257,7 @@ void run_tick(lb_rd_server *s) {
             release(s, r);
             finish(s, r, LB_RD_ENOMEM);
         }
-        act.clear();
+        prune_active(s);
         return;
     }
     // K-step launches: FP32 and 16-bit deviation requests with two state
@@ -352,7 +380,6 @@ void run_tick(lb_rd_server *s) {
     }
     if (!e) e = cudaStreamSynchronize(s->stream);  // the pinned descriptors are reused next tick
     s->ticks++;
-    std::vector<Request *> keep;
     for (Request *r : act) {
         if (e) {
             release(s, r);
@@ -361,15 +388,12 @@ void run_tick(lb_rd_server *s) {
         }
         r->cur = (int)((r->cur + L) & 1);
         r->remaining -= tick;
-        if (r->remaining > 0) {
-            keep.push_back(r);
-            continue;
-        }
+        if (r->remaining > 0) continue;
         const int st = collect_request(s, r);
         release(s, r);
         finish(s, r, st);
     }
-    act.swap(keep);
+    prune_active(s);
 }
 
 void worker_main(lb_rd_server *s) {
@@ -416,8 +440,9 @@ extern "C" {
 int lb_rd_server_create(const lb_rd_server_config *cfg, lb_rd_server **out) {
     if (!cfg || !out) return lbrd::report_error(LB_RD_EINVAL, "lb_rd_server_create: NULL argument");
     *out = nullptr;
-    if (cfg->max_slots < 1 || cfg->steps_per_tick < 1 || cfg->hbm_budget_bytes == 0)
-        return lbrd::report_error(LB_RD_EINVAL, "lb_rd_server_create: need max_slots >= 1, steps_per_tick >= 1, budget > 0");
+    if (cfg->max_slots < 1 || cfg->steps_per_tick < 1 || cfg->hbm_budget_bytes == 0 || cfg->tick_sites < 0)
+        return lbrd::report_error(LB_RD_EINVAL, "lb_rd_server_create: need max_slots >= 1, steps_per_tick >= 1, "
+                                                "budget > 0, tick_sites >= 0");
     if (cfg->lattice != LB_RD_D2Q9 && cfg->lattice != LB_RD_D2Q5)
         return lbrd::report_error(LB_RD_EINVAL, "lb_rd_server_create: unknown lattice");
     if (cfg->nspecies < 1 || cfg->nspecies > 2)

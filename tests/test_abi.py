@@ -119,6 +119,8 @@ def test_server_and_batch_reject_bad_configs_on_the_host(lib):
     assert lib.lb_rd_server_create(B.ctypes.byref(cfg), B.ctypes.byref(out)) == B.LB_RD_EINVAL
     cfg = B.lb_rd_server_config(1 << 30, 4, 8, 0, 3, 0, None)  # three species
     assert lib.lb_rd_server_create(B.ctypes.byref(cfg), B.ctypes.byref(out)) == B.LB_RD_EINVAL
+    cfg = B.lb_rd_server_config(1 << 30, 4, 8, 0, 2, 1, None, -1)  # negative tick_sites
+    assert lib.lb_rd_server_create(B.ctypes.byref(cfg), B.ctypes.byref(out)) == B.LB_RD_EINVAL
     assert lib.lb_rd_batch_create(None, 0, B.ctypes.byref(out)) == B.LB_RD_EINVAL
     assert lib.lb_rd_poll(None, 1, None, None, None) == B.LB_RD_EINVAL
 

@@ -254,3 +254,26 @@ def test_half_storage_requests_equal_single_handles(precision):
         assert B.lb_rd_server_stats(srv)["launches"] < sum(r[2] for r in reqs) // 2
     finally:
         B.lb_rd_server_destroy(srv)
+
+
+def test_least_remaining_work_ticks():
+    """tick_sites > 0: each tick advances the requests with the least
+    remaining work (sites x steps left) first, enough of them to make up
+    tick_sites sites; the others wait.  Every request still finishes with
+    the bits of a single handle, and a short request submitted beside long
+    ones finishes first."""
+    reqs = [_request(70, 128, 1, 600), _request(71, 128, 2, 600), _request(72, 96, 1, 20),
+            _request(73, 64, 4, 300), _request(74, 100, 1, 45)]
+    srv = B.lb_rd_server_create(hbm_budget_bytes=1 << 30, max_slots=8, steps_per_tick=16, tick_sites=20000)
+    try:
+        tickets = [B.lb_rd_submit(srv, B.make_config(**kw), rho0, steps) for kw, rho0, steps in reqs]
+        ends = {}
+        for (kw, rho0, steps), t in zip(reqs, tickets):
+            rc, rho, _, st = _wait(srv, t, 2, kw["nx"])
+            assert rc == B.LB_RD_OK and st["steps"] == steps
+            ref_rho, _ = _alone(kw, rho0, steps)
+            np.testing.assert_array_equal(rho, ref_rho)
+            ends[steps] = st["end_ns"]
+        assert ends[20] < ends[600]
+    finally:
+        B.lb_rd_server_destroy(srv)
