@@ -743,15 +743,37 @@ def main():
 
     # -- device-timed region: K step launches and nothing else, bracketed by
     # CUDA events on the launching stream ------------------------------------
-    launches0 = B.lb_rd_launch_count(sim.h)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # The clock samples (every 200 ms) span the timed region and, under the
+    # same load, an untimed stretch of the same calls before it and the
+    # per-launch-timed repeats after it: a short timed region alone can fall
+    # between two samples.
     with ClockSampler(local) as clocks:
+        t_pre = time.perf_counter()
+        while time.perf_counter() - t_pre < 0.5:
+            B.lb_rd_step(sim.h, args.steps)
+            torch.cuda.synchronize()
+        launches0 = B.lb_rd_launch_count(sim.h)
         barrier()
         ev0.record(stream)
         B.lb_rd_step(sim.h, args.steps)
         ev1.record(stream)
         barrier()
-    launches = B.lb_rd_launch_count(sim.h) - launches0
+        launches = B.lb_rd_launch_count(sim.h) - launches0
+        # the timed call repeated with per-launch CUDA events on the launching
+        # stream (lb_rd_launch_times): the same launch plan, each launch timed
+        # on its own; enough repetitions for >= 30 launches of the dominant kernel
+        reps = max(1, -(-30 // max(launches, 1)))
+        B.lb_rd_set_timing(sim.h, True)
+        t_rep = time.perf_counter()
+        while True:
+            for _ in range(reps):
+                B.lb_rd_step(sim.h, args.steps)
+            torch.cuda.synchronize()
+            if time.perf_counter() - t_rep >= 0.5:
+                break
+        l_ms, l_steps, l_var = B.lb_rd_launch_times(sim.h)
+        B.lb_rd_set_timing(sim.h, False)
     ms_total = ev0.elapsed_time(ev1)
     steps_per_launch = args.steps / max(launches, 1)
     sites = n * n
@@ -762,20 +784,13 @@ def main():
     value = work / (ms_total / 1e3) / 1e6
 
     # -- roofline of the dominant kernel -----------------------------------------
-    # The timed call repeated with per-launch CUDA events on the launching stream
-    # (lb_rd_launch_times): the same launch plan, each launch timed on its own.
-    # The dominant kernel is the (variant, steps per launch) pair with the most
-    # device time; its achieved bandwidth is the algorithmic bytes of one launch
-    # (one read and one write of the state, bps per site) over its mean launch
-    # time.  Enough repetitions for >= 30 launches of it.
+    # From the per-launch events above: the dominant kernel is the (variant,
+    # steps per launch) pair with the most device time; its achieved bandwidth
+    # is the algorithmic bytes of one launch (one read and one write of the
+    # state, bps per site) over its mean launch time.
     peak, peak_kind = measured_peaks()
     bps = BYTES_PER_SITE[(args.lattice, args.precision, 2)]
-    reps = max(1, -(-30 // max(launches, 1)))
-    B.lb_rd_set_timing(sim.h, True)
-    for _ in range(reps):
-        B.lb_rd_step(sim.h, args.steps)
-    l_ms, l_steps, l_var = B.lb_rd_launch_times(sim.h)
-    B.lb_rd_set_timing(sim.h, False)
+    reps = len(l_ms) // max(launches, 1)
     by_kernel = {}
     for t, d, v in zip(l_ms, l_steps, l_var):
         e = by_kernel.setdefault((names[v], d), [0.0, 0])
@@ -877,6 +892,8 @@ def main():
                      "steps_per_launch": dom_steps, "bytes_per_site_per_launch": bps,
                      "avg_launch_ms": avg_launch_s * 1e3, "launches_timed": dom_n,
                      "timing": f"per-launch CUDA events on the launching stream, the timed call repeated {reps}x",
+                     "clock_samples": "nvidia-smi every 200 ms over the timed region, 0.5 s of the same calls before "
+                                      "it and the per-launch-timed repeats after it",
                      "launch_plan": launch_plan, "mean_steps_per_launch": steps_per_launch,
                      "effective_per_step_GBs": effective, "effective_frac": effective / peak,
                      "peak_kind": peak_kind, "single_step": single,

@@ -318,7 +318,7 @@ LB_RD_API int lb_rd_batch_set_graph(lb_rd_batch *b, int32_t steps_per_graph);
  * values >= 2 (and 2 otherwise) run the depth-K kernel over the (band, strip)
  * units of all instances (FP32, two state copies, any nx; bitwise the same as
  * K single steps; for K <= 5 (D2Q9) or 6 (D2Q5) its form with two columns per
- * lane; the default for such batches: 4 for D2Q9, 6 for D2Q5); 16-bit
+ * lane; the default for such batches: 5 for D2Q9, 6 for D2Q5); 16-bit
  * deviation storage runs its own depth-K kernel, K = 2 .. 5 (default 4).
  * EINVAL if neither applies.  1: one step per launch (the default for other
  * batches).  The graphs of lb_rd_batch_set_graph hold steps_per_graph / K
@@ -340,7 +340,7 @@ LB_RD_API int lb_rd_batch_get_time(const lb_rd_batch *b, int64_t *t, int64_t *la
  * Resident requests advance together, steps_per_tick steps at a time (fewer
  * when a request finishes sooner), by launches of the batched kernels over
  * all of them: for FP32 and 16-bit deviation requests with two state copies,
- * tick / K launches of the depth-K kernel (K as the batches' default: 4 for
+ * tick / K launches of the depth-K kernel (K as the batches' default: 5 for
  * D2Q9 and 6 for D2Q5 in FP32, 4 in 16-bit storage) and one launch of the
  * tick % K
  * steps left (a single step if one is left), otherwise one launch per step;

@@ -406,7 +406,7 @@ int lb_rd_batch_create(const lb_rd_config *cfgs, int32_t n, lb_rd_batch **out) {
             b->deep_base[i].a = items[i].a;
             b->deep_base[i].a.rho_out = b->rho + b->rho_off[i];
         }
-        // default: the depth-K kernel, K = 4 (D2Q9) or 6 (D2Q5) in its
+        // default: the depth-K kernel, K = 5 (D2Q9) or 6 (D2Q5) in its
         // two-column form, K = 4 for 16-bit deviation storage; should its
         // descriptors not be planned (no launch shape for this device), the
         // batch keeps the previous default

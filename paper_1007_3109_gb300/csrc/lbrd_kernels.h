@@ -178,9 +178,9 @@ int64_t batch_half_deep_plan(int K, int Q, int S, int half_kind, DeepItem *items
 cudaError_t launch_batch_half_deep(int K, int Q, int S, int half_kind, const DeepItem *items, int n,
                                    int64_t total_units, bool emit, cudaStream_t st);
 bool batch_deep_depth_ok(int K);
-// Default steps per launch of a list of grids: 4 (D2Q9) / 6 (D2Q5), the
-// deepest two-column forms that keep every carried level in registers when
-// the grid's parameters come from a descriptor (K = 5 D2Q9 spills there).
+// Default steps per launch of a list of grids: 5 (D2Q9) / 6 (D2Q5), the
+// fastest two-column forms over a list (the grid's parameters read from a
+// per-warp shared copy where they are used).
 int batch_deep_default_k(int Q);
 int64_t batch_deep_plan(int K, int Q, int S, bool v16, DeepItem *items, int n);
 cudaError_t launch_batch_deep(int K, int Q, int S, bool v16, const DeepItem *items, int n, int64_t total_units,

@@ -8,7 +8,7 @@
 //   2. advances every resident request by one tick of up to steps_per_tick
 //      steps (never past the earliest finishing request): FP32 requests with
 //      two state copies by K-step launches of the depth-K kernel over all
-//      resident requests (K = 4 for D2Q9, 6 for D2Q5: the two-column form;
+//      resident requests (K = 5 for D2Q9, 6 for D2Q5: the two-column form;
 //      16-bit deviation storage its own kernel, K = 4) and one shorter
 //      depth-K launch for the steps left (a single step if one is left),
 //      other requests one batched launch per step; the tick's last launch

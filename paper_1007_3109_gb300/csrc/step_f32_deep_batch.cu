@@ -149,7 +149,7 @@ cudaError_t launch_v(int Q, int S, bool v16, const DeepItem *items, int n, int64
 
 bool batch_deep_depth_ok(int K) { return K >= 2 && K <= 8; }
 
-int batch_deep_default_k(int Q) { return Q == 9 ? 4 : 6; }
+int batch_deep_default_k(int Q) { return Q == 9 ? 5 : 6; }
 
 int64_t batch_deep_plan(int K, int Q, int S, bool v16, DeepItem *items, int n) {
     switch (K) {

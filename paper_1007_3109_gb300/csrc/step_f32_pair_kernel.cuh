@@ -54,6 +54,19 @@ __device__ __forceinline__ void cp_async4s(unsigned dst, const float *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
 }
 
+// Volatile shared-memory loads: a list's grid parameters are read from the
+// warp's shared copy where they are used (never hoisted into registers).
+__device__ __forceinline__ unsigned long long lds_v64(const void *p) {
+    unsigned long long v;
+    asm volatile("ld.volatile.shared.u64 %0, [%1];\n" : "=l"(v) : "r"(static_cast<unsigned>(__cvta_generic_to_shared(p))));
+    return v;
+}
+__device__ __forceinline__ unsigned lds_v32(const void *p) {
+    unsigned v;
+    asm volatile("ld.volatile.shared.u32 %0, [%1];\n" : "=r"(v) : "r"(static_cast<unsigned>(__cvta_generic_to_shared(p))));
+    return v;
+}
+
 template <int K>
 struct PairGeom {
     static constexpr int HL = (K + 1) / 2 * 2;  // left (and right) halo columns of the window, even
@@ -84,6 +97,46 @@ __global__ void __launch_bounds__(NW * 32, MINB)
         load_seg(a, g);
         if (!emit) g.rho_out = nullptr;
     }
+    // BATCH: the unit's grid parameters, one copy per warp, read where they
+    // are used so that they hold no registers across the row loop (a single
+    // grid reads them from the kernel's parameter space)
+    __shared__ SegArgs seg_sh[BATCH ? NW : 1];
+    SegArgs &gs = seg_sh[BATCH ? w : 0];
+    auto p_src = [&]() -> const float * {
+        if constexpr (BATCH) return reinterpret_cast<const float *>(lds_v64(&gs.src));
+        else return static_cast<const float *>(a.src);
+    };
+    auto p_dst = [&]() -> float * {
+        if constexpr (BATCH) return reinterpret_cast<float *>(lds_v64(&gs.dst));
+        else return static_cast<float *>(a.dst);
+    };
+    auto p_rho = [&]() -> float * {
+        if constexpr (BATCH) return reinterpret_cast<float *>(lds_v64(&gs.rho_out));
+        else return emit ? static_cast<float *>(a.rho_out) : nullptr;
+    };
+    auto p_pitch = [&]() -> int64_t {
+        if constexpr (BATCH) return (int64_t)lds_v64(&gs.pitch);
+        else return a.pitch;
+    };
+    auto p_plane = [&]() -> int64_t {
+        if constexpr (BATCH) return (int64_t)lds_v64(&gs.plane);
+        else return a.plane;
+    };
+    // relaxation and reaction constants of the collisions
+    auto p_coll = [&]() -> SegArgs {
+        if constexpr (BATCH) {
+            SegArgs c;
+            c.omega[0] = __uint_as_float(lds_v32(&gs.omega[0]));
+            c.omega[1] = __uint_as_float(lds_v32(&gs.omega[1]));
+            c.rkind = (int)lds_v32(&gs.rkind);
+            c.kappa = __uint_as_float(lds_v32(&gs.kappa));
+            c.F = __uint_as_float(lds_v32(&gs.F));
+            c.k = __uint_as_float(lds_v32(&gs.k));
+            return c;
+        } else {
+            return g;
+        }
+    };
     double acc[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[s] = 0.0;
@@ -100,9 +153,10 @@ __global__ void __launch_bounds__(NW * 32, MINB)
             local = u - items[it].unit_begin;
             ns = items[it].nstrips;
             bh = items[it].band;
+            __syncwarp();  // the previous unit's reads of gs are done
+            if (lane == 0) gs = g;
+            __syncwarp();
         }
-        const float *__restrict__ src = static_cast<const float *>(g.src);
-        float *__restrict__ dst = static_cast<float *>(g.dst);
         // rows and columns fit 32 bits (sides <= 65535); plane offsets need 64
         const int nx = (int)g.nx, ny = (int)g.ny;
         const int64_t b = local / ns, strip = local - b * ns;
@@ -122,10 +176,10 @@ __global__ void __launch_bounds__(NW * 32, MINB)
         int yl = (int)wrap_mod(y0 - K, ny);
         auto stage = [&](int j, int slot) {
             if (j < nrows) {
-                const float *row = src + (int64_t)yl * g.pitch;
+                const float *row = p_src() + (int64_t)yl * p_pitch();
                 const unsigned d = ring_s + (unsigned)(slot * kRow + cpar * CW + 4 * cch) * 4u;
                 const float *sp = row + offA;
-                int64_t pl2 = 2 * g.plane;
+                int64_t pl2 = 2 * p_plane();
                 asm volatile("" : "+l"(pl2));  // no plane multiples kept live across the row loop
                 if (!ANY || cleanA) {
 #pragma unroll
@@ -210,8 +264,11 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                     f0[s][i] = L::ex(i) > 0 ? __shfl_up_sync(kFullMask, v.y, 1) : (L::ex(i) < 0 ? v.y : v.x);
                     f1[s][i] = L::ex(i) > 0 ? v.x : (L::ex(i) < 0 ? __shfl_down_sync(kFullMask, v.x, 1) : v.y);
                 }
-            collide_site<Q, S>(g, f0, rho0);
-            collide_site<Q, S>(g, f1, rho1);
+            {
+                const SegArgs cg = p_coll();
+                collide_site<Q, S>(cg, f0, rho0);
+                collide_site<Q, S>(cg, f1, rho1);
+            }
 #pragma unroll
             for (int m = 1; m < K; ++m) {  // level m + 1 from level m (carried index m - 1)
                 if constexpr (PP) {
@@ -268,26 +325,26 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                             f1[s][i] = h1[s][i];
                         }
                 }
-                collide_site<Q, S>(g, f0, rho0);
-                collide_site<Q, S>(g, f1, rho1);
+                const SegArgs cg = p_coll();
+                collide_site<Q, S>(cg, f0, rho0);
+                collide_site<Q, S>(cg, f1, rho1);
             }
             if (j >= 2 * K) {  // level K of row y0 + j - 2K: window columns HL .. 63 - HL
                 const int x = xb + 2 * lane;
                 if (lane >= HL / 2 && lane < (HL + WO) / 2 && x < nx) {
                     const int y = y0 + j - 2 * K;
-                    int64_t pl = g.plane;
+                    int64_t pl = p_plane();
                     asm volatile("" : "+l"(pl));  // no plane multiples kept live across the row loop
-                    const int64_t yx = (int64_t)y * g.pitch + x;
-                    float *dp = dst + yx;
+                    const int64_t yx = (int64_t)y * p_pitch() + x;
+                    float *dp = p_dst() + yx;
+                    float *rp = p_rho();
                     if (!ANY || x + 1 < nx) {  // both columns (x is even: 8-byte stores)
 #pragma unroll
                         for (int s = 0; s < S; ++s) {
 #pragma unroll
                             for (int i = 0; i < Q; ++i)
                                 *reinterpret_cast<float2 *>(dp + (s * Q + i) * pl) = make_float2(f0[s][i], f1[s][i]);
-                            if (g.rho_out)
-                                *reinterpret_cast<float2 *>(static_cast<float *>(g.rho_out) + s * pl + yx) =
-                                    make_float2(rho0[s], rho1[s]);
+                            if (rp) *reinterpret_cast<float2 *>(rp + s * pl + yx) = make_float2(rho0[s], rho1[s]);
                             sum[s] += rho0[s] + rho1[s];
                         }
                     } else if constexpr (ANY) {  // the last column of an odd nx
@@ -295,7 +352,7 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                         for (int s = 0; s < S; ++s) {
 #pragma unroll
                             for (int i = 0; i < Q; ++i) dp[(s * Q + i) * pl] = f0[s][i];
-                            if (g.rho_out) static_cast<float *>(g.rho_out)[s * pl + yx] = rho0[s];
+                            if (rp) rp[s * pl + yx] = rho0[s];
                             sum[s] += rho0[s];
                         }
                     }

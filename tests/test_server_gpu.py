@@ -94,13 +94,14 @@ def test_d2q5_k_step_ticks_equal_single_handles(tick):
         B.lb_rd_server_destroy(srv)
 
 
-@pytest.mark.parametrize("tick,launches", [(64, 16), (63, 16), (14, 4), (6, 2), (5, 2), (1, 1)])
+@pytest.mark.parametrize("tick,launches", [(64, 13), (65, 13), (13, 3), (6, 2), (5, 1), (1, 1)])
 def test_d2q9_tick_launches(tick, launches):
     """One D2Q9 request of `tick` steps (the two-column depth-K kernel,
-    K = 4) is one tick: tick // 4 four-step launches and one launch of the
-    tick % 4 steps left (a single step when one is left), the last writing
-    the densities: a 64-step tick is sixteen four-step launches, with no
-    single step.  The result is bitwise a single handle's."""
+    K = 5) is one tick: tick // 5 five-step launches and one launch of the
+    tick % 5 steps left (a single step when one is left), the last writing
+    the densities: a 64-step tick is twelve five-step launches and one
+    four-step launch, with no single step.  The result is bitwise a single
+    handle's."""
     kw, rho0, _ = _request(3, 96, 1, tick)
     srv = B.lb_rd_server_create(hbm_budget_bytes=1 << 30, max_slots=4, steps_per_tick=tick)
     try:
