@@ -101,6 +101,32 @@ __device__ __forceinline__ void reaction_f32(int kind, float kappa, float F, flo
     }
 }
 
+// The reactions of two sites under one test of the kind (the expressions of
+// reaction_f32 site by site, so the same bits).  RK >= 0 fixes the kind at
+// compile time (the caller has checked that kind == RK).
+template <int S, int RK = -1>
+__device__ __forceinline__ void reaction2_f32(int kind, float kappa, float F, float k, const float (&r0)[S],
+                                              const float (&r1)[S], float (&R0)[S], float (&R1)[S]) {
+    const int kd = RK >= 0 ? RK : kind;
+#pragma unroll
+    for (int s = 0; s < S; ++s) R0[s] = R1[s] = 0.f;
+    if (kd == kLinear) {
+        R0[0] = -kappa * r0[0];
+        R1[0] = -kappa * r1[0];
+        if (S == 2) {
+            R0[S - 1] = kappa * r0[0];
+            R1[S - 1] = kappa * r1[0];
+        }
+    } else if (kd == kGrayScott && S == 2) {
+        const float u0 = r0[0], v0 = r0[S - 1], u1 = r1[0], v1 = r1[S - 1];
+        const float uvv0 = u0 * v0 * v0, uvv1 = u1 * v1 * v1;
+        R0[0] = F * (1.f - u0) - uvv0;
+        R1[0] = F * (1.f - u1) - uvv1;
+        R0[S - 1] = uvv0 - (F + k) * v0;
+        R1[S - 1] = uvv1 - (F + k) * v1;
+    }
+}
+
 // FP64 path: every operation rounded on its own (no FMA), in the order
 // (u v) v;  (-uvv) + F (1 - u);  uvv - (F + k) v;  -kappa rho_A;  kappa rho_A.
 template <int S>

@@ -168,6 +168,8 @@ cudaError_t launch_batch_tb2(const TbwItem *items, int n, int64_t total_units, i
 // or -1 for an unsupported K.  v16: every grid has nx
 // and pitch multiples of 4 (16-byte staging).  emit: the launch also writes
 // rho(t + K) of every item to its a.rho_out (the last launch of a call).
+// rk: the reaction kind that every item has (a.rkind), or -1 when they differ
+// (list_reaction_kind); selects a kernel with the kind fixed at compile time.
 struct DeepItem {
     StepArgs a;
     int64_t unit_begin, nstrips, band;
@@ -184,7 +186,14 @@ bool batch_deep_depth_ok(int K);
 int batch_deep_default_k(int Q);
 int64_t batch_deep_plan(int K, int Q, int S, bool v16, DeepItem *items, int n);
 cudaError_t launch_batch_deep(int K, int Q, int S, bool v16, const DeepItem *items, int n, int64_t total_units,
-                              bool emit, cudaStream_t st);
+                              bool emit, int rk, cudaStream_t st);
+// The reaction kind every item of a host-side list has, or -1.
+inline int list_reaction_kind(const DeepItem *items, int n) {
+    if (n <= 0) return -1;
+    for (int i = 1; i < n; ++i)
+        if (items[i].a.rkind != items[0].a.rkind) return -1;
+    return items[0].a.rkind;
+}
 int64_t batch_tiles_x(int64_t nx);
 int64_t batch_tiles(int64_t nx, int64_t ny);
 // mode: 0 FP32 storage, 1 bf16 deviations, 2 fp16 deviations, 3 FP64,

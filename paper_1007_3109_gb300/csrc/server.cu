@@ -361,17 +361,19 @@ void run_tick(lb_rd_server *s) {
     cudaMemcpyAsync(s->d_items, s->h_items, 3 * n * sizeof(lbrd::BatchItem), cudaMemcpyHostToDevice, s->stream);
     cudaError_t e = cudaSuccess;
     const int S = s->cfg.nspecies;
+    int rk = n > 0 ? act[0]->cfg.reaction.kind : -1;  // the reaction kind every request has, or -1
+    for (Request *r : act) rk = r->cfg.reaction.kind == rk ? rk : -1;
     for (int64_t l = 0; l < L && !e; ++l) {
         if (l < n_multi) {
             e = half ? lbrd::launch_batch_half_deep(K, s->Q, S, s->mode - 1, s->d_deep + (l & 1) * n, (int)n,
                                                     deep_units, l == L - 1, s->stream)
                      : lbrd::launch_batch_deep(K, s->Q, S, v16, s->d_deep + (l & 1) * n, (int)n, deep_units,
-                                               l == L - 1, s->stream);
+                                               l == L - 1, rk, s->stream);
         } else if (l == n_multi && rem > 0) {
             e = half ? lbrd::launch_batch_half_deep(rem, s->Q, S, s->mode - 1, s->d_deep + 2 * n, (int)n, rem_units,
                                                     l == L - 1, s->stream)
                      : lbrd::launch_batch_deep(rem, s->Q, S, v16, s->d_deep + 2 * n, (int)n, rem_units, l == L - 1,
-                                               s->stream);
+                                               rk, s->stream);
         } else {
             const lbrd::BatchItem *items = s->d_items + (l == L - 1 ? 2 : (l & 1)) * n;
             e = lbrd::launch_batch_step(any_inplace ? 4 : s->mode, s->Q, S, items, (int)n, total, s->stream);

@@ -17,8 +17,8 @@ template <int Q, int K, bool V16>
 struct UsePair {
     static constexpr bool value = Q == 9 ? K <= 5 : K <= 6;
 };
-template <int Q, int S, int K, bool V16>
-struct PairShape : PairKernel<Q, S, K, 4, (K < 5 ? 5 : 4), (K == 6 ? 1 : 2), true, true, !V16> {
+template <int Q, int S, int K, bool V16, int RK = -1>
+struct PairShape : PairKernel<Q, S, K, 4, (K < 5 ? 5 : 4), (K == 6 ? 1 : 2), true, true, !V16, RK> {
     static constexpr int NW = 4, NS = K < 5 ? 5 : 4, MINB = K == 6 ? 1 : 2;
 };
 
@@ -97,27 +97,38 @@ int64_t plan_batch(DeepItem *items, int n) {
     return units;
 }
 
-template <int Q, int S, int K, bool V16>
-cudaError_t launch_batch(const DeepItem *items, int n, int64_t total_units, bool emit, cudaStream_t st) {
+template <int Q, int S, int K, bool V16, int RK>
+cudaError_t launch_pair_list(const DeepItem *items, int n, int64_t total_units, bool emit, cudaStream_t st) {
+    using PS = PairShape<Q, S, K, V16, RK>;
     unsigned full = 0;
+    cudaError_t e = PS::get(&full);
+    if (e != cudaSuccess) return e;
+    const int64_t nwarps = (int64_t)full * PS::NW;
+    const unsigned grid = total_units < nwarps ? (unsigned)((total_units + PS::NW - 1) / PS::NW) : full;
+    step_pair_kernel<Q, S, K, PS::NW, PS::NS, PS::MINB, true, true, !V16, RK>
+        <<<grid, PS::NW * 32, PS::smem, st>>>(StepArgs{}, 0, 0, 0, items, n, total_units, emit ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// rk: the reaction kind of every grid of the list, or -1 (mixed); two-species
+// Gray-Scott lists run the two-column form with the reaction fixed at compile time.
+template <int Q, int S, int K, bool V16>
+cudaError_t launch_batch(const DeepItem *items, int n, int64_t total_units, bool emit, int rk, cudaStream_t st) {
     if constexpr (UsePair<Q, K, V16>::value) {
-        using PS = PairShape<Q, S, K, V16>;
-        cudaError_t e = PS::get(&full);
-        if (e != cudaSuccess) return e;
-        const int64_t nwarps = (int64_t)full * PS::NW;
-        const unsigned grid = total_units < nwarps ? (unsigned)((total_units + PS::NW - 1) / PS::NW) : full;
-        step_pair_kernel<Q, S, K, PS::NW, PS::NS, PS::MINB, true, true, !V16>
-            <<<grid, PS::NW * 32, PS::smem, st>>>(StepArgs{}, 0, 0, 0, items, n, total_units, emit ? 1 : 0);
+        if constexpr (S == 2)
+            if (rk == kGrayScott) return launch_pair_list<Q, S, K, V16, kGrayScott>(items, n, total_units, emit, st);
+        return launch_pair_list<Q, S, K, V16, -1>(items, n, total_units, emit, st);
     } else {
         using BS = BatchShape<Q, S, K, V16>;
+        unsigned full = 0;
         cudaError_t e = BS::get(&full);
         if (e != cudaSuccess) return e;
         const int64_t nwarps = (int64_t)full * BS::NW;
         const unsigned grid = total_units < nwarps ? (unsigned)((total_units + BS::NW - 1) / BS::NW) : full;
         step_deep_kernel<Q, S, K, BS::NW, 4, BS::MINB, V16, true, BS::PP>
             <<<grid, BS::NW * 32, BS::smem, st>>>(StepArgs{}, 0, 0, 0, items, n, total_units, emit ? 1 : 0);
+        return cudaGetLastError();
     }
-    return cudaGetLastError();
 }
 
 template <int K, bool V16>
@@ -130,19 +141,20 @@ int64_t plan_qs(int Q, int S, DeepItem *items, int n) {
 }
 
 template <int K, bool V16>
-cudaError_t launch_qs(int Q, int S, const DeepItem *items, int n, int64_t total_units, bool emit, cudaStream_t st) {
-    if (Q == 9 && S == 1) return launch_batch<9, 1, K, V16>(items, n, total_units, emit, st);
-    if (Q == 9 && S == 2) return launch_batch<9, 2, K, V16>(items, n, total_units, emit, st);
-    if (Q == 5 && S == 1) return launch_batch<5, 1, K, V16>(items, n, total_units, emit, st);
-    if (Q == 5 && S == 2) return launch_batch<5, 2, K, V16>(items, n, total_units, emit, st);
+cudaError_t launch_qs(int Q, int S, const DeepItem *items, int n, int64_t total_units, bool emit, int rk,
+                      cudaStream_t st) {
+    if (Q == 9 && S == 1) return launch_batch<9, 1, K, V16>(items, n, total_units, emit, rk, st);
+    if (Q == 9 && S == 2) return launch_batch<9, 2, K, V16>(items, n, total_units, emit, rk, st);
+    if (Q == 5 && S == 1) return launch_batch<5, 1, K, V16>(items, n, total_units, emit, rk, st);
+    if (Q == 5 && S == 2) return launch_batch<5, 2, K, V16>(items, n, total_units, emit, rk, st);
     return cudaErrorInvalidValue;
 }
 
 template <int K>
-cudaError_t launch_v(int Q, int S, bool v16, const DeepItem *items, int n, int64_t total_units, bool emit,
+cudaError_t launch_v(int Q, int S, bool v16, const DeepItem *items, int n, int64_t total_units, bool emit, int rk,
                      cudaStream_t st) {
-    return v16 ? launch_qs<K, true>(Q, S, items, n, total_units, emit, st)
-               : launch_qs<K, false>(Q, S, items, n, total_units, emit, st);
+    return v16 ? launch_qs<K, true>(Q, S, items, n, total_units, emit, rk, st)
+               : launch_qs<K, false>(Q, S, items, n, total_units, emit, rk, st);
 }
 
 }  // namespace
@@ -165,15 +177,15 @@ int64_t batch_deep_plan(int K, int Q, int S, bool v16, DeepItem *items, int n) {
 }
 
 cudaError_t launch_batch_deep(int K, int Q, int S, bool v16, const DeepItem *items, int n, int64_t total_units,
-                              bool emit, cudaStream_t st) {
+                              bool emit, int rk, cudaStream_t st) {
     switch (K) {
-        case 2: return launch_v<2>(Q, S, v16, items, n, total_units, emit, st);
-        case 3: return launch_v<3>(Q, S, v16, items, n, total_units, emit, st);
-        case 4: return launch_v<4>(Q, S, v16, items, n, total_units, emit, st);
-        case 5: return launch_v<5>(Q, S, v16, items, n, total_units, emit, st);
-        case 6: return launch_v<6>(Q, S, v16, items, n, total_units, emit, st);
-        case 7: return launch_v<7>(Q, S, v16, items, n, total_units, emit, st);
-        case 8: return launch_v<8>(Q, S, v16, items, n, total_units, emit, st);
+        case 2: return launch_v<2>(Q, S, v16, items, n, total_units, emit, rk, st);
+        case 3: return launch_v<3>(Q, S, v16, items, n, total_units, emit, rk, st);
+        case 4: return launch_v<4>(Q, S, v16, items, n, total_units, emit, rk, st);
+        case 5: return launch_v<5>(Q, S, v16, items, n, total_units, emit, rk, st);
+        case 6: return launch_v<6>(Q, S, v16, items, n, total_units, emit, rk, st);
+        case 7: return launch_v<7>(Q, S, v16, items, n, total_units, emit, rk, st);
+        case 8: return launch_v<8>(Q, S, v16, items, n, total_units, emit, rk, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -75,7 +75,8 @@ struct PairGeom {
 
 // ANY: grids of any nx (the seam chunks copied column by column, the last
 // column of an odd nx stored alone); otherwise nx must be a multiple of 4.
-template <int Q, int S, int K, int NW, int NS, int MINB, bool BATCH, bool PP, bool ANY = false>
+// RK >= 0: the grid's reaction kind, fixed at compile time (single grids).
+template <int Q, int S, int K, int NW, int NS, int MINB, bool BATCH, bool PP, bool ANY = false, int RK = -1>
 __global__ void __launch_bounds__(NW * 32, MINB)
     step_pair_kernel(StepArgs a, int64_t nstrips, int64_t nbands, int64_t band, const DeepItem *__restrict__ items,
                      int nitems, int64_t total_units, int emit) {
@@ -266,8 +267,7 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                 }
             {
                 const SegArgs cg = p_coll();
-                collide_site<Q, S>(cg, f0, rho0);
-                collide_site<Q, S>(cg, f1, rho1);
+                collide_pair<Q, S, RK>(cg, f0, f1, rho0, rho1);
             }
 #pragma unroll
             for (int m = 1; m < K; ++m) {  // level m + 1 from level m (carried index m - 1)
@@ -326,8 +326,7 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                         }
                 }
                 const SegArgs cg = p_coll();
-                collide_site<Q, S>(cg, f0, rho0);
-                collide_site<Q, S>(cg, f1, rho1);
+                collide_pair<Q, S, RK>(cg, f0, f1, rho0, rho1);
             }
             if (j >= 2 * K) {  // level K of row y0 + j - 2K: window columns HL .. 63 - HL
                 const int x = xb + 2 * lane;
@@ -368,11 +367,11 @@ __global__ void __launch_bounds__(NW * 32, MINB)
     if (a.mass_out) block_mass_reduce<S, NW * 32>(acc, a.partials, a.counter, a.mass_out);
 }
 
-template <int Q, int S, int K, int NW, int NS, int MINB, bool BATCH, bool PP = false, bool ANY = false>
+template <int Q, int S, int K, int NW, int NS, int MINB, bool BATCH, bool PP = false, bool ANY = false, int RK = -1>
 struct PairKernel {
     static constexpr size_t smem = (size_t)NW * NS * S * Q * 68 * sizeof(float);
     static cudaError_t get(unsigned *full) {
-        auto kern = step_pair_kernel<Q, S, K, NW, NS, MINB, BATCH, PP, ANY>;
+        auto kern = step_pair_kernel<Q, S, K, NW, NS, MINB, BATCH, PP, ANY, RK>;
         static std::atomic<bool> configured[64] = {};
         int dev = 0;
         cudaGetDevice(&dev);
@@ -386,11 +385,10 @@ struct PairKernel {
     }
 };
 
-template <int Q, int S, int K, int NW, int NS, int MINB, bool PP, bool ANY = false>
-cudaError_t launch_pair(const StepArgs &a, cudaStream_t st) {
+template <int Q, int S, int K, int NW, int NS, int MINB, bool PP, bool ANY, int RK>
+cudaError_t launch_pair_rk(const StepArgs &a, cudaStream_t st) {
     constexpr int WO = PairGeom<K>::WO;
-    if ((!ANY && a.nx % 4 != 0) || a.pitch % 4 != 0) return cudaErrorInvalidValue;
-    using PK = PairKernel<Q, S, K, NW, NS, MINB, false, PP, ANY>;
+    using PK = PairKernel<Q, S, K, NW, NS, MINB, false, PP, ANY, RK>;
     unsigned full = 0;
     cudaError_t e = PK::get(&full);
     if (e != cudaSuccess) return e;
@@ -400,9 +398,19 @@ cudaError_t launch_pair(const StepArgs &a, cudaStream_t st) {
     const int64_t band = (a.ny + nb - 1) / nb, nbands = (a.ny + band - 1) / band;
     const int64_t units = nstrips * nbands;
     const unsigned grid = units < nwarps ? (unsigned)((units + NW - 1) / NW) : full;
-    step_pair_kernel<Q, S, K, NW, NS, MINB, false, PP, ANY>
+    step_pair_kernel<Q, S, K, NW, NS, MINB, false, PP, ANY, RK>
         <<<grid, NW * 32, PK::smem, st>>>(a, nstrips, nbands, band, nullptr, 0, 0, a.rho_out != nullptr);
     return cudaGetLastError();
+}
+
+// Two-species Gray-Scott grids run the form with the reaction fixed at
+// compile time (no test of the kind in the row loop); the others test it.
+template <int Q, int S, int K, int NW, int NS, int MINB, bool PP, bool ANY = false>
+cudaError_t launch_pair(const StepArgs &a, cudaStream_t st) {
+    if ((!ANY && a.nx % 4 != 0) || a.pitch % 4 != 0) return cudaErrorInvalidValue;
+    if constexpr (S == 2)
+        if (a.rkind == kGrayScott) return launch_pair_rk<Q, S, K, NW, NS, MINB, PP, ANY, kGrayScott>(a, st);
+    return launch_pair_rk<Q, S, K, NW, NS, MINB, PP, ANY, -1>(a, st);
 }
 
 }  // namespace

@@ -37,6 +37,45 @@ __device__ __forceinline__ void collide_site(const Args &a, float (&f)[S][Q], fl
     }
 }
 
+// collide_site for two sites at once: the two density sums side by side and
+// one test of the reaction kind (RK >= 0: fixed at compile time), the same
+// operations per site in the same order, so the same bits.
+template <int Q, int S, int RK = -1, typename Args>
+__device__ __forceinline__ void collide_pair(const Args &a, float (&f0)[S][Q], float (&f1)[S][Q], float (&rho0)[S],
+                                             float (&rho1)[S]) {
+    using L = Lattice<Q>;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        float r0 = f0[s][0], r1 = f1[s][0];
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            r0 += f0[s][i];
+            r1 += f1[s][i];
+        }
+        rho0[s] = r0;
+        rho1[s] = r1;
+    }
+    float R0[S], R1[S];
+    reaction2_f32<S, RK>(a.rkind, (float)a.kappa, (float)a.F, (float)a.k, rho0, rho1, R0, R1);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const float om = (float)a.omega[s];
+        const float c1 = 1.f - om;
+        const float t0 = om * rho0[s] + R0[s], t1 = om * rho1[s] + R1[s];
+        float wt0[L::kClasses], wt1[L::kClasses];
+#pragma unroll
+        for (int c = 0; c < L::kClasses; ++c) {
+            wt0[c] = L::template wc<float>(c) * t0;
+            wt1[c] = L::template wc<float>(c) * t1;
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            f0[s][i] = fmaf(c1, f0[s][i], wt0[L::wclass(i)]);
+            f1[s][i] = fmaf(c1, f1[s][i], wt1[L::wclass(i)]);
+        }
+    }
+}
+
 // The fields of one grid a multi-step segment needs, in registers (FP32 copies
 // of the relaxation rates and reaction constants: the values the one-step
 // kernels compute with).
