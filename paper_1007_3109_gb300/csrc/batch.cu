@@ -237,12 +237,12 @@ cudaError_t plan_deep(lb_rd_batch *b, int K) {
 cudaError_t launch_deep(lb_rd_batch *b, int K, int parity, bool emit) {
     cudaError_t e = plan_deep(b, K);
     if (e) return e;
+    const int rk = lbrd::list_reaction_kind(b->deep_base.data(), (int)b->deep_base.size());
     if (half_batch(b))
         return lbrd::launch_batch_half_deep(K, b->Q, b->S, b->mode - 1, b->d_deep[K][parity], (int)b->cfgs.size(),
-                                            b->deep_units[K], emit, b->stream);
+                                            b->deep_units[K], emit, rk, b->stream);
     return lbrd::launch_batch_deep(K, b->Q, b->S, b->deep_v16, b->d_deep[K][parity], (int)b->cfgs.size(),
-                                   b->deep_units[K], emit,
-                                   lbrd::list_reaction_kind(b->deep_base.data(), (int)b->deep_base.size()), b->stream);
+                                   b->deep_units[K], emit, rk, b->stream);
 }
 
 // One launch of steps_per_launch (>= 2) steps from buffer parity `parity`.

@@ -45,12 +45,12 @@ __global__ void export_half_kernel(const char *state, int64_t nx, int64_t ny, in
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         gs[i] = (float)g[(int64_t)(i - 1) * plane + y * pitch + x];
-        sum += gs[i];
+        sum = rn_add(sum, gs[i]);
     }
     gs[0] = -sum;
 #pragma unroll
     for (int i = 0; i < Q; ++i)
-        out[(((int64_t)s * Q + i) * ny + y) * nx + x] = (double)(weight<Q, float>(i) * rs + gs[i]);
+        out[(((int64_t)s * Q + i) * ny + y) * nx + x] = (double)rn_fma(weight<Q, float>(i), rs, gs[i]);
 }
 
 template <typename T>

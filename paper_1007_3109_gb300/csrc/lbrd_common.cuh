@@ -84,20 +84,32 @@ struct Network {
     signed char change[kMaxReactions][kMaxSpecies];
 };
 
-// FP32 and faster paths: plain expression, contraction allowed.
-template <int S>
+// FP32 operations rounded as written.  An FP32 multiply or add without an
+// explicit rounding mode may be fused into an FMA by the compiler, and
+// whether it is depends on the surrounding code; with these forms every
+// kernel performs the same operations and so gives the same bits.
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float rn_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// FP32 and faster paths: (u v) v;  fma(F, 1 - u, -uvv);  fma(-(F + k), v,
+// uvv);  -kappa rho_A;  kappa rho_A.  RK >= 0 fixes the kind at compile time
+// (the caller has checked that kind == RK).
+template <int S, int RK = -1>
 __device__ __forceinline__ void reaction_f32(int kind, float kappa, float F, float k, const float (&rho)[S],
                                              float (&R)[S]) {
+    const int kd = RK >= 0 ? RK : kind;
 #pragma unroll
     for (int s = 0; s < S; ++s) R[s] = 0.f;
-    if (kind == kLinear) {
-        R[0] = -kappa * rho[0];
-        if (S == 2) R[S - 1] = kappa * rho[0];
-    } else if (kind == kGrayScott && S == 2) {
+    if (kd == kLinear) {
+        R[0] = rn_mul(-kappa, rho[0]);
+        if (S == 2) R[S - 1] = rn_mul(kappa, rho[0]);
+    } else if (kd == kGrayScott && S == 2) {
         const float u = rho[0], v = rho[S - 1];
-        const float uvv = u * v * v;
-        R[0] = F * (1.f - u) - uvv;
-        R[S - 1] = uvv - (F + k) * v;
+        const float uvv = rn_mul(rn_mul(u, v), v);
+        R[0] = rn_fma(F, rn_sub(1.f, u), -uvv);
+        R[S - 1] = rn_fma(-rn_add(F, k), v, uvv);
     }
 }
 
@@ -111,19 +123,20 @@ __device__ __forceinline__ void reaction2_f32(int kind, float kappa, float F, fl
 #pragma unroll
     for (int s = 0; s < S; ++s) R0[s] = R1[s] = 0.f;
     if (kd == kLinear) {
-        R0[0] = -kappa * r0[0];
-        R1[0] = -kappa * r1[0];
+        R0[0] = rn_mul(-kappa, r0[0]);
+        R1[0] = rn_mul(-kappa, r1[0]);
         if (S == 2) {
-            R0[S - 1] = kappa * r0[0];
-            R1[S - 1] = kappa * r1[0];
+            R0[S - 1] = rn_mul(kappa, r0[0]);
+            R1[S - 1] = rn_mul(kappa, r1[0]);
         }
     } else if (kd == kGrayScott && S == 2) {
         const float u0 = r0[0], v0 = r0[S - 1], u1 = r1[0], v1 = r1[S - 1];
-        const float uvv0 = u0 * v0 * v0, uvv1 = u1 * v1 * v1;
-        R0[0] = F * (1.f - u0) - uvv0;
-        R1[0] = F * (1.f - u1) - uvv1;
-        R0[S - 1] = uvv0 - (F + k) * v0;
-        R1[S - 1] = uvv1 - (F + k) * v1;
+        const float uvv0 = rn_mul(rn_mul(u0, v0), v0), uvv1 = rn_mul(rn_mul(u1, v1), v1);
+        const float fk = -rn_add(F, k);
+        R0[0] = rn_fma(F, rn_sub(1.f, u0), -uvv0);
+        R1[0] = rn_fma(F, rn_sub(1.f, u1), -uvv1);
+        R0[S - 1] = rn_fma(fk, v0, uvv0);
+        R1[S - 1] = rn_fma(fk, v1, uvv1);
     }
 }
 

@@ -178,7 +178,7 @@ struct DeepItem {
 // any nx a multiple of 4), the depth-K kernel of step_half_deep_kernel.cuh.
 int64_t batch_half_deep_plan(int K, int Q, int S, int half_kind, DeepItem *items, int n);
 cudaError_t launch_batch_half_deep(int K, int Q, int S, int half_kind, const DeepItem *items, int n,
-                                   int64_t total_units, bool emit, cudaStream_t st);
+                                   int64_t total_units, bool emit, int rk, cudaStream_t st);
 bool batch_deep_depth_ok(int K);
 // Default steps per launch of a list of grids: 5 (D2Q9) / 6 (D2Q5), the
 // fastest two-column forms over a list (the grid's parameters read from a

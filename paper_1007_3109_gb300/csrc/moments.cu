@@ -44,7 +44,7 @@ __global__ void pull_rho_f32(const float *src, int64_t nx, int64_t ny, int64_t p
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const float f = src[(int64_t)(s * Q + i) * plane + wrap(y - L::ey(i), ny) * pitch + wrap(x - L::ex(i), nx)];
-            r = i == 0 ? f : r + f;
+            r = i == 0 ? f : rn_add(r, f);
         }
         rho[(int64_t)s * plane + y * pitch + x] = r;
     }
@@ -76,13 +76,13 @@ __global__ void pull_rho_half(const char *src, int64_t nx, int64_t ny, int64_t p
         for (int i = 1; i < Q; ++i) {
             const int64_t ys = wrap(y - L::ey(i), ny), xs = wrap(x - L::ex(i), nx);
             const float gp = h2f<H>(g[(int64_t)(i - 1) * plane + ys * pitch + xs]);
-            gsum += h2f<H>(g[(int64_t)(i - 1) * plane + y * pitch + x]);
-            f[i] = fmaf(weight<Q, float>(i), rs[ys * pitch + xs], gp);
+            gsum = rn_add(gsum, h2f<H>(g[(int64_t)(i - 1) * plane + y * pitch + x]));
+            f[i] = rn_fma(weight<Q, float>(i), rs[ys * pitch + xs], gp);
         }
-        f[0] = fmaf(weight<Q, float>(0), rs[y * pitch + x], -gsum);
+        f[0] = rn_fma(weight<Q, float>(0), rs[y * pitch + x], -gsum);
         float r = f[0];
 #pragma unroll
-        for (int i = 1; i < Q; ++i) r += f[i];
+        for (int i = 1; i < Q; ++i) r = rn_add(r, f[i]);
         rho[(int64_t)s * plane + y * pitch + x] = r;
     }
 }

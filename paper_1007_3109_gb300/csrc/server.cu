@@ -366,12 +366,12 @@ void run_tick(lb_rd_server *s) {
     for (int64_t l = 0; l < L && !e; ++l) {
         if (l < n_multi) {
             e = half ? lbrd::launch_batch_half_deep(K, s->Q, S, s->mode - 1, s->d_deep + (l & 1) * n, (int)n,
-                                                    deep_units, l == L - 1, s->stream)
+                                                    deep_units, l == L - 1, rk, s->stream)
                      : lbrd::launch_batch_deep(K, s->Q, S, v16, s->d_deep + (l & 1) * n, (int)n, deep_units,
                                                l == L - 1, rk, s->stream);
         } else if (l == n_multi && rem > 0) {
             e = half ? lbrd::launch_batch_half_deep(rem, s->Q, S, s->mode - 1, s->d_deep + 2 * n, (int)n, rem_units,
-                                                    l == L - 1, s->stream)
+                                                    l == L - 1, rk, s->stream)
                      : lbrd::launch_batch_deep(rem, s->Q, S, v16, s->d_deep + 2 * n, (int)n, rem_units, l == L - 1,
                                                rk, s->stream);
         } else {

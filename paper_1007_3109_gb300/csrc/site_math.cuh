@@ -64,11 +64,11 @@ __device__ __forceinline__ void network_source(const NetSmem &n, const float (&r
         float p = n.ratef[r];
 #pragma unroll
         for (int j = 0; j < S; ++j)
-            for (int e = 0; e < n.order[r][j]; ++e) p *= rho[j];
+            for (int e = 0; e < n.order[r][j]; ++e) p = rn_mul(p, rho[j]);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             const int c = n.change[r][s];
-            if (c != 0) R[s] += (float)c * p;
+            if (c != 0) R[s] = rn_fma((float)c, p, R[s]);
         }
     }
 }
@@ -91,7 +91,7 @@ __device__ __forceinline__ void network_source_vec(const NetSmem &n, const float
             const int o = n.order[r][j];
             for (int e = 0; e < o; ++e)
 #pragma unroll
-                for (int v = 0; v < V; ++v) p[v] *= rho[j][v];
+                for (int v = 0; v < V; ++v) p[v] = rn_mul(p[v], rho[j][v]);
         }
 #pragma unroll
         for (int s = 0; s < S; ++s) {
@@ -99,7 +99,7 @@ __device__ __forceinline__ void network_source_vec(const NetSmem &n, const float
             if (c != 0) {
                 const float cf = (float)c;
 #pragma unroll
-                for (int v = 0; v < V; ++v) R[s][v] += cf * p[v];
+                for (int v = 0; v < V; ++v) R[s][v] = rn_fma(cf, p[v], R[s][v]);
             }
         }
     }
@@ -111,12 +111,12 @@ __device__ __forceinline__ double relax(double f, double w, double rho, double o
     return __dadd_rn(__dadd_rn(f, __dmul_rn(__dsub_rn(__dmul_rn(w, rho), f), om)), __dmul_rn(w, R));
 }
 __device__ __forceinline__ float relax(float f, float w, float rho, float om, float R) {
-    return fmaf(1.f - om, f, w * (om * rho + R));
+    return rn_fma(rn_sub(1.f, om), f, rn_mul(w, rn_fma(om, rho, R)));
 }
 
 // The density sum's additions (index order; FP64 never contracted).
 __device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ float radd(float a, float b) { return a + b; }
+__device__ __forceinline__ float radd(float a, float b) { return rn_add(a, b); }
 
 }  // namespace sm
 }  // namespace lbrd

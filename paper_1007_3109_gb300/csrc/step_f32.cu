@@ -17,10 +17,10 @@ __global__ void __launch_bounds__(256) init_f32_kernel(InitArgs a) {
     for (int s = 0; s < S; ++s) {
         const float r0 = (float)a.rho0[((int64_t)s * a.ny + y) * a.nx + x];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) f[s][i] = weight<Q, float>(i) * r0;
+        for (int i = 0; i < Q; ++i) f[s][i] = rn_mul(weight<Q, float>(i), r0);
         float r = f[s][0];
 #pragma unroll
-        for (int i = 1; i < Q; ++i) r += f[s][i];
+        for (int i = 1; i < Q; ++i) r = rn_add(r, f[s][i]);
         rho[s] = r;
     }
     reaction_f32<S>(a.rkind, (float)a.kappa, (float)a.F, (float)a.k, rho, R);
@@ -28,10 +28,11 @@ __global__ void __launch_bounds__(256) init_f32_kernel(InitArgs a) {
 #pragma unroll
     for (int s = 0; s < S; ++s) {
         const float om = (float)a.omega[s];
-        const float t = om * rho[s] + R[s];
+        const float t = rn_fma(om, rho[s], R[s]);
 #pragma unroll
         for (int i = 0; i < Q; ++i)
-            dst[(int64_t)(s * Q + i) * a.plane + y * a.pitch + x] = fmaf(1.f - om, f[s][i], weight<Q, float>(i) * t);
+            dst[(int64_t)(s * Q + i) * a.plane + y * a.pitch + x] =
+                rn_fma(rn_sub(1.f, om), f[s][i], rn_mul(weight<Q, float>(i), t));
         if (a.rho_out) static_cast<float *>(a.rho_out)[(int64_t)s * a.plane + y * a.pitch + x] = rho[s];
     }
 }

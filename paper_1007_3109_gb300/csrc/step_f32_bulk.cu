@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(NT, 1) step_bulk_kernel(StepArgs a, int64_t ns
             for (int jj = 0; jj < 4; ++jj) {
                 float r = f[s][0][jj];
 #pragma unroll
-                for (int i = 1; i < Q; ++i) r += f[s][i][jj];
+                for (int i = 1; i < Q; ++i) r = rn_add(r, f[s][i][jj]);
                 rho[s][jj] = r;
             }
         }
@@ -224,22 +224,22 @@ __global__ void __launch_bounds__(NT, 1) step_bulk_kernel(StepArgs a, int64_t ns
 #pragma unroll
             for (int s = 0; s < S; ++s) {
                 const float om = (float)a.omega[s];
-                const float c1 = 1.f - om;
+                const float c1 = rn_sub(1.f, om);
                 float wt[L::kClasses][4];
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj) {
-                    const float t = om * rho[s][jj] + R[s][jj];
+                    const float t = rn_fma(om, rho[s][jj], R[s][jj]);
 #pragma unroll
-                    for (int c = 0; c < L::kClasses; ++c) wt[c][jj] = L::template wc<float>(c) * t;
+                    for (int c = 0; c < L::kClasses; ++c) wt[c][jj] = rn_mul(L::template wc<float>(c), t);
                 }
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
                     const int c = L::wclass(i);
                     float4 o;
-                    o.x = fmaf(c1, f[s][i][0], wt[c][0]);
-                    o.y = fmaf(c1, f[s][i][1], wt[c][1]);
-                    o.z = fmaf(c1, f[s][i][2], wt[c][2]);
-                    o.w = fmaf(c1, f[s][i][3], wt[c][3]);
+                    o.x = rn_fma(c1, f[s][i][0], wt[c][0]);
+                    o.y = rn_fma(c1, f[s][i][1], wt[c][1]);
+                    o.z = rn_fma(c1, f[s][i][2], wt[c][2]);
+                    o.w = rn_fma(c1, f[s][i][3], wt[c][3]);
                     *reinterpret_cast<float4 *>(dst + (int64_t)(s * Q + i) * a.plane + y * a.pitch + x0) = o;
                 }
                 if (a.rho_out)

@@ -112,7 +112,7 @@ __device__ __forceinline__ void tile_f32(const StepArgs &a, int64_t x0, int64_t 
         for (int j = 0; j < kVec; ++j) {
             float r = f[s][0][j];
 #pragma unroll
-            for (int i = 1; i < Q; ++i) r += f[s][i][j];
+            for (int i = 1; i < Q; ++i) r = rn_add(r, f[s][i][j]);
             rho[s][j] = r;
         }
     }
@@ -133,22 +133,22 @@ __device__ __forceinline__ void tile_f32(const StepArgs &a, int64_t x0, int64_t 
 #pragma unroll
     for (int s = 0; s < S; ++s) {
         const float om = (float)a.omega[s];
-        const float c1 = 1.f - om;
+        const float c1 = rn_sub(1.f, om);
         float wt[L::kClasses][kVec];
 #pragma unroll
         for (int j = 0; j < kVec; ++j) {
-            const float t = om * rho[s][j] + R[s][j];
+            const float t = rn_fma(om, rho[s][j], R[s][j]);
 #pragma unroll
-            for (int c = 0; c < L::kClasses; ++c) wt[c][j] = L::template wc<float>(c) * t;
+            for (int c = 0; c < L::kClasses; ++c) wt[c][j] = rn_mul(L::template wc<float>(c), t);
         }
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const int c = L::wclass(i);
             float4 o;
-            o.x = fmaf(c1, f[s][i][0], wt[c][0]);
-            o.y = fmaf(c1, f[s][i][1], wt[c][1]);
-            o.z = fmaf(c1, f[s][i][2], wt[c][2]);
-            o.w = fmaf(c1, f[s][i][3], wt[c][3]);
+            o.x = rn_fma(c1, f[s][i][0], wt[c][0]);
+            o.y = rn_fma(c1, f[s][i][1], wt[c][1]);
+            o.z = rn_fma(c1, f[s][i][2], wt[c][2]);
+            o.w = rn_fma(c1, f[s][i][3], wt[c][3]);
             stv4<CACHE>(dst + (int64_t)(s * Q + i) * plane + y * pitch + x0, o);
         }
         if (a.rho_out)

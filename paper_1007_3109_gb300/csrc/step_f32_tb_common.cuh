@@ -19,7 +19,7 @@ __device__ __forceinline__ void collide_site(const Args &a, float (&f)[S][Q], fl
     for (int s = 0; s < S; ++s) {
         float r = f[s][0];
 #pragma unroll
-        for (int i = 1; i < Q; ++i) r += f[s][i];
+        for (int i = 1; i < Q; ++i) r = rn_add(r, f[s][i]);
         rho[s] = r;
     }
     float R[S];
@@ -27,13 +27,13 @@ __device__ __forceinline__ void collide_site(const Args &a, float (&f)[S][Q], fl
 #pragma unroll
     for (int s = 0; s < S; ++s) {
         const float om = (float)a.omega[s];
-        const float c1 = 1.f - om;
-        const float t = om * rho[s] + R[s];
+        const float c1 = rn_sub(1.f, om);
+        const float t = rn_fma(om, rho[s], R[s]);
         float wt[L::kClasses];
 #pragma unroll
-        for (int c = 0; c < L::kClasses; ++c) wt[c] = L::template wc<float>(c) * t;
+        for (int c = 0; c < L::kClasses; ++c) wt[c] = rn_mul(L::template wc<float>(c), t);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) f[s][i] = fmaf(c1, f[s][i], wt[L::wclass(i)]);
+        for (int i = 0; i < Q; ++i) f[s][i] = rn_fma(c1, f[s][i], wt[L::wclass(i)]);
     }
 }
 
@@ -49,8 +49,8 @@ __device__ __forceinline__ void collide_pair(const Args &a, float (&f0)[S][Q], f
         float r0 = f0[s][0], r1 = f1[s][0];
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
-            r0 += f0[s][i];
-            r1 += f1[s][i];
+            r0 = rn_add(r0, f0[s][i]);
+            r1 = rn_add(r1, f1[s][i]);
         }
         rho0[s] = r0;
         rho1[s] = r1;
@@ -60,18 +60,18 @@ __device__ __forceinline__ void collide_pair(const Args &a, float (&f0)[S][Q], f
 #pragma unroll
     for (int s = 0; s < S; ++s) {
         const float om = (float)a.omega[s];
-        const float c1 = 1.f - om;
-        const float t0 = om * rho0[s] + R0[s], t1 = om * rho1[s] + R1[s];
+        const float c1 = rn_sub(1.f, om);
+        const float t0 = rn_fma(om, rho0[s], R0[s]), t1 = rn_fma(om, rho1[s], R1[s]);
         float wt0[L::kClasses], wt1[L::kClasses];
 #pragma unroll
         for (int c = 0; c < L::kClasses; ++c) {
-            wt0[c] = L::template wc<float>(c) * t0;
-            wt1[c] = L::template wc<float>(c) * t1;
+            wt0[c] = rn_mul(L::template wc<float>(c), t0);
+            wt1[c] = rn_mul(L::template wc<float>(c), t1);
         }
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            f0[s][i] = fmaf(c1, f0[s][i], wt0[L::wclass(i)]);
-            f1[s][i] = fmaf(c1, f1[s][i], wt1[L::wclass(i)]);
+            f0[s][i] = rn_fma(c1, f0[s][i], wt0[L::wclass(i)]);
+            f1[s][i] = rn_fma(c1, f1[s][i], wt1[L::wclass(i)]);
         }
     }
 }

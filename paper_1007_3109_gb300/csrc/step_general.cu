@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(kBX) init_general_kernel(InitArgs a) {
         const T r0 = (T)a.rho0[((int64_t)s * a.ny + y) * a.nx + x];
 #pragma unroll
         for (int i = 0; i < Q; ++i) f[s][i] = sizeof(T) == 8 ? (T)__dmul_rn(weight<Q, double>(i), (double)r0)
-                                                             : weight<Q, T>(i) * r0;
+                                                             : (T)rn_mul(weight<Q, float>(i), (float)r0);
         T r = f[s][0];
 #pragma unroll
         for (int i = 1; i < Q; ++i) r = radd(r, f[s][i]);

@@ -25,23 +25,23 @@ __global__ void __launch_bounds__(256) init_half_kernel(InitArgs a) {
     for (int s = 0; s < S; ++s) {
         const float r0 = (float)a.rho0[((int64_t)s * a.ny + y) * a.nx + x];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) f[s][i] = weight<Q, float>(i) * r0;
+        for (int i = 0; i < Q; ++i) f[s][i] = rn_mul(weight<Q, float>(i), r0);
         float r = f[s][0];
 #pragma unroll
-        for (int i = 1; i < Q; ++i) r += f[s][i];
+        for (int i = 1; i < Q; ++i) r = rn_add(r, f[s][i]);
         rho[s] = r;
     }
     reaction_f32<S>(a.rkind, (float)a.kappa, (float)a.F, (float)a.k, rho, R);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
         char *base = static_cast<char *>(a.dst) + (size_t)s * species_bytes;
-        reinterpret_cast<float *>(base)[y * a.pitch + x] = rho[s] + R[s];
+        reinterpret_cast<float *>(base)[y * a.pitch + x] = rn_add(rho[s], R[s]);
         unsigned short *g = reinterpret_cast<unsigned short *>(base + (size_t)plane * 4);
-        const float c1 = 1.f - (float)a.omega[s];
+        const float c1 = rn_sub(1.f, (float)a.omega[s]);
 #pragma unroll
         for (int i = 1; i < Q; ++i)
             g[(int64_t)(i - 1) * plane + y * a.pitch + x] =
-                (unsigned short)f2h<H>(c1 * fmaf(-weight<Q, float>(i), rho[s], f[s][i]));
+                (unsigned short)f2h<H>(rn_mul(c1, rn_fma(-weight<Q, float>(i), rho[s], f[s][i])));
         if (a.rho_out) static_cast<float *>(a.rho_out)[(int64_t)s * plane + y * a.pitch + x] = rho[s];
     }
 }

@@ -31,18 +31,27 @@ int64_t plan_half_batch(DeepItem *items, int n) {
     return units;
 }
 
-template <int Q, int S, int H, int K>
-cudaError_t launch_half_batch(const DeepItem *items, int n, int64_t total_units, bool emit, cudaStream_t st) {
+template <int Q, int S, int H, int K, int RK>
+cudaError_t launch_half_batch_rk(const DeepItem *items, int n, int64_t total_units, bool emit, cudaStream_t st) {
     using HS = HalfShape<K>;
-    using HK = HalfDeepKernel<Q, S, H, K, HS::NW, HS::NS, HS::MINB, true>;
+    using HK = HalfDeepKernel<Q, S, H, K, HS::NW, HS::NS, HS::MINB, true, RK>;
     unsigned full = 0;
     cudaError_t e = HK::get(&full);
     if (e != cudaSuccess) return e;
     const int64_t nwarps = (int64_t)full * HS::NW;
     const unsigned grid = total_units < nwarps ? (unsigned)((total_units + HS::NW - 1) / HS::NW) : full;
-    step_half_deep_kernel<Q, S, H, K, HS::NW, HS::NS, HS::MINB, true>
+    step_half_deep_kernel<Q, S, H, K, HS::NW, HS::NS, HS::MINB, true, RK>
         <<<grid, HS::NW * 32, HK::smem, st>>>(StepArgs{}, 0, 0, 0, items, n, total_units, emit ? 1 : 0);
     return cudaGetLastError();
+}
+
+// rk: the reaction kind of every grid of the list, or -1 (mixed).
+template <int Q, int S, int H, int K>
+cudaError_t launch_half_batch(const DeepItem *items, int n, int64_t total_units, bool emit, int rk,
+                              cudaStream_t st) {
+    if constexpr (S == 2)
+        if (rk == kGrayScott) return launch_half_batch_rk<Q, S, H, K, kGrayScott>(items, n, total_units, emit, st);
+    return launch_half_batch_rk<Q, S, H, K, -1>(items, n, total_units, emit, st);
 }
 
 template <int H, int K>
@@ -55,11 +64,12 @@ int64_t plan_qs(int Q, int S, DeepItem *items, int n) {
 }
 
 template <int H, int K>
-cudaError_t launch_qs(int Q, int S, const DeepItem *items, int n, int64_t total_units, bool emit, cudaStream_t st) {
-    if (Q == 9 && S == 1) return launch_half_batch<9, 1, H, K>(items, n, total_units, emit, st);
-    if (Q == 9 && S == 2) return launch_half_batch<9, 2, H, K>(items, n, total_units, emit, st);
-    if (Q == 5 && S == 1) return launch_half_batch<5, 1, H, K>(items, n, total_units, emit, st);
-    if (Q == 5 && S == 2) return launch_half_batch<5, 2, H, K>(items, n, total_units, emit, st);
+cudaError_t launch_qs(int Q, int S, const DeepItem *items, int n, int64_t total_units, bool emit, int rk,
+                      cudaStream_t st) {
+    if (Q == 9 && S == 1) return launch_half_batch<9, 1, H, K>(items, n, total_units, emit, rk, st);
+    if (Q == 9 && S == 2) return launch_half_batch<9, 2, H, K>(items, n, total_units, emit, rk, st);
+    if (Q == 5 && S == 1) return launch_half_batch<5, 1, H, K>(items, n, total_units, emit, rk, st);
+    if (Q == 5 && S == 2) return launch_half_batch<5, 2, H, K>(items, n, total_units, emit, rk, st);
     return cudaErrorInvalidValue;
 }
 
@@ -75,13 +85,13 @@ int64_t plan_k(int K, int Q, int S, DeepItem *items, int n) {
 }
 
 template <int H>
-cudaError_t launch_k(int K, int Q, int S, const DeepItem *items, int n, int64_t total_units, bool emit,
+cudaError_t launch_k(int K, int Q, int S, const DeepItem *items, int n, int64_t total_units, bool emit, int rk,
                      cudaStream_t st) {
     switch (K) {
-        case 2: return launch_qs<H, 2>(Q, S, items, n, total_units, emit, st);
-        case 3: return launch_qs<H, 3>(Q, S, items, n, total_units, emit, st);
-        case 4: return launch_qs<H, 4>(Q, S, items, n, total_units, emit, st);
-        case 5: return launch_qs<H, 5>(Q, S, items, n, total_units, emit, st);
+        case 2: return launch_qs<H, 2>(Q, S, items, n, total_units, emit, rk, st);
+        case 3: return launch_qs<H, 3>(Q, S, items, n, total_units, emit, rk, st);
+        case 4: return launch_qs<H, 4>(Q, S, items, n, total_units, emit, rk, st);
+        case 5: return launch_qs<H, 5>(Q, S, items, n, total_units, emit, rk, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -93,9 +103,9 @@ int64_t batch_half_deep_plan(int K, int Q, int S, int half_kind, DeepItem *items
 }
 
 cudaError_t launch_batch_half_deep(int K, int Q, int S, int half_kind, const DeepItem *items, int n,
-                                   int64_t total_units, bool emit, cudaStream_t st) {
-    return half_kind ? launch_k<1>(K, Q, S, items, n, total_units, emit, st)
-                     : launch_k<0>(K, Q, S, items, n, total_units, emit, st);
+                                   int64_t total_units, bool emit, int rk, cudaStream_t st) {
+    return half_kind ? launch_k<1>(K, Q, S, items, n, total_units, emit, rk, st)
+                     : launch_k<0>(K, Q, S, items, n, total_units, emit, rk, st);
 }
 
 }  // namespace lbrd

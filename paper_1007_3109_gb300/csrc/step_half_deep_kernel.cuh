@@ -44,35 +44,36 @@ __device__ __forceinline__ void cp_async8(unsigned dst, const void *src) {
 // Collision of one site in the stored form: rho_s = sum_i f_i (index order),
 // R, rho*_s = rho_s + R_s and the deviations g_i rounded to 16 bits (as the
 // floats they convert back to), with their sum over i >= 1 in index order.
-// The arithmetic of half::tile_half.
-template <int Q, int S, int H>
+// The arithmetic of half::tile_half; RK >= 0: the reaction kind fixed at
+// compile time.
+template <int Q, int S, int H, int RK = -1>
 __device__ __forceinline__ void collide_half(const tb::SegArgs &g, const float (&f)[S][Q], float (&rho)[S],
                                              float (&rstar)[S], float (&gh)[S][Q], float (&gsum)[S]) {
 #pragma unroll
     for (int s = 0; s < S; ++s) {
         float r = f[s][0];
 #pragma unroll
-        for (int i = 1; i < Q; ++i) r += f[s][i];
+        for (int i = 1; i < Q; ++i) r = rn_add(r, f[s][i]);
         rho[s] = r;
     }
     float R[S];
-    reaction_f32<S>(g.rkind, g.kappa, g.F, g.k, rho, R);
+    reaction_f32<S, RK>(g.rkind, g.kappa, g.F, g.k, rho, R);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        rstar[s] = rho[s] + R[s];
-        const float c1 = 1.f - g.omega[s];
+        rstar[s] = rn_add(rho[s], R[s]);
+        const float c1 = rn_sub(1.f, g.omega[s]);
         float gs = 0.f;
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
-            const float hv = c1 * fmaf(-weight<Q, float>(i), rho[s], f[s][i]);
+            const float hv = rn_mul(c1, rn_fma(-weight<Q, float>(i), rho[s], f[s][i]));
             gh[s][i] = half::h2f<H>(half::f2h<H>(hv));
-            gs += gh[s][i];
+            gs = rn_add(gs, gh[s][i]);
         }
         gsum[s] = gs;
     }
 }
 
-template <int Q, int S, int H, int K, int NW, int NS, int MINB, bool BATCH>
+template <int Q, int S, int H, int K, int NW, int NS, int MINB, bool BATCH, int RK = -1>
 __global__ void __launch_bounds__(NW * 32, MINB)
     step_half_deep_kernel(StepArgs a, int64_t nstrips, int64_t nbands, int64_t band,
                           const DeepItem *__restrict__ items, int nitems, int64_t total_units, int emit) {
@@ -187,12 +188,12 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                     const int c = o + 1 + lane - L::ex(i);
                     const float rp = reinterpret_cast<const float *>(rs)[c];
                     const float gp = half::h2f<H>(reinterpret_cast<const unsigned short *>(rs + CW * 4 + (i - 1) * CW * 2)[c]);
-                    f[s][i] = fmaf(weight<Q, float>(i), rp, gp);
-                    gs += half::h2f<H>(reinterpret_cast<const unsigned short *>(own + CW * 4 + (i - 1) * CW * 2)[o + 1 + lane]);
+                    f[s][i] = rn_fma(weight<Q, float>(i), rp, gp);
+                    gs = rn_add(gs, half::h2f<H>(reinterpret_cast<const unsigned short *>(own + CW * 4 + (i - 1) * CW * 2)[o + 1 + lane]));
                 }
-                f[s][0] = fmaf(weight<Q, float>(0), reinterpret_cast<const float *>(own)[o + 1 + lane], -gs);
+                f[s][0] = rn_fma(weight<Q, float>(0), reinterpret_cast<const float *>(own)[o + 1 + lane], -gs);
             }
-            collide_half<Q, S, H>(g, f, rho, rstar, gh, gsum);
+            collide_half<Q, S, H, RK>(g, f, rho, rstar, gh, gsum);
 #pragma unroll
             for (int m = 1; m < K; ++m) {  // level m + 1 from level m (carried index m - 1)
                 float nf[S][Q];
@@ -213,9 +214,9 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                         const float gp = L::ex(i) > 0   ? __shfl_up_sync(kFullMask, v, 1)
                                          : L::ex(i) < 0 ? __shfl_down_sync(kFullMask, v, 1)
                                                         : v;
-                        nf[s][i] = fmaf(weight<Q, float>(i), rsh[1 - L::ey(i)][1 - L::ex(i)], gp);
+                        nf[s][i] = rn_fma(weight<Q, float>(i), rsh[1 - L::ey(i)][1 - L::ex(i)], gp);
                     }
-                    nf[s][0] = fmaf(weight<Q, float>(0), P1r[m - 1][s], -E0s[m - 1][s]);
+                    nf[s][0] = rn_fma(weight<Q, float>(0), P1r[m - 1][s], -E0s[m - 1][s]);
                 }
                 // level m's rows move down: this row becomes the previous one
 #pragma unroll
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                         }
                     }
                 }
-                collide_half<Q, S, H>(g, nf, rho, rstar, gh, gsum);
+                collide_half<Q, S, H, RK>(g, nf, rho, rstar, gh, gsum);
             }
             if (j >= 2 * K) {  // level K of row y0 + j - 2K
                 const int x = xb + lane;
@@ -262,11 +263,11 @@ __global__ void __launch_bounds__(NW * 32, MINB)
     if (a.mass_out) block_mass_reduce<S, NW * 32>(acc, a.partials, a.counter, a.mass_out);
 }
 
-template <int Q, int S, int H, int K, int NW, int NS, int MINB, bool BATCH>
+template <int Q, int S, int H, int K, int NW, int NS, int MINB, bool BATCH, int RK = -1>
 struct HalfDeepKernel {
     static constexpr size_t smem = (size_t)NW * NS * S * (40 * 4 + (Q - 1) * 40 * 2);
     static cudaError_t get(unsigned *full) {
-        auto kern = step_half_deep_kernel<Q, S, H, K, NW, NS, MINB, BATCH>;
+        auto kern = step_half_deep_kernel<Q, S, H, K, NW, NS, MINB, BATCH, RK>;
         static std::atomic<bool> configured[64] = {};
         int dev = 0;
         cudaGetDevice(&dev);
@@ -280,11 +281,10 @@ struct HalfDeepKernel {
     }
 };
 
-template <int Q, int S, int H, int K, int NW, int NS, int MINB>
-cudaError_t launch_half_deep(const StepArgs &a, cudaStream_t st) {
+template <int Q, int S, int H, int K, int NW, int NS, int MINB, int RK>
+cudaError_t launch_half_deep_rk(const StepArgs &a, cudaStream_t st) {
     constexpr int WO = 34 - 2 * K;
-    if (a.nx % 4 != 0 || a.pitch % 4 != 0) return cudaErrorInvalidValue;
-    using HK = HalfDeepKernel<Q, S, H, K, NW, NS, MINB, false>;
+    using HK = HalfDeepKernel<Q, S, H, K, NW, NS, MINB, false, RK>;
     unsigned full = 0;
     cudaError_t e = HK::get(&full);
     if (e != cudaSuccess) return e;
@@ -294,9 +294,19 @@ cudaError_t launch_half_deep(const StepArgs &a, cudaStream_t st) {
     const int64_t band = (a.ny + nb - 1) / nb, nbands = (a.ny + band - 1) / band;
     const int64_t units = nstrips * nbands;
     const unsigned grid = units < nwarps ? (unsigned)((units + NW - 1) / NW) : full;
-    step_half_deep_kernel<Q, S, H, K, NW, NS, MINB, false>
+    step_half_deep_kernel<Q, S, H, K, NW, NS, MINB, false, RK>
         <<<grid, NW * 32, HK::smem, st>>>(a, nstrips, nbands, band, nullptr, 0, 0, a.rho_out != nullptr);
     return cudaGetLastError();
+}
+
+// Two-species Gray-Scott grids run the form with the reaction fixed at
+// compile time; the others test the kind per site.
+template <int Q, int S, int H, int K, int NW, int NS, int MINB>
+cudaError_t launch_half_deep(const StepArgs &a, cudaStream_t st) {
+    if (a.nx % 4 != 0 || a.pitch % 4 != 0) return cudaErrorInvalidValue;
+    if constexpr (S == 2)
+        if (a.rkind == kGrayScott) return launch_half_deep_rk<Q, S, H, K, NW, NS, MINB, kGrayScott>(a, st);
+    return launch_half_deep_rk<Q, S, H, K, NW, NS, MINB, -1>(a, st);
 }
 
 }  // namespace

@@ -126,20 +126,20 @@ __device__ __forceinline__ void tile_half(const StepArgs &a, int64_t x0, int64_t
             uint2 raw;
             pull4h<H>(gi + wrap(yc - ey, ny) * pitch, c, ex, gp, raw);
             if (ey != 0) raw = __ldg(reinterpret_cast<const uint2 *>(gi + yc * pitch + c.xc));
-            gsum[0] += h2f<H>(raw.x);
-            gsum[1] += h2f<H>(raw.x >> 16);
-            gsum[2] += h2f<H>(raw.y);
-            gsum[3] += h2f<H>(raw.y >> 16);
+            gsum[0] = rn_add(gsum[0], h2f<H>(raw.x));
+            gsum[1] = rn_add(gsum[1], h2f<H>(raw.x >> 16));
+            gsum[2] = rn_add(gsum[2], h2f<H>(raw.y));
+            gsum[3] = rn_add(gsum[3], h2f<H>(raw.y >> 16));
             const float w = weight<Q, float>(i);
 #pragma unroll
-            for (int j = 0; j < kVec; ++j) f[s][i][j] = fmaf(w, rw[1 - ey][j + 1 - ex], gp[j]);
+            for (int j = 0; j < kVec; ++j) f[s][i][j] = rn_fma(w, rw[1 - ey][j + 1 - ex], gp[j]);
         }
 #pragma unroll
         for (int j = 0; j < kVec; ++j) {
-            f[s][0][j] = fmaf(weight<Q, float>(0), rw[1][j + 1], -gsum[j]);
+            f[s][0][j] = rn_fma(weight<Q, float>(0), rw[1][j + 1], -gsum[j]);
             float r = f[s][0][j];
 #pragma unroll
-            for (int i = 1; i < Q; ++i) r += f[s][i][j];
+            for (int i = 1; i < Q; ++i) r = rn_add(r, f[s][i][j]);
             rho[s][j] = r;
         }
     }
@@ -162,15 +162,16 @@ __device__ __forceinline__ void tile_half(const StepArgs &a, int64_t x0, int64_t
             char *base = dst + (size_t)s * species_bytes;
             float *rs = reinterpret_cast<float *>(base);
             unsigned short *g = reinterpret_cast<unsigned short *>(base + (size_t)plane * 4);
-            const float c1 = 1.f - (float)a.omega[s];
+            const float c1 = rn_sub(1.f, (float)a.omega[s]);
             *reinterpret_cast<float4 *>(rs + y * pitch + x0) =
-                make_float4(rho[s][0] + R[s][0], rho[s][1] + R[s][1], rho[s][2] + R[s][2], rho[s][3] + R[s][3]);
+                make_float4(rn_add(rho[s][0], R[s][0]), rn_add(rho[s][1], R[s][1]), rn_add(rho[s][2], R[s][2]),
+                            rn_add(rho[s][3], R[s][3]));
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
                 const float w = weight<Q, float>(i);
                 float hv[kVec];
 #pragma unroll
-                for (int j = 0; j < kVec; ++j) hv[j] = c1 * fmaf(-w, rho[s][j], f[s][i][j]);
+                for (int j = 0; j < kVec; ++j) hv[j] = rn_mul(c1, rn_fma(-w, rho[s][j], f[s][i][j]));
                 *reinterpret_cast<uint2 *>(g + (int64_t)(i - 1) * plane + y * pitch + x0) =
                     make_uint2(f2h2<H>(hv[0], hv[1]), f2h2<H>(hv[2], hv[3]));
             }
