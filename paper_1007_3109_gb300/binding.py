@@ -296,8 +296,9 @@ def lb_rd_variant_name(precision, variant: int) -> str:
 
 def variant_steps(name: str) -> int:
     """Time steps per launch of a launch variant, from its name: tb2*_
-    variants two, deep<K><letters>_ and hdeep<K>_ variants K, the others one."""
-    m = re.match(r"h?deep(\d+)[a-z]*_", name)
+    variants two, deep<K><letters>_, hdeep<K>_ and hpair<K>_ variants K, the
+    others one."""
+    m = re.match(r"(?:h?deep|hpair)(\d+)[a-z]*_", name)
     if m:
         return int(m.group(1))
     return 2 if name.startswith("tb2") else 1

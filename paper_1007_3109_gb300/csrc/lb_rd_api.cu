@@ -134,6 +134,7 @@ int variant_steps(const lb_rd_handle *h, int v) {
 bool variant_fits(const lb_rd_handle *h, int v) {
     if (h->inplace) return h->prec == LB_RD_FP64 || h->cfg.nx % lbrd::kAAVariants[v].sites == 0;
     if (h->general) return h->prec == LB_RD_FP64 || h->cfg.nx % lbrd::kGeneralVariants[v].sites == 0;
+    if (is_half(h)) return h->cfg.nx % lbrd::kHalfVariantNx[v] == 0;
     return h->prec != LB_RD_FP32 || h->cfg.nx % lbrd::kF32Variants[v].nx_multiple == 0;
 }
 
@@ -769,6 +770,7 @@ int lb_rd_set_variant(lb_rd_handle *h, int32_t variant) {
                                       " needs nx to be a multiple of " +
                                       std::to_string(h->inplace   ? lbrd::kAAVariants[variant].sites
                                                      : h->general ? lbrd::kGeneralVariants[variant].sites
+                                                     : is_half(h) ? lbrd::kHalfVariantNx[variant]
                                                                   : lbrd::kF32Variants[variant].nx_multiple));
     if (variant_steps(h, variant) >= 2) {
         h->tb_variant = variant;

@@ -110,9 +110,11 @@ StepShape step_shape_half(int64_t nx, int64_t ny);
 cudaError_t launch_step_half(int Q, int S, int half_kind, const StepArgs &a, cudaStream_t st);
 extern const char *const kHalfVariantNames[];
 extern const int kHalfVariantSteps[];  // time steps per launch of each variant
+extern const int kHalfVariantNx[];     // the variant needs nx % kHalfVariantNx[v] == 0
 extern const int kHalfVariantCount;
 // Depth-K launches of the 16-bit deviation step (variant v of that family).
 cudaError_t launch_step_half_deep(int v, int Q, int S, int half_kind, const StepArgs &a, cudaStream_t st);
+cudaError_t launch_step_half_pair(int v, int Q, int S, int half_kind, const StepArgs &a, cudaStream_t st);
 cudaError_t launch_step_half_variant(int v, int Q, int S, int half_kind, const StepArgs &a, cudaStream_t st);
 cudaError_t launch_init_half(int Q, int S, int half_kind, const InitArgs &a, cudaStream_t st);
 

@@ -113,19 +113,25 @@ cudaError_t dispatch_variant(int v, int Q, int S, const StepArgs &a, cudaStream_
         case 4: return dispatch_shape<H, 64, 2, 6>(Q, S, a, st);
         case 5: case 6: case 7: case 8: case 9: case 10:
             return launch_step_half_deep(v - 5, Q, S, H, a, st);
+        case 11: case 12: case 13: case 14: case 15: case 16:
+            return launch_step_half_pair(v - 11, Q, S, H, a, st);
         default: return cudaErrorInvalidValue;
     }
 }
 }  // namespace
 
 // One step per launch (tile shape, register budget), then temporal blocking to
-// depth K (step_half_deep_kernel.cuh): hdeep<K>_<threads>_minb<blocks>[_s<rows staged>].
-const char *const kHalfVariantNames[] = {"half_64x2", "half_64x2_minb5", "half_32x4_minb4", "half_128x2_minb2",
-                                         "half_64x2_minb6", "hdeep2_128_minb4", "hdeep3_128_minb3",
-                                         "hdeep4_128_minb2", "hdeep4_128_minb3", "hdeep3_128_minb3_s5",
-                                         "hdeep5_128_minb2"};
-const int kHalfVariantSteps[] = {1, 1, 1, 1, 1, 2, 3, 4, 4, 3, 5};
-const int kHalfVariantCount = 11;
+// depth K (step_half_deep_kernel.cuh): hdeep<K>_<threads>_minb<blocks>[_s<rows staged>],
+// and with two columns per lane (step_half_pair_kernel.cuh, nx a multiple of 8): hpair<K>_.
+const char *const kHalfVariantNames[] = {"half_64x2",          "half_64x2_minb5",  "half_32x4_minb4",
+                                         "half_128x2_minb2",   "half_64x2_minb6",  "hdeep2_128_minb4",
+                                         "hdeep3_128_minb3",   "hdeep4_128_minb2", "hdeep4_128_minb3",
+                                         "hdeep3_128_minb3_s5", "hdeep5_128_minb2", "hpair4_128_minb2",
+                                         "hpair4_128_minb3",   "hpair5_128_minb2", "hpair3_128_minb3",
+                                         "hpair6_128_minb2",   "hpair2_128_minb4"};
+const int kHalfVariantSteps[] = {1, 1, 1, 1, 1, 2, 3, 4, 4, 3, 5, 4, 4, 5, 3, 6, 2};
+const int kHalfVariantNx[] = {4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 8, 8, 8, 8, 8, 8};
+const int kHalfVariantCount = 17;
 
 cudaError_t launch_step_half_variant(int v, int Q, int S, int half_kind, const StepArgs &a, cudaStream_t st) {
     if (a.nx % kVec) return cudaErrorInvalidValue;

@@ -137,8 +137,8 @@ def test_variant_table_on_the_host(lib):
     assert B.lb_rd_variant_count("fp64") == 1
     half = [B.lb_rd_variant_name("fp32_bf16dev", v) for v in range(B.lb_rd_variant_count("fp32_bf16dev"))]
     assert half == [B.lb_rd_variant_name("fp32_fp16dev", v) for v in range(len(half))]
-    assert sorted(set(B.variant_steps(x) for x in half)) == [1, 2, 3, 4, 5]
-    assert all(B.variant_steps(x) == int(x[5]) for x in half if x.startswith("hdeep"))
+    assert sorted(set(B.variant_steps(x) for x in half)) == [1, 2, 3, 4, 5, 6]
+    assert all(B.variant_steps(x) == int(x[5]) for x in half if x.startswith(("hdeep", "hpair")))
 
 
 def test_null_arguments_are_errors_not_crashes(lib):
