@@ -237,7 +237,8 @@ LB_RD_API int lb_rd_launch_count(const lb_rd_handle *h, int64_t *launches);
  * bulk-copy staging, temporal blocking of K = 2 .. 8 steps per launch:
  * FP32 variants named tb2*_ (two steps) and deep<K>*_ (K steps, the deep1_
  * form one step; deep<K>vw*_ with two columns per lane), 16-bit deviation
- * variants hdeep<K>_ (K steps); see lb_rd_variant_name).  lb_rd_autotune times every
+ * variants hdeep<K>_ and hpair<K>_ (K steps; hpair: two columns per lane, nx
+ * a multiple of 8); see lb_rd_variant_name).  lb_rd_autotune times every
  * variant that fits the grid on the handle's own state -- reading the current
  * state and writing the spare copy, so the simulation is unchanged -- with
  * one warm-up launch and `iters` timed launches each, and selects the fastest
@@ -319,7 +320,9 @@ LB_RD_API int lb_rd_batch_set_graph(lb_rd_batch *b, int32_t steps_per_graph);
  * units of all instances (FP32, two state copies, any nx; bitwise the same as
  * K single steps; for K <= 5 (D2Q9) or 6 (D2Q5) its form with two columns per
  * lane; the default for such batches: 5 for D2Q9, 6 for D2Q5); 16-bit
- * deviation storage runs its own depth-K kernel, K = 2 .. 5 (default 4).
+ * deviation storage runs its own depth-K kernels, K = 2 .. 5 (the
+ * two-column form when every nx is a multiple of 8, default 5; else default
+ * 4).
  * EINVAL if neither applies.  1: one step per launch (the default for other
  * batches).  The graphs of lb_rd_batch_set_graph hold steps_per_graph / K
  * launches.  Synchronises the batch's stream. */
@@ -341,7 +344,7 @@ LB_RD_API int lb_rd_batch_get_time(const lb_rd_batch *b, int64_t *t, int64_t *la
  * when a request finishes sooner), by launches of the batched kernels over
  * all of them: for FP32 and 16-bit deviation requests with two state copies,
  * tick / K launches of the depth-K kernel (K as the batches' default: 5 for
- * D2Q9 and 6 for D2Q5 in FP32, 4 in 16-bit storage) and one launch of the
+ * D2Q9 and 6 for D2Q5 in FP32; 5 or 4 in 16-bit storage) and one launch of the
  * tick % K
  * steps left (a single step if one is left), otherwise one launch per step;
  * the last launch of a tick also writes the densities.  Requests that arrive

@@ -240,7 +240,8 @@ cudaError_t launch_deep(lb_rd_batch *b, int K, int parity, bool emit) {
     const int rk = lbrd::list_reaction_kind(b->deep_base.data(), (int)b->deep_base.size());
     if (half_batch(b))
         return lbrd::launch_batch_half_deep(K, b->Q, b->S, b->mode - 1, b->d_deep[K][parity], (int)b->cfgs.size(),
-                                            b->deep_units[K], emit, rk, b->stream);
+                                            b->deep_units[K], emit, rk,
+                                            lbrd::list_nx8(b->deep_base.data(), (int)b->deep_base.size()), b->stream);
     return lbrd::launch_batch_deep(K, b->Q, b->S, b->deep_v16, b->d_deep[K][parity], (int)b->cfgs.size(),
                                    b->deep_units[K], emit, rk, b->stream);
 }
@@ -408,10 +409,12 @@ int lb_rd_batch_create(const lb_rd_config *cfgs, int32_t n, lb_rd_batch **out) {
             b->deep_base[i].a.rho_out = b->rho + b->rho_off[i];
         }
         // default: the depth-K kernel, K = 5 (D2Q9) or 6 (D2Q5) in its
-        // two-column form, K = 4 for 16-bit deviation storage; should its
+        // two-column form; 16-bit deviation storage: K = 5 in the two-column
+        // form (every nx a multiple of 8), else 4; should its
         // descriptors not be planned (no launch shape for this device), the
         // batch keeps the previous default
-        const int K = half ? 4 : lbrd::batch_deep_default_k(b->Q);
+        const int K = half ? lbrd::batch_half_default_k(lbrd::list_nx8(b->deep_base.data(), (int)b->deep_base.size()))
+                           : lbrd::batch_deep_default_k(b->Q);
         if (!e && plan_deep(b, K) == cudaSuccess) b->steps_per_launch = K;
         cudaGetLastError();  // clear a non-sticky error of the attempt
     }

@@ -177,10 +177,16 @@ struct DeepItem {
     int64_t unit_begin, nstrips, band;
 };
 // The same over 16-bit deviation storage (K = 2 .. 5; half_kind 0 bf16, 1 fp16;
-// any nx a multiple of 4), the depth-K kernel of step_half_deep_kernel.cuh.
+// any nx a multiple of 4): the two-column depth-K kernel of
+// step_half_pair_kernel.cuh when every grid has nx a multiple of 8 (v8, which
+// the caller passes to the launch as the plan found it), else the one-column
+// kernel of step_half_deep_kernel.cuh.
 int64_t batch_half_deep_plan(int K, int Q, int S, int half_kind, DeepItem *items, int n);
+// Default steps per launch of a 16-bit list: 5 with the two-column kernel
+// (v8), else 4.
+int batch_half_default_k(bool v8);
 cudaError_t launch_batch_half_deep(int K, int Q, int S, int half_kind, const DeepItem *items, int n,
-                                   int64_t total_units, bool emit, int rk, cudaStream_t st);
+                                   int64_t total_units, bool emit, int rk, bool v8, cudaStream_t st);
 bool batch_deep_depth_ok(int K);
 // Default steps per launch of a list of grids: 5 (D2Q9) / 6 (D2Q5), the
 // fastest two-column forms over a list (the grid's parameters read from a
@@ -189,6 +195,12 @@ int batch_deep_default_k(int Q);
 int64_t batch_deep_plan(int K, int Q, int S, bool v16, DeepItem *items, int n);
 cudaError_t launch_batch_deep(int K, int Q, int S, bool v16, const DeepItem *items, int n, int64_t total_units,
                               bool emit, int rk, cudaStream_t st);
+// Every item of a host-side list has nx and the row pitch multiples of 8.
+inline bool list_nx8(const DeepItem *items, int n) {
+    for (int i = 0; i < n; ++i)
+        if (items[i].a.nx % 8 != 0 || items[i].a.pitch % 8 != 0) return false;
+    return true;
+}
 // The reaction kind every item of a host-side list has, or -1.
 inline int list_reaction_kind(const DeepItem *items, int n) {
     if (n <= 0) return -1;

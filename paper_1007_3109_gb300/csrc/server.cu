@@ -262,16 +262,17 @@ void run_tick(lb_rd_server *s) {
     }
     // K-step launches: FP32 and 16-bit deviation requests with two state
     // copies run the tick as q = tick / K depth-K launches (FP32:
-    // lbrd::batch_deep_default_k; 16-bit storage: 4) and, for the r = tick % K
+    // lbrd::batch_deep_default_k; 16-bit storage: lbrd::batch_half_default_k) and, for the r = tick % K
     // steps left, one
     // depth-r launch (r >= 2) or one single step (r = 1); the tick's last
     // launch writes the densities.  Other requests: one launch per step.
     bool any_inplace = false;
     for (Request *r : act) any_inplace = any_inplace || r->cfg.streaming == LB_RD_STREAM_INPLACE;
-    bool v16 = true;
+    bool v16 = true, v8 = true;  // every request has nx and pitch multiples of 4 (of 8)
     for (Request *r : act) v16 = v16 && r->cfg.nx % 4 == 0 && r->pitch % 4 == 0;
-    const bool half = s->mode == 1 || s->mode == 2;  // 16-bit deviation storage: its own depth-K kernel
-    const int K = half ? 4 : lbrd::batch_deep_default_k(s->Q);
+    for (Request *r : act) v8 = v8 && r->cfg.nx % 8 == 0 && r->pitch % 8 == 0;
+    const bool half = s->mode == 1 || s->mode == 2;  // 16-bit deviation storage: its own depth-K kernels
+    const int K = half ? lbrd::batch_half_default_k(v8) : lbrd::batch_deep_default_k(s->Q);
     const bool deep = (s->mode == 0 || half) && !any_inplace && tick >= 2;
     int64_t n_multi = deep ? tick / K : 0;
     int rem = deep ? (int)(tick % K) : 0;  // steps of the depth-r launch (0: none)
@@ -366,12 +367,12 @@ void run_tick(lb_rd_server *s) {
     for (int64_t l = 0; l < L && !e; ++l) {
         if (l < n_multi) {
             e = half ? lbrd::launch_batch_half_deep(K, s->Q, S, s->mode - 1, s->d_deep + (l & 1) * n, (int)n,
-                                                    deep_units, l == L - 1, rk, s->stream)
+                                                    deep_units, l == L - 1, rk, v8, s->stream)
                      : lbrd::launch_batch_deep(K, s->Q, S, v16, s->d_deep + (l & 1) * n, (int)n, deep_units,
                                                l == L - 1, rk, s->stream);
         } else if (l == n_multi && rem > 0) {
             e = half ? lbrd::launch_batch_half_deep(rem, s->Q, S, s->mode - 1, s->d_deep + 2 * n, (int)n, rem_units,
-                                                    l == L - 1, rk, s->stream)
+                                                    l == L - 1, rk, v8, s->stream)
                      : lbrd::launch_batch_deep(rem, s->Q, S, v16, s->d_deep + 2 * n, (int)n, rem_units, l == L - 1,
                                                rk, s->stream);
         } else {

@@ -199,13 +199,16 @@ def test_batch_k_steps_per_launch_equals_single_handles(lat, K, staging, graph):
 
 @pytest.mark.parametrize("precision", ["fp32_bf16dev", "fp32_fp16dev"])
 @pytest.mark.parametrize("K", [2, 3, 4, 5])
-def test_batch_half_k_steps_per_launch_equals_single_handles(precision, K):
-    """16-bit deviation storage: K = 2 .. 5 steps per launch run its depth-K
+@pytest.mark.parametrize("shapes", [[(64, 48), (100, 37), (36, 70), (8, 3), (256, 16), (68, 9)],
+                                    [(64, 48), (104, 37), (40, 70), (8, 3), (256, 16), (72, 9)]],
+                         ids=["nx%4", "nx%8"])
+def test_batch_half_k_steps_per_launch_equals_single_handles(precision, K, shapes):
+    """16-bit deviation storage: K = 2 .. 5 steps per launch run a depth-K
     kernel over the (band, strip) units of all instances (each level holds
-    rho* and the deviations rounded as a single step stores them); each
-    instance gives the bits of a single handle (which runs single steps),
-    over calls of 21 steps (21 // K launches of K and one of the rest)."""
-    shapes = [(64, 48), (100, 37), (36, 70), (8, 3), (256, 16), (68, 9)]
+    rho* and the deviations rounded as a single step stores them; the
+    two-column kernel when every instance has nx % 8 == 0); each instance
+    gives the bits of a single handle (which runs single steps), over calls
+    of 21 steps (21 // K launches of K and one of the rest)."""
     cfgs = [dict(lattice="D2Q9", nspecies=2, nx=nx, ny=ny, tau=[0.8 + 0.05 * j, 0.65], reaction="gray_scott",
                  F=0.03 + 0.004 * j, k=0.06 - 0.002 * j, precision=precision) for j, (nx, ny) in enumerate(shapes)]
     steps = 21

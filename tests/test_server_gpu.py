@@ -233,13 +233,15 @@ def test_inplace_requests_mix_and_double_the_residents():
 
 
 @pytest.mark.parametrize("precision", ["fp32_bf16dev", "fp32_fp16dev"])
-def test_half_storage_requests_equal_single_handles(precision):
-    """A server of 16-bit deviation storage: ticks run the 16-bit depth-K
-    kernel (K = 4 steps per launch, one launch for the rest) over all
-    resident requests; every result is bitwise a single handle's (which runs
-    single steps: each level rounds the deviations as a single step stores
-    them)."""
-    sides = [(64, 41), (36, 17), (68, 9), (128, 30)]
+@pytest.mark.parametrize("sides", [[(64, 41), (36, 17), (68, 9), (128, 30)], [(64, 41), (40, 17), (72, 9), (128, 30)]],
+                         ids=["nx%4", "nx%8"])
+def test_half_storage_requests_equal_single_handles(precision, sides):
+    """A server of 16-bit deviation storage: ticks run a 16-bit depth-K
+    kernel over all resident requests (the one-column kernel, K = 4 steps per
+    launch, unless every request has nx % 8 == 0: the two-column kernel, K =
+    5), one launch for the rest; every result is bitwise a single handle's
+    (which runs single steps: each level rounds the deviations as a single
+    step stores them)."""
     reqs = []
     for j, (side, steps) in enumerate(sides):
         kw, rho0, _ = _request(60 + j, side, 1 + j % 2, steps)
