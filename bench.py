@@ -653,7 +653,8 @@ def main():
     ap.add_argument("--cpu-window", type=int, default=1024)
     ap.add_argument("--cpu-steps", type=int, default=2000,
                     help="FP64 oracle steps of the CPU baseline sample (about 10-30 s on the host cores)")
-    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--e2e-steps", type=int, default=0,
+                    help="steps of each end-to-end repetition (0: the workload's full run, 10000 for gs_8192)")
     ap.add_argument("--batch-steps", type=int, default=20,
                     help="steps of the gs_sweep_256 batched sub-measure beside the headline (0: skip)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
@@ -855,10 +856,11 @@ def main():
     pinned_out = torch.empty(rho0.shape, dtype=torch.float64).pin_memory()
     mass_out = np.empty(2)
     rho_in_np, rho_out_np = pinned_in.numpy(), pinned_out.numpy()
-    # Three repetitions (each: host rho0 in, e2e_steps steps, host rho out); the
-    # median over them, each the slowest rank's time, is the result: the host
-    # copies share the machine's memory system with other jobs.
-    e2e_steps = args.e2e_steps
+    # Three repetitions of the workload as a user runs it (each: host rho0 in,
+    # the configuration's full run of e2e_steps steps, host rho out); the median
+    # over them, each the slowest rank's time, is the result: the host copies
+    # share the machine's memory system with other jobs.
+    e2e_steps = args.e2e_steps or int(w["steps"])
     e2e_reps = []
     for _ in range(3):
         barrier()

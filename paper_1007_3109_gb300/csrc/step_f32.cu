@@ -125,6 +125,10 @@ const F32Variant kF32Variants[] = {
     {"deep4vwa_128_minb2", 128, 4, 2, 4, 4, 1},
     {"deep6vwpa_128_minb1", 128, 6, 1, 4, 6, 1},
     {"deep3vwpa_128_minb2_s5", 128, 3, 2, 4, 3, 1},
+    // two columns per lane, two or three rows staged ahead
+    {"deep6vwp_128_minb1_s5", 128, 6, 1, 4, 6, 4},
+    {"deep6vwp_128_minb1_s6", 128, 6, 1, 4, 6, 4},
+    {"deep5vw_128_minb2_s6", 128, 5, 2, 4, 5, 4},
 };
 const int kF32VariantCount = sizeof(kF32Variants) / sizeof(kF32Variants[0]);
 

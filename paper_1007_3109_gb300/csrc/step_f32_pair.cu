@@ -36,6 +36,10 @@ cudaError_t launch_step_f32_pair(int v, int Q, int S, const StepArgs &a, cudaStr
         case 12: return dispatch_pair<4, 4, 4, 2, false, true>(Q, S, a, st);
         case 13: return dispatch_pair<6, 4, 4, 1, true, true>(Q, S, a, st);
         case 14: return dispatch_pair<3, 4, 5, 2, true, true>(Q, S, a, st);
+        // more rows staged ahead (two or three): the smaller D2Q5 rows leave L1 its share
+        case 15: return dispatch_pair<6, 4, 5, 1, true>(Q, S, a, st);
+        case 16: return dispatch_pair<6, 4, 6, 1, true>(Q, S, a, st);
+        case 17: return dispatch_pair<5, 4, 6, 2, false>(Q, S, a, st);
         default: return cudaErrorInvalidValue;
     }
 }
