@@ -32,9 +32,11 @@
 //     level K is stored for columns HL .. 63 - HL (8-byte stores; the last
 //     column of an odd nx alone in the ANY form), and with `emit` rho(t + K)
 //     of level K too.
-// Each level is tb::collide_site per column: K levels give the bits of K
-// single steps.  Units, bands, the periodic wrap and the FP64 mass reduction
-// are those of the one-column kernel.
+// Each level collides the lane's two columns together (tb::collide_pair: the
+// operations of tb::collide_site per column, one test of the reaction kind
+// for both, or none with the kind fixed at compile time): K levels give the
+// bits of K single steps.  Units, bands, the periodic wrap and the FP64 mass
+// reduction are those of the one-column kernel.
 #pragma once
 
 #include "step_f32_deep_kernel.cuh"
