@@ -195,7 +195,7 @@ def batch_mode(args):
     n = w["nx"]
     ninst = args.instances or w["instances"]
     taus = [float(B.lb_rd_tau_from_diffusion(D)) for D in w["D"]]
-    cfgs = [dict(lattice="D2Q9", nspecies=2, nx=n, ny=n, tau=taus, reaction="gray_scott", F=float(F[i]),
+    cfgs = [dict(lattice=args.lattice, nspecies=2, nx=n, ny=n, tau=taus, reaction="gray_scott", F=float(F[i]),
                  k=float(k[i]), precision=args.precision) for i in range(ninst)]
     rho0s = [inputs.rho0_square(n, n, seed=w["seed"] + i) for i in range(ninst)]
     K, W = args.steps, args.warmup
@@ -247,15 +247,16 @@ def batch_mode(args):
     for sim in sims:
         sim.close()
     peak, peak_kind = measured_peaks()
-    bps = BYTES_PER_SITE[("D2Q9", args.precision, 2)]
+    bps = BYTES_PER_SITE[(args.lattice, args.precision, 2)]
     line = {"metric": "MLUPS", "value": ssu / (batched_ms / 1e3) / 1e6, "unit": "MLUPS (species-site updates/s / 1e6)",
             "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": batched_ms / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
             "data": "synthetic",
-            "config": {"workload": "gs_sweep_256", "instances": ninst, "nx": n, "ny": n, "species": 2,
-                       "precision": args.precision, "graph_steps": 64, "steps_per_launch": steps_per_launch,
+            "config": {"workload": "gs_sweep_256", "lattice": args.lattice, "instances": ninst, "nx": n, "ny": n,
+                       "species": 2, "precision": args.precision, "graph_steps": 64,
+                       "steps_per_launch": steps_per_launch,
                        "batched_ms_per_step_by_steps_per_launch": {str(k): v[0] / K for k, v in per_launch.items()},
-                       "l2": f"no flush: state of {2 * ninst * sim_state_bytes('D2Q9', args.precision, n) / 1e9:.2f} GB"},
+                       "l2": f"no flush: state of {2 * ninst * sim_state_bytes(args.lattice, args.precision, n) / 1e9:.2f} GB"},
             "roofline": {"bound": "hbm", "achieved": bps * n * n * ninst / (batched_ms / launches / 1e3) / 1e9,
                          "peak": peak, "unit": "GB/s", "peak_kind": peak_kind,
                          "bytes_per_site_per_launch": bps, "steps_per_launch": K / launches,
@@ -272,10 +273,10 @@ def batch_mode(args):
         otaus = [float(t) for t in orc.tau_from_diffusion(np.array(w["D"]))]
         t_cpu, ssu_cpu = 0.0, 0
         for i in range(nsample):
-            f = orc.init("D2Q9", rho0s[i])
+            f = orc.init(args.lattice, rho0s[i])
             reac = Reaction("gray_scott", F=float(F[i]), k=float(k[i]))
             t0 = time.perf_counter()
-            orc.run("D2Q9", otaus, reac, f, args.cpu_steps)
+            orc.run(args.lattice, otaus, reac, f, args.cpu_steps)
             t_cpu += time.perf_counter() - t0
             ssu_cpu += 2 * n * n * args.cpu_steps
         line["cpu_baseline"] = {"value": ssu_cpu / t_cpu / 1e6, "unit": "MLUPS", "cores": orc.threads(),

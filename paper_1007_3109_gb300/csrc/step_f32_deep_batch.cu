@@ -12,14 +12,16 @@ namespace {
 // faster one: depths whose carried levels fit the register file without
 // heavy spills (K <= 5 for D2Q9, K <= 6 for D2Q5); its any-nx form unless
 // every grid has nx a multiple of 4.  Four warps, the pulls from earlier rows
-// first, five staged rows below K = 5.
+// first, five staged rows below K = 5 and for D2Q5 (whose smaller rows leave
+// L1 its share with two rows staged ahead).
 template <int Q, int K, bool V16>
 struct UsePair {
     static constexpr bool value = Q == 9 ? K <= 5 : K <= 6;
 };
 template <int Q, int S, int K, bool V16, int RK = -1>
-struct PairShape : PairKernel<Q, S, K, 4, (K < 5 ? 5 : 4), (K == 6 ? 1 : 2), true, true, !V16, RK> {
-    static constexpr int NW = 4, NS = K < 5 ? 5 : 4, MINB = K == 6 ? 1 : 2;
+struct PairShape
+    : PairKernel<Q, S, K, 4, (K < 5 || Q == 5 ? 5 : 4), (K == 6 ? 1 : 2), true, true, !V16, RK> {
+    static constexpr int NW = 4, NS = K < 5 || Q == 5 ? 5 : 4, MINB = K == 6 ? 1 : 2;
 };
 
 // Batched launch shapes per K: the single-grid choices (K = 4, 5: six warps,
