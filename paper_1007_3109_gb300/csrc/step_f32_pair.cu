@@ -40,6 +40,9 @@ cudaError_t launch_step_f32_pair(int v, int Q, int S, const StepArgs &a, cudaStr
         case 15: return dispatch_pair<6, 4, 5, 1, true>(Q, S, a, st);
         case 16: return dispatch_pair<6, 4, 6, 1, true>(Q, S, a, st);
         case 17: return dispatch_pair<5, 4, 6, 2, false>(Q, S, a, st);
+        // eight warps per block, one block per SM: the SM's warps walk eight adjacent strips
+        case 18: return dispatch_pair<5, 8, 4, 1, false>(Q, S, a, st);
+        case 19: return dispatch_pair<6, 8, 5, 1, true>(Q, S, a, st);
         default: return cudaErrorInvalidValue;
     }
 }
