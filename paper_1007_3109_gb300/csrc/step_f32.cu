@@ -131,6 +131,7 @@ const F32Variant kF32Variants[] = {
     {"deep5vw_128_minb2_s6", 128, 5, 2, 4, 5, 4},
     {"deep5vw_256_minb1", 256, 5, 1, 4, 5, 4},
     {"deep6vwp_256_minb1_s5", 256, 6, 1, 4, 6, 4},
+    {"deep5vwpa_256_minb1", 256, 5, 1, 4, 5, 1},
 };
 const int kF32VariantCount = sizeof(kF32Variants) / sizeof(kF32Variants[0]);
 

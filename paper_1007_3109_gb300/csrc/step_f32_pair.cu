@@ -43,6 +43,7 @@ cudaError_t launch_step_f32_pair(int v, int Q, int S, const StepArgs &a, cudaStr
         // eight warps per block, one block per SM: the SM's warps walk eight adjacent strips
         case 18: return dispatch_pair<5, 8, 4, 1, false>(Q, S, a, st);
         case 19: return dispatch_pair<6, 8, 5, 1, true>(Q, S, a, st);
+        case 20: return dispatch_pair<5, 8, 4, 1, true, true>(Q, S, a, st);
         default: return cudaErrorInvalidValue;
     }
 }
