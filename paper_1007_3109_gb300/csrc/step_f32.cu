@@ -132,6 +132,8 @@ const F32Variant kF32Variants[] = {
     {"deep5vw_256_minb1", 256, 5, 1, 4, 5, 4},
     {"deep6vwp_256_minb1_s5", 256, 6, 1, 4, 6, 4},
     {"deep5vwpa_256_minb1", 256, 5, 1, 4, 5, 1},
+    // two columns per lane, a row staged as soon as level 1 has read the oldest one: deep<K>vw[p]e_
+    {"deep6vwpe_128_minb1_s5", 128, 6, 1, 4, 6, 4},
 };
 const int kF32VariantCount = sizeof(kF32Variants) / sizeof(kF32Variants[0]);
 

@@ -20,7 +20,7 @@ cudaError_t launch_step_f32_variant_b(int v, int Q, int S, const StepArgs &a, cu
         case 48: case 49: case 50: case 51: case 52: case 53: case 54: case 55: case 56: case 57: case 58:
             return per_tile ? cudaErrorInvalidValue : launch_step_f32_deep(v - 28, Q, S, a, st);
         case 59: case 60: case 61: case 62: case 63: case 64: case 65: case 66: case 67: case 68: case 69:
-        case 70: case 71: case 72: case 73: case 74: case 75: case 76: case 77: case 78: case 79:
+        case 70: case 71: case 72: case 73: case 74: case 75: case 76: case 77: case 78: case 79: case 80:
             return per_tile ? cudaErrorInvalidValue : launch_step_f32_pair(v - 59, Q, S, a, st);
         default: return cudaErrorInvalidValue;
     }

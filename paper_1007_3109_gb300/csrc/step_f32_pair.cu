@@ -6,12 +6,12 @@ namespace lbrd {
 
 namespace {
 
-template <int K, int NW, int NS, int MINB, bool PP, bool ANY = false>
+template <int K, int NW, int NS, int MINB, bool PP, bool ANY = false, bool EA = false>
 cudaError_t dispatch_pair(int Q, int S, const StepArgs &a, cudaStream_t st) {
-    if (Q == 9 && S == 1) return launch_pair<9, 1, K, NW, NS, MINB, PP, ANY>(a, st);
-    if (Q == 9 && S == 2) return launch_pair<9, 2, K, NW, NS, MINB, PP, ANY>(a, st);
-    if (Q == 5 && S == 1) return launch_pair<5, 1, K, NW, NS, MINB, PP, ANY>(a, st);
-    if (Q == 5 && S == 2) return launch_pair<5, 2, K, NW, NS, MINB, PP, ANY>(a, st);
+    if (Q == 9 && S == 1) return launch_pair<9, 1, K, NW, NS, MINB, PP, ANY, EA>(a, st);
+    if (Q == 9 && S == 2) return launch_pair<9, 2, K, NW, NS, MINB, PP, ANY, EA>(a, st);
+    if (Q == 5 && S == 1) return launch_pair<5, 1, K, NW, NS, MINB, PP, ANY, EA>(a, st);
+    if (Q == 5 && S == 2) return launch_pair<5, 2, K, NW, NS, MINB, PP, ANY, EA>(a, st);
     return cudaErrorInvalidValue;
 }
 
@@ -44,6 +44,9 @@ cudaError_t launch_step_f32_pair(int v, int Q, int S, const StepArgs &a, cudaStr
         case 18: return dispatch_pair<5, 8, 4, 1, false>(Q, S, a, st);
         case 19: return dispatch_pair<6, 8, 5, 1, true>(Q, S, a, st);
         case 20: return dispatch_pair<5, 8, 4, 1, true, true>(Q, S, a, st);
+        // a row staged as soon as level 1 has read the oldest one (one more row in flight;
+        // D2Q5: the D2Q9 forms are slower so)
+        case 21: return dispatch_pair<6, 4, 5, 1, true, false, true>(Q, S, a, st);
         default: return cudaErrorInvalidValue;
     }
 }

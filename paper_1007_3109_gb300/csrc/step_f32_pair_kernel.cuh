@@ -77,8 +77,11 @@ struct PairGeom {
 
 // ANY: grids of any nx (the seam chunks copied column by column, the last
 // column of an odd nx stored alone); otherwise nx must be a multiple of 4.
-// RK >= 0: the grid's reaction kind, fixed at compile time (single grids).
-template <int Q, int S, int K, int NW, int NS, int MINB, bool BATCH, bool PP, bool ANY = false, int RK = -1>
+// RK >= 0: the grid's reaction kind, fixed at compile time.  EA: a row is
+// staged as soon as level 1 has read the oldest staged row, whose slot it
+// takes: NS - 2 rows in flight instead of NS - 3, in the same ring.
+template <int Q, int S, int K, int NW, int NS, int MINB, bool BATCH, bool PP, bool ANY = false, int RK = -1,
+          bool EA = false>
 __global__ void __launch_bounds__(NW * 32, MINB)
     step_pair_kernel(StepArgs a, int64_t nstrips, int64_t nbands, int64_t band, const DeepItem *__restrict__ items,
                      int nitems, int64_t total_units, int emit) {
@@ -86,7 +89,7 @@ __global__ void __launch_bounds__(NW * 32, MINB)
     constexpr int SQ = S * Q;
     constexpr int CW = 68;          // staged columns of a warp row: 17 chunks of four
     constexpr int kRow = SQ * CW;   // one staged row, all planes
-    constexpr int P = NS - 3;       // rows staged ahead of use
+    constexpr int P = EA ? NS - 2 : NS - 3;  // rows staged ahead of use
     constexpr int HL = PairGeom<K>::HL;
     constexpr int WO = PairGeom<K>::WO;
     constexpr int KC = K > 1 ? K - 1 : 1;
@@ -227,8 +230,8 @@ __global__ void __launch_bounds__(NW * 32, MINB)
         for (int s = 0; s < S; ++s) sum[s] = 0.f;
         int sl = 0;
         for (int j = 0; j < nrows; ++j) {
-            stage(j + P, sl + P >= NS ? sl + P - NS : sl + P);
-            cp_async_wait<P>();
+            if constexpr (!EA) stage(j + P, sl + P >= NS ? sl + P - NS : sl + P);
+            cp_async_wait<EA ? P - 1 : P>();  // this lane's copies of row j have landed
             __syncwarp();
             const int s1 = sl == 0 ? NS - 1 : sl - 1, s2 = s1 == 0 ? NS - 1 : s1 - 1;
             // staged rows of iterations j - 2, j - 1, j: pulled with e_iy = +1, 0, -1
@@ -267,6 +270,10 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                     f0[s][i] = L::ex(i) > 0 ? __shfl_up_sync(kFullMask, v.y, 1) : (L::ex(i) < 0 ? v.y : v.x);
                     f1[s][i] = L::ex(i) > 0 ? v.x : (L::ex(i) < 0 ? __shfl_down_sync(kFullMask, v.x, 1) : v.y);
                 }
+            if constexpr (EA) {  // every lane has read row j - 2: its slot takes row j + P
+                __syncwarp();
+                stage(j + P, sl + P >= NS ? sl + P - NS : sl + P);
+            }
             {
                 const SegArgs cg = p_coll();
                 collide_pair<Q, S, RK>(cg, f0, f1, rho0, rho1);
@@ -369,11 +376,12 @@ __global__ void __launch_bounds__(NW * 32, MINB)
     if (a.mass_out) block_mass_reduce<S, NW * 32>(acc, a.partials, a.counter, a.mass_out);
 }
 
-template <int Q, int S, int K, int NW, int NS, int MINB, bool BATCH, bool PP = false, bool ANY = false, int RK = -1>
+template <int Q, int S, int K, int NW, int NS, int MINB, bool BATCH, bool PP = false, bool ANY = false, int RK = -1,
+          bool EA = false>
 struct PairKernel {
     static constexpr size_t smem = (size_t)NW * NS * S * Q * 68 * sizeof(float);
     static cudaError_t get(unsigned *full) {
-        auto kern = step_pair_kernel<Q, S, K, NW, NS, MINB, BATCH, PP, ANY, RK>;
+        auto kern = step_pair_kernel<Q, S, K, NW, NS, MINB, BATCH, PP, ANY, RK, EA>;
         static std::atomic<bool> configured[64] = {};
         int dev = 0;
         cudaGetDevice(&dev);
@@ -387,10 +395,10 @@ struct PairKernel {
     }
 };
 
-template <int Q, int S, int K, int NW, int NS, int MINB, bool PP, bool ANY, int RK>
+template <int Q, int S, int K, int NW, int NS, int MINB, bool PP, bool ANY, int RK, bool EA>
 cudaError_t launch_pair_rk(const StepArgs &a, cudaStream_t st) {
     constexpr int WO = PairGeom<K>::WO;
-    using PK = PairKernel<Q, S, K, NW, NS, MINB, false, PP, ANY, RK>;
+    using PK = PairKernel<Q, S, K, NW, NS, MINB, false, PP, ANY, RK, EA>;
     unsigned full = 0;
     cudaError_t e = PK::get(&full);
     if (e != cudaSuccess) return e;
@@ -400,19 +408,19 @@ cudaError_t launch_pair_rk(const StepArgs &a, cudaStream_t st) {
     const int64_t band = (a.ny + nb - 1) / nb, nbands = (a.ny + band - 1) / band;
     const int64_t units = nstrips * nbands;
     const unsigned grid = units < nwarps ? (unsigned)((units + NW - 1) / NW) : full;
-    step_pair_kernel<Q, S, K, NW, NS, MINB, false, PP, ANY, RK>
+    step_pair_kernel<Q, S, K, NW, NS, MINB, false, PP, ANY, RK, EA>
         <<<grid, NW * 32, PK::smem, st>>>(a, nstrips, nbands, band, nullptr, 0, 0, a.rho_out != nullptr);
     return cudaGetLastError();
 }
 
 // Two-species Gray-Scott grids run the form with the reaction fixed at
 // compile time (no test of the kind in the row loop); the others test it.
-template <int Q, int S, int K, int NW, int NS, int MINB, bool PP, bool ANY = false>
+template <int Q, int S, int K, int NW, int NS, int MINB, bool PP, bool ANY = false, bool EA = false>
 cudaError_t launch_pair(const StepArgs &a, cudaStream_t st) {
     if ((!ANY && a.nx % 4 != 0) || a.pitch % 4 != 0) return cudaErrorInvalidValue;
     if constexpr (S == 2)
-        if (a.rkind == kGrayScott) return launch_pair_rk<Q, S, K, NW, NS, MINB, PP, ANY, kGrayScott>(a, st);
-    return launch_pair_rk<Q, S, K, NW, NS, MINB, PP, ANY, -1>(a, st);
+        if (a.rkind == kGrayScott) return launch_pair_rk<Q, S, K, NW, NS, MINB, PP, ANY, kGrayScott, EA>(a, st);
+    return launch_pair_rk<Q, S, K, NW, NS, MINB, PP, ANY, -1, EA>(a, st);
 }
 
 }  // namespace
