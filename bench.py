@@ -47,9 +47,14 @@ BYTES_PER_SITE = {("D2Q9", "fp32", 2): 144, ("D2Q5", "fp32", 2): 80, ("D2Q9", "f
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 
-def _src_hash(path):
-    with open(path, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+def _src_hash(names):
+    """Hash of a kernel's source files (its own file and the headers that hold
+    its arithmetic), in the order listed."""
+    h = hashlib.sha256()
+    for name in [names] if isinstance(names, str) else names:
+        with open(os.path.join(ROOT, "paper_1007_3109_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def measured_peaks():
@@ -810,8 +815,7 @@ def main():
         with open(TRAFFIC_FILE) as fh:
             tr = json.load(fh)
         ent = tr.get(f"{args.workload}/{args.lattice}/{args.precision}/{variant_name}")
-        if ent and ent.get("n") == n and ent.get("src_sha") == _src_hash(
-                os.path.join(ROOT, "paper_1007_3109_gb300", "csrc", ent["src"])):
+        if ent and ent.get("n") == n and ent.get("src_sha") == _src_hash(ent["src"]):
             traffic = ent["bytes_per_launch"]
             inst_per_launch = ent.get("warp_inst_per_launch")
     # Instruction-issue roofline of the same kernel (the limiter of a K-step

@@ -409,12 +409,11 @@ int lb_rd_batch_create(const lb_rd_config *cfgs, int32_t n, lb_rd_batch **out) {
             b->deep_base[i].a.rho_out = b->rho + b->rho_off[i];
         }
         // default: the depth-K kernel, K = 5 (D2Q9) or 6 (D2Q5) in its
-        // two-column form; 16-bit deviation storage: K = 5 in the two-column
-        // form (every nx a multiple of 8), else 4; should its
-        // descriptors not be planned (no launch shape for this device), the
-        // batch keeps the previous default
-        const int K = half ? lbrd::batch_half_default_k(lbrd::list_nx8(b->deep_base.data(), (int)b->deep_base.size()))
-                           : lbrd::batch_deep_default_k(b->Q);
+        // two-column form; 16-bit deviation storage: K = 4 (the two-column
+        // form where every nx is a multiple of 8); should its descriptors not
+        // be planned (no launch shape for this device), the batch keeps the
+        // previous default
+        const int K = half ? lbrd::batch_half_default_k() : lbrd::batch_deep_default_k(b->Q);
         if (!e && plan_deep(b, K) == cudaSuccess) b->steps_per_launch = K;
         cudaGetLastError();  // clear a non-sticky error of the attempt
     }

@@ -93,6 +93,15 @@ __device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, 
 __device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float rn_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
+// The same operations on pairs of floats, one packed FP32x2 instruction for
+// two (sm_100 and later): each component is rounded as the scalar form
+// above, so a pair gives the bits of the two scalar operations in half the
+// issue slots.
+__device__ __forceinline__ float2 rn_add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 rn_mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 rn_fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 pair2(float v) { return make_float2(v, v); }
+
 // FP32 and faster paths: (u v) v;  fma(F, 1 - u, -uvv);  fma(-(F + k), v,
 // uvv);  -kappa rho_A;  kappa rho_A.  RK >= 0 fixes the kind at compile time
 // (the caller has checked that kind == RK).

@@ -182,9 +182,9 @@ struct DeepItem {
 // the caller passes to the launch as the plan found it), else the one-column
 // kernel of step_half_deep_kernel.cuh.
 int64_t batch_half_deep_plan(int K, int Q, int S, int half_kind, DeepItem *items, int n);
-// Default steps per launch of a 16-bit list: 5 with the two-column kernel
-// (v8), else 4.
-int batch_half_default_k(bool v8);
+// Default steps per launch of a 16-bit list: 4, with either kernel (the
+// two-column form spills at K = 5).
+int batch_half_default_k();
 cudaError_t launch_batch_half_deep(int K, int Q, int S, int half_kind, const DeepItem *items, int n,
                                    int64_t total_units, bool emit, int rk, bool v8, cudaStream_t st);
 bool batch_deep_depth_ok(int K);

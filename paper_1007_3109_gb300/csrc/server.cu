@@ -272,7 +272,7 @@ void run_tick(lb_rd_server *s) {
     for (Request *r : act) v16 = v16 && r->cfg.nx % 4 == 0 && r->pitch % 4 == 0;
     for (Request *r : act) v8 = v8 && r->cfg.nx % 8 == 0 && r->pitch % 8 == 0;
     const bool half = s->mode == 1 || s->mode == 2;  // 16-bit deviation storage: its own depth-K kernels
-    const int K = half ? lbrd::batch_half_default_k(v8) : lbrd::batch_deep_default_k(s->Q);
+    const int K = half ? lbrd::batch_half_default_k() : lbrd::batch_deep_default_k(s->Q);
     const bool deep = (s->mode == 0 || half) && !any_inplace && tick >= 2;
     int64_t n_multi = deep ? tick / K : 0;
     int rem = deep ? (int)(tick % K) : 0;  // steps of the depth-r launch (0: none)

@@ -39,21 +39,44 @@ __device__ __forceinline__ void collide_site(const Args &a, float (&f)[S][Q], fl
 
 // collide_site for two sites at once: the two density sums side by side and
 // one test of the reaction kind (RK >= 0: fixed at compile time), the same
-// operations per site in the same order, so the same bits.
+// operations per site in the same order, so the same bits.  Two forms: one
+// scalar instruction per operation and site, or the two sites' operands
+// packed in pairs (FP32x2 instructions for the density sums and the
+// relaxation, half the issue slots).  Packed operands must sit in aligned
+// register pairs, which costs moves after the shifted pulls and, in kernels
+// already at the register limit, spills: the packed form is taken where a
+// level's carried state is small (S Q <= 10: D2Q5, or one D2Q9 species).
+template <int Q, int S>
+struct PackPair {
+    static constexpr bool value = S * Q <= 10;
+};
+
 template <int Q, int S, int RK = -1, typename Args>
 __device__ __forceinline__ void collide_pair(const Args &a, float (&f0)[S][Q], float (&f1)[S][Q], float (&rho0)[S],
                                              float (&rho1)[S]) {
     using L = Lattice<Q>;
+    if constexpr (PackPair<Q, S>::value) {
+        float2 r[S];
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-        float r0 = f0[s][0], r1 = f1[s][0];
+        for (int s = 0; s < S; ++s) {
+            r[s] = make_float2(f0[s][0], f1[s][0]);
 #pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            r0 = rn_add(r0, f0[s][i]);
-            r1 = rn_add(r1, f1[s][i]);
+            for (int i = 1; i < Q; ++i) r[s] = rn_add2(r[s], make_float2(f0[s][i], f1[s][i]));
+            rho0[s] = r[s].x;
+            rho1[s] = r[s].y;
         }
-        rho0[s] = r0;
-        rho1[s] = r1;
+    } else {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            float r0 = f0[s][0], r1 = f1[s][0];
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                r0 = rn_add(r0, f0[s][i]);
+                r1 = rn_add(r1, f1[s][i]);
+            }
+            rho0[s] = r0;
+            rho1[s] = r1;
+        }
     }
     float R0[S], R1[S];
     reaction2_f32<S, RK>(a.rkind, (float)a.kappa, (float)a.F, (float)a.k, rho0, rho1, R0, R1);
@@ -70,8 +93,15 @@ __device__ __forceinline__ void collide_pair(const Args &a, float (&f0)[S][Q], f
         }
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            f0[s][i] = rn_fma(c1, f0[s][i], wt0[L::wclass(i)]);
-            f1[s][i] = rn_fma(c1, f1[s][i], wt1[L::wclass(i)]);
+            if constexpr (PackPair<Q, S>::value) {
+                const float2 v = rn_fma2(pair2(c1), make_float2(f0[s][i], f1[s][i]),
+                                         make_float2(wt0[L::wclass(i)], wt1[L::wclass(i)]));
+                f0[s][i] = v.x;
+                f1[s][i] = v.y;
+            } else {
+                f0[s][i] = rn_fma(c1, f0[s][i], wt0[L::wclass(i)]);
+                f1[s][i] = rn_fma(c1, f1[s][i], wt1[L::wclass(i)]);
+            }
         }
     }
 }

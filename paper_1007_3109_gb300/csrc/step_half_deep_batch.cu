@@ -137,7 +137,7 @@ cudaError_t launch_k(int K, int Q, int S, const DeepItem *items, int n, int64_t 
 
 }  // namespace
 
-int batch_half_default_k(bool v8) { return v8 ? 5 : 4; }
+int batch_half_default_k() { return 4; }
 
 int64_t batch_half_deep_plan(int K, int Q, int S, int half_kind, DeepItem *items, int n) {
     return half_kind ? plan_k<1>(K, Q, S, items, n) : plan_k<0>(K, Q, S, items, n);

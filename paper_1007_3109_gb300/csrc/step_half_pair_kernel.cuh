@@ -48,46 +48,96 @@ __device__ __forceinline__ float hi16(unsigned w) {
     return half::h2f<H>(w >> 16);
 }
 
+// f = fma(w, rho*, g) of the lane's two sites: one packed FP32x2
+// instruction (PK) or two scalar ones, the same bits.
+template <bool PK>
+__device__ __forceinline__ void pull_pair(float w, float r0, float r1, float g0, float g1, float &f0, float &f1) {
+    if constexpr (PK) {
+        const float2 v = rn_fma2(pair2(w), make_float2(r0, r1), make_float2(g0, g1));
+        f0 = v.x;
+        f1 = v.y;
+    } else {
+        f0 = rn_fma(w, r0, g0);
+        f1 = rn_fma(w, r1, g1);
+    }
+}
+
 // Collision of the lane's two sites in the stored form (collide_half's
 // operations per site): rho_s = sum_i f_i (index order), R, rho*_s = rho_s +
 // R_s, the deviations g_i = (1 - omega) fma(-w_i, rho, f_i) rounded to 16 bits
 // (both columns in one paired conversion, kept packed in gp) and their sum
-// over i >= 1 in index order.  RK >= 0: the reaction kind fixed at compile time.
-template <int Q, int S, int H, int RK>
+// over i >= 1 in index order.  PK: the two sites' operands packed in pairs
+// (FP32x2 instructions, each component rounded as the scalar operation, half
+// the issue slots; the constant pairs take registers, so it is the form of
+// the launch bounds that leave room for them).  RK >= 0: the reaction kind
+// fixed at compile time.
+template <int Q, int S, int H, int RK, bool PK>
 __device__ __forceinline__ void collide_half_pair(const tb::SegArgs &g, const float (&f0)[S][Q],
                                                   const float (&f1)[S][Q], float (&rho0)[S], float (&rho1)[S],
                                                   float (&rs0)[S], float (&rs1)[S], unsigned (&gp)[S][Q],
                                                   float (&gs0)[S], float (&gs1)[S]) {
+    if constexpr (PK) {
+        float2 r[S];
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-        float r0 = f0[s][0], r1 = f1[s][0];
+        for (int s = 0; s < S; ++s) {
+            r[s] = make_float2(f0[s][0], f1[s][0]);
 #pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            r0 = rn_add(r0, f0[s][i]);
-            r1 = rn_add(r1, f1[s][i]);
+            for (int i = 1; i < Q; ++i) r[s] = rn_add2(r[s], make_float2(f0[s][i], f1[s][i]));
+            rho0[s] = r[s].x;
+            rho1[s] = r[s].y;
         }
-        rho0[s] = r0;
-        rho1[s] = r1;
-    }
-    float R0[S], R1[S];
-    reaction2_f32<S, RK>(g.rkind, g.kappa, g.F, g.k, rho0, rho1, R0, R1);
+        float R0[S], R1[S];
+        reaction2_f32<S, RK>(g.rkind, g.kappa, g.F, g.k, rho0, rho1, R0, R1);
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-        rs0[s] = rn_add(rho0[s], R0[s]);
-        rs1[s] = rn_add(rho1[s], R1[s]);
-        const float c1 = rn_sub(1.f, g.omega[s]);
-        float a0 = 0.f, a1 = 0.f;
+        for (int s = 0; s < S; ++s) {
+            const float2 rs = rn_add2(r[s], make_float2(R0[s], R1[s]));
+            rs0[s] = rs.x;
+            rs1[s] = rs.y;
+            const float2 c1 = pair2(rn_sub(1.f, g.omega[s]));
+            float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            const float w = weight<Q, float>(i);
-            const unsigned p =
-                half::f2h2<H>(rn_mul(c1, rn_fma(-w, rho0[s], f0[s][i])), rn_mul(c1, rn_fma(-w, rho1[s], f1[s][i])));
-            gp[s][i] = p;
-            a0 = rn_add(a0, lo16<H>(p));
-            a1 = rn_add(a1, hi16<H>(p));
+            for (int i = 1; i < Q; ++i) {
+                const float2 d =
+                    rn_mul2(c1, rn_fma2(pair2(-weight<Q, float>(i)), r[s], make_float2(f0[s][i], f1[s][i])));
+                const unsigned p = half::f2h2<H>(d.x, d.y);
+                gp[s][i] = p;
+                acc = rn_add2(acc, make_float2(lo16<H>(p), hi16<H>(p)));
+            }
+            gs0[s] = acc.x;
+            gs1[s] = acc.y;
         }
-        gs0[s] = a0;
-        gs1[s] = a1;
+    } else {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            float r0 = f0[s][0], r1 = f1[s][0];
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                r0 = rn_add(r0, f0[s][i]);
+                r1 = rn_add(r1, f1[s][i]);
+            }
+            rho0[s] = r0;
+            rho1[s] = r1;
+        }
+        float R0[S], R1[S];
+        reaction2_f32<S, RK>(g.rkind, g.kappa, g.F, g.k, rho0, rho1, R0, R1);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            rs0[s] = rn_add(rho0[s], R0[s]);
+            rs1[s] = rn_add(rho1[s], R1[s]);
+            const float c1 = rn_sub(1.f, g.omega[s]);
+            float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                const float w = weight<Q, float>(i);
+                const unsigned p = half::f2h2<H>(rn_mul(c1, rn_fma(-w, rho0[s], f0[s][i])),
+                                                 rn_mul(c1, rn_fma(-w, rho1[s], f1[s][i])));
+                gp[s][i] = p;
+                a0 = rn_add(a0, lo16<H>(p));
+                a1 = rn_add(a1, hi16<H>(p));
+            }
+            gs0[s] = a0;
+            gs1[s] = a1;
+        }
     }
 }
 
@@ -108,6 +158,7 @@ __global__ void __launch_bounds__(NW * 32, MINB)
     constexpr int HL = HalfPairGeom<K>::HL;
     constexpr int WO = HalfPairGeom<K>::WO;
     constexpr int KC = K > 1 ? K - 1 : 1;
+    constexpr bool PK = MINB <= 2;  // packed pairs where the launch bounds allow 255 registers
     static_assert(K >= 1 && K <= 8 && NS >= 4 && WO > 0 && kSp % 16 == 0, "depth 1 .. 8, four staged rows");
     extern __shared__ __align__(16) unsigned char hps[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -224,7 +275,7 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                     rsh[d][1][1] = v.y;
                     rsh[d][1][2] = r;
                 }
-                float a0s = 0.f, a1s = 0.f;
+                float2 own = make_float2(0.f, 0.f);  // the middle row's own-deviation sums
 #pragma unroll
                 for (int i = 1; i < Q; ++i) {
                     const int dv = s * kSp + CW * 4 + (i - 1) * CW * 2 + 2 * t0;  // the lane's pair of plane i
@@ -241,16 +292,19 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                         g0 = lo16<H>(wsrc);
                         g1 = hi16<H>(wsrc);
                     }
-                    const float w = weight<Q, float>(i);
-                    f0[s][i] = rn_fma(w, rsh[1 - L::ey(i)][0][1 - L::ex(i)], g0);
-                    f1[s][i] = rn_fma(w, rsh[1 - L::ey(i)][1][1 - L::ex(i)], g1);
-                    a0s = rn_add(a0s, lo16<H>(wown));
-                    a1s = rn_add(a1s, hi16<H>(wown));
+                    pull_pair<PK>(weight<Q, float>(i), rsh[1 - L::ey(i)][0][1 - L::ex(i)],
+                                  rsh[1 - L::ey(i)][1][1 - L::ex(i)], g0, g1, f0[s][i], f1[s][i]);
+                    if constexpr (PK) {
+                        own = rn_add2(own, make_float2(lo16<H>(wown), hi16<H>(wown)));
+                    } else {
+                        own.x = rn_add(own.x, lo16<H>(wown));
+                        own.y = rn_add(own.y, hi16<H>(wown));
+                    }
                 }
-                f0[s][0] = rn_fma(weight<Q, float>(0), rsh[1][0][1], -a0s);
-                f1[s][0] = rn_fma(weight<Q, float>(0), rsh[1][1][1], -a1s);
+                f0[s][0] = rn_fma(weight<Q, float>(0), rsh[1][0][1], -own.x);
+                f1[s][0] = rn_fma(weight<Q, float>(0), rsh[1][1][1], -own.y);
             }
-            collide_half_pair<Q, S, H, RK>(g, f0, f1, rho0, rho1, rs0, rs1, gp, gs0, gs1);
+            collide_half_pair<Q, S, H, RK, PK>(g, f0, f1, rho0, rho1, rs0, rs1, gp, gs0, gs1);
 #pragma unroll
             for (int m = 1; m < K; ++m) {  // level m + 1 from level m (carried index m - 1)
 #pragma unroll
@@ -286,9 +340,8 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                             g0 = lo16<H>(wsrc);
                             g1 = hi16<H>(wsrc);
                         }
-                        const float w = weight<Q, float>(i);
-                        f0[s][i] = rn_fma(w, rsh[1 - L::ey(i)][0][1 - L::ex(i)], g0);
-                        f1[s][i] = rn_fma(w, rsh[1 - L::ey(i)][1][1 - L::ex(i)], g1);
+                        pull_pair<PK>(weight<Q, float>(i), rsh[1 - L::ey(i)][0][1 - L::ex(i)],
+                                      rsh[1 - L::ey(i)][1][1 - L::ex(i)], g0, g1, f0[s][i], f1[s][i]);
                     }
                     f0[s][0] = rn_fma(weight<Q, float>(0), P1r[m - 1][0][s], -E0s[m - 1][0][s]);
                     f1[s][0] = rn_fma(weight<Q, float>(0), P1r[m - 1][1][s], -E0s[m - 1][1][s]);
@@ -312,7 +365,7 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                         }
                     }
                 }
-                collide_half_pair<Q, S, H, RK>(g, f0, f1, rho0, rho1, rs0, rs1, gp, gs0, gs1);
+                collide_half_pair<Q, S, H, RK, PK>(g, f0, f1, rho0, rho1, rs0, rs1, gp, gs0, gs1);
             }
             if (j >= 2 * K) {  // level K of row y0 + j - 2K: window columns HL .. 63 - HL
                 const int x = xb + 2 * lane;
